@@ -1,0 +1,130 @@
+"""Pins of the oracle's L and N (paper Sec. 2.5) against closed forms and invariants."""
+
+import numpy as np
+import pytest
+
+from oracle import spectrum
+from oracle.elements import dg1_values
+from oracle.operators import UPWIND_AS_PRINTED
+from oracle.quadrature import triangle_rule
+from paper_2103_07706_gb300.inputs import harmonic_state
+
+R = 6.37122e6
+
+
+def _state(m, seed=2103, lmax=8):
+    U, _ = harmonic_state(m.mesh.verts, m.mesh.cells, seed, lmax)
+    return U
+
+
+def proj_u(ops, v):
+    """L2 projection of a 3-vector field v(x) onto BDM2."""
+    A = ops.asm
+    xq, wq = triangle_rule(4)
+    psi = A.element.values(xq)
+    x = A.a[:, None, :] + np.einsum("fxa,qa->fqx", A.J, xq)
+    b_loc = np.einsum("q,fxa,qia,fqx->fi", wq, A.J, psi, v(x)) * A.sign
+    b = np.zeros(ops.n_u)
+    np.add.at(b, A.udofs.ravel(), b_loc.ravel())
+    return ops.solve_M1(b)
+
+
+def proj_eta(ops, f):
+    A = ops.asm
+    xq, wq = triangle_rule(4)
+    x = A.a[:, None, :] + np.einsum("fxa,qa->fqx", A.J, xq)
+    b = np.einsum("q,f,qi,fq->fi", wq, A.det, dg1_values(xq), f(x)).ravel()
+    return ops.solve_M2(b)
+
+
+def test_spectrum_purely_imaginary(om):
+    """L is skew in the energy inner product, so its eigenvalues are imaginary (Sec. 2.5)."""
+    m = om(1)
+    ev = np.linalg.eigvals(spectrum.dense_L(m.ops))
+    assert np.abs(ev.real).max() <= 1e-10 * np.abs(ev).max()
+
+
+@pytest.mark.parametrize("r", [2, 3])
+def test_energy_skewness(om, r):
+    m = om(r)
+    U = np.random.default_rng(3).standard_normal(m.n)
+    LU = m.L(U)
+    assert abs(spectrum.w_inner(m.ops, LU, U)) <= 1e-13 * np.sqrt(
+        spectrum.w_inner(m.ops, LU, LU) * spectrum.w_inner(m.ops, U, U))
+    u = U[: m.n_u]
+    assert abs(u @ (m.ops.C @ u)) <= 1e-14 * abs(u) @ (abs(m.ops.C) @ abs(u))
+
+
+def test_rest_state_is_steady(om):
+    """(u, eta) = (0, const): L U = 0 and N(U) = 0."""
+    m = om(3)
+    U = np.zeros(m.n)
+    U[m.n_u:] = 7.0
+    LU = m.L(U)
+    scale = m.ops.g * 7.0 * np.abs(m.ops.D).sum(axis=0).max()
+    assert np.abs(m.ops.linear_rhs(U)).max() <= 1e-14 * scale
+    assert np.abs(m.N(U)).max() == 0.0
+    assert np.isfinite(LU).all()
+
+
+def test_mass_conservation_and_homogeneity(om):
+    m = om(3)
+    U = _state(m)
+    NR = m.ops.nonlinear_rhs(U)
+    LR = m.ops.linear_rhs(np.random.default_rng(4).standard_normal(m.n))
+    assert abs(NR[m.n_u:].sum()) <= 1e-15 * np.abs(NR[m.n_u:]).sum()
+    assert abs(LR[m.n_u:].sum()) <= 1e-14 * np.abs(LR[m.n_u:]).sum()
+    # b = 0: N is quadratic and the upwind choice is invariant under positive scaling
+    N2 = m.ops.nonlinear_rhs(2.0 * U)
+    assert np.abs(N2 - 4.0 * NR).max() <= 1e-14 * np.abs(NR).max()
+
+
+def test_upwind_elevation_flux_dissipates(om):
+    """With a divergence-free velocity, the upwind elevation flux makes
+    eta . r_eta = -1/2 sum_facets int |u.n| [[eta]]^2 <= 0 (Sec. 2.5: upwinding is
+    the scheme's only dissipation).  A downwind (or centred-with-wrong-sign)
+    reading breaks the sign."""
+    m = om(3)
+    U = _state(m)
+    rng = np.random.default_rng(5)
+    U[m.n_u:] = rng.standard_normal(m.n_eta) * 50.0
+    r = m.ops.nonlinear_rhs(U)[m.n_u:]
+    eta = U[m.n_u:]
+    assert eta @ r < 0.0
+    assert abs(m.ops.D @ U[: m.n_u]).max() < 1e-12 * abs(m.ops.D).max() * abs(U[: m.n_u]).max()
+
+
+def _solid_body_errors(m, omega_body=1e-5, amp=100.0):
+    ops = m.ops
+    ub = lambda x: omega_body * np.stack([-x[..., 1], x[..., 0], 0 * x[..., 0]], -1)  # noqa: E731
+
+    def n_u_exact(x):
+        # -(u.grad)u for zonal solid-body rotation: the tangential part of the
+        # centripetal acceleration, omega^2 P (x, y, 0)
+        xp = np.stack([x[..., 0], x[..., 1], 0 * x[..., 0]], -1)
+        xh = x / np.linalg.norm(x, axis=-1, keepdims=True)
+        return omega_body ** 2 * (xp - (xp * xh).sum(-1, keepdims=True) * xh)
+
+    eta_f = lambda x: amp * x[..., 0] / R                      # noqa: E731
+    n_eta_exact = lambda x: omega_body * amp * x[..., 1] / R    # noqa: E731  (-u . grad eta)
+    U = np.concatenate([proj_u(ops, ub), proj_eta(ops, eta_f)])
+    nu, ne = ops.split(m.N(U))
+    pu, pe = proj_u(ops, n_u_exact), proj_eta(ops, n_eta_exact)
+    eu, ee = nu - pu, ne - pe
+    return (np.sqrt(eu @ (ops.M1 @ eu) / (pu @ (ops.M1 @ pu))),
+            np.sqrt(ee @ (ops.M2 @ ee) / (pe @ (ops.M2 @ pe))))
+
+
+@pytest.mark.parametrize("upwind", [0, UPWIND_AS_PRINTED])
+def test_nonlinear_consistency_solid_body(om, upwind):
+    """N converges to -(u.grad)u and -div(u eta) for solid-body rotation.
+
+    On flat facets the rate is first order (facet normals differ from the
+    sphere's by O(h)).  A flipped facet sign, a dropped kinetic-energy term or
+    mismatched facet points leave an O(1) error that does not decrease.
+    """
+    errs = [_solid_body_errors(om(r, upwind=upwind)) for r in (2, 3, 4)]
+    for k in range(2):
+        e = [x[k] for x in errs]
+        assert e[2] < 0.06
+        assert e[0] / e[1] > 1.8 and e[1] / e[2] > 1.8
