@@ -1,0 +1,160 @@
+/*
+ * pavg.h - phase-averaged rotating shallow water on the sphere, GB300 (sm_103a).
+ *
+ * C-ABI of libpavg.so.  The method is that of Yamazaki, Cotter & Wingate,
+ * "Time parallel integration and phase averaging for the nonlinear shallow
+ * water equations on the sphere" (arXiv 2103.07706):
+ *   U_t = L U + N(U)                                   (Sec. 2.1, Eq. split_eqs)
+ *   N-bar(U) = sum_m w_m e^{-s_m L} N(e^{s_m L} U)      (Sec. 2.2, Eq. vt_discretised)
+ *   e^{tL} by a truncated Chebyshev series               (Sec. 2.4, Eq. cheby)
+ *   averaged Lawson RK4                                  (Sec. 2.3, Eqs. stage1_c-stage4)
+ * with L and N the compatible finite element operators of Sec. 2.5
+ * (BDM2 velocity, DG1 elevation) on an icosahedral mesh (Sec. 3).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * State vectors are FP64, contiguous, u first then eta:
+ *   U = [u (n_u = 3E + 3F) | eta (n_eta = 3F)],  n = n_u + n_eta,
+ * F = 20 * 4^r cells, E = 30 * 4^r edges.  Velocity DOF 3e + j is the j-th
+ * Legendre moment (j = 0, 1, 2 on [0, 1], low -> high vertex) of the flux
+ * across edge e towards the side of t x k (t the low->high tangent, k the
+ * cell's outward normal); DOF 3E + 3c + j is the j-th interior moment of cell c
+ * against (1,0), (0,1), (-y,x) on the reference triangle.  Elevation DOF
+ * 3c + i is the value at local vertex i of cell c.  Cells, vertices and edges
+ * are numbered by the canonical icosahedral construction exported by
+ * pavg_mesh_export.  A batch of B states is laid out [B][n].
+ *
+ * Pointers marked "device" are caller-owned CUDA device memory (e.g. a torch
+ * tensor's data_ptr()); the library never frees them.  Calls that take a
+ * `stream` enqueue their work on that cudaStream_t (NULL = legacy default
+ * stream) and return without synchronising unless stated; the caller keeps
+ * inputs alive until the work completes.  One context must not be used from
+ * two streams at the same time: it owns one set of scratch buffers.
+ *
+ * Every function returns PAVG_OK (0) or a negative error code and never throws.
+ * Errors raised on the device (a CG solve that did not converge, a bounded
+ * device-side wait that timed out, a non-finite value) are latched in the
+ * context and reported by pavg_get_stats / pavg_sync.  pavg_last_error gives a
+ * readable message for the last failure of a context.
+ */
+#ifndef PAVG_H
+#define PAVG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PAVG_OK 0
+#define PAVG_ERR_INVAL (-1)     /* bad argument (null pointer, size, range) */
+#define PAVG_ERR_NOMEM (-2)     /* device allocation failed */
+#define PAVG_ERR_CUDA (-3)      /* a CUDA runtime call failed */
+#define PAVG_ERR_NOCONV (-4)    /* mass-matrix CG reached cg_maxit */
+#define PAVG_ERR_NONFINITE (-5) /* NaN or Inf detected */
+#define PAVG_ERR_TIMEOUT (-6)   /* a bounded device-side wait gave up */
+
+#define PAVG_QUAD_MIDPOINT 0     /* s_m = -T/2 + (m + 1/2) T / M            */
+#define PAVG_QUAD_CLOSED 1       /* odd M = 2N+1, s_k = k (T/2) / N, k=-N..N */
+#define PAVG_UPWIND_STANDARD 0   /* u~, (eta-b)~ from the side the flow leaves */
+#define PAVG_UPWIND_AS_PRINTED 1 /* u~ = u+ when u.n+ < 0, as printed in Sec. 2.5 */
+
+typedef struct pavg_ctx pavg_ctx; /* opaque, library-owned */
+
+/* Model parameters (SI units).  Sec. 2.1 (R, Omega, g, H), Sec. 2.4 (cheb_tol). */
+typedef struct {
+  int refinement;         /* r >= 0: F = 20 * 4^r cells (r = 5 is the paper's N_C = 20480) */
+  double radius;          /* R, sphere radius [m] */
+  double omega;           /* Omega, rotation rate [1/s]; f = 2 Omega z / R */
+  double g;               /* gravity [m/s^2] */
+  double H;               /* mean depth [m] */
+  double cheb_tol;        /* Chebyshev tail threshold (1e-6 in Sec. 2.4); > 0 */
+  double cg_rtol;         /* relative residual target of the M1 CG solves; > 0 */
+  int cg_maxit;           /* iteration cap of each M1 CG solve; > 0 */
+  double lambda_max;      /* |lambda_max| of L [1/s]; 0 -> estimate by power iteration at create */
+  int quad_rule;          /* PAVG_QUAD_MIDPOINT or PAVG_QUAD_CLOSED */
+  int upwind_convention;  /* PAVG_UPWIND_STANDARD or PAVG_UPWIND_AS_PRINTED */
+} pavg_params;
+
+/* Fill `p` with the defaults: r = 3, R = 6.37122e6, Omega = 7.292e-5,
+ * g = 9.80616, H = 5000, cheb_tol = 1e-6, cg_rtol = 1e-14, cg_maxit = 400,
+ * lambda_max = 0, midpoint rule, standard upwinding. */
+int pavg_default_params(pavg_params* p);
+
+/* Build the mesh and FE data (Sec. 2.5, Sec. 3) on the current CUDA device and
+ * upload them.  *out receives a new context; free it with pavg_destroy.
+ * Errors: INVAL (bad params, r > 8), NOMEM, CUDA. */
+int pavg_create(const pavg_params* p, pavg_ctx** out);
+int pavg_destroy(pavg_ctx* ctx);
+
+/* Sizes of the discretisation.  Any output pointer may be NULL. */
+int pavg_sizes(const pavg_ctx* ctx, int64_t* n_u, int64_t* n_eta, int64_t* n_cells,
+               int64_t* n_edges, int64_t* n_verts);
+
+/* Copy the canonical mesh to HOST buffers: vert_xyz [V][3] (metres) and
+ * cell_verts [F][3] (counter-clockwise seen from outside).  Either may be NULL. */
+int pavg_mesh_export(const pavg_ctx* ctx, double* vert_xyz, int32_t* cell_verts);
+
+/* Topography b as a DG1 field (device, n_eta doubles, copied).  Default 0. */
+int pavg_set_topography(pavg_ctx* ctx, const double* b_dg1);
+
+/* The lambda_max in use (given, or estimated at create).  Host output. */
+int pavg_lambda_max(const pavg_ctx* ctx, double* out);
+
+/* LU = L U for B states (device [B][n] in, device [B][n] out; may not alias).
+ * Sec. 2.5, Eq. ueq_int and the eta equation after it. */
+int pavg_linear(pavg_ctx* ctx, const double* U, double* LU, int B, void* stream);
+
+/* NU = N(U) for B states (device [B][n]; may not alias).  Sec. 2.5, the two
+ * weak forms after Eq. ueq_int, with upwinded facet terms. */
+int pavg_nonlinear(pavg_ctx* ctx, const double* U, double* NU, int B, void* stream);
+
+/* out = e^{tL} U for B states by the truncated Chebyshev series (Sec. 2.4,
+ * Eq. cheby, truncation at cheb_tol).  t in seconds, any sign; t = 0 copies.
+ * U and out are device [B][n] and may not alias. */
+int pavg_expL_apply(pavg_ctx* ctx, double t, const double* U, double* out, int B, void* stream);
+
+/* out = N-bar(U) = sum_m w_m e^{-s_m L} N(e^{s_m L} U) (Sec. 2.2, Eq. vt_discretised),
+ * window T >= 0 seconds, M >= 1 shifts; T = 0 gives N(U).  Shared-basis
+ * evaluation: one Chebyshev chain of L / lambda_max serves every shift and the
+ * backward maps are summed by a Clenshaw recurrence (exact rewriting of the
+ * sum; see the design notes).  U, out: device, n doubles, may not alias.
+ * The work for each (T, M) is captured once in a CUDA graph and replayed. */
+int pavg_averaged_rhs(pavg_ctx* ctx, double T, int M, const double* U, double* out, void* stream);
+
+/* The same sum in its literal form: for each shift its own forward exponential,
+ * N with its mass solves and backward exponential, summed in shift order. */
+int pavg_averaged_rhs_literal(pavg_ctx* ctx, double T, int M, const double* U, double* out,
+                              void* stream);
+
+/* nsteps averaged Lawson RK4 steps of size dt (Sec. 2.3, Eqs. stage1_c to stage4),
+ * in place on the device state U_inout (n doubles). */
+int pavg_timestep(pavg_ctx* ctx, double dt, double T, int M, double* U_inout, int nsteps,
+                  void* stream);
+
+/* Wait for the context's work on `stream` and report latched device errors. */
+int pavg_sync(pavg_ctx* ctx, void* stream);
+
+typedef struct {
+  double lambda_max;      /* in use */
+  int last_degree;        /* Chebyshev degree K of the last exponential / K_max of the last average */
+  int cg_solves;          /* M1 solves since create */
+  int cg_iters_max;       /* largest iteration count of one solve */
+  double cg_iters_mean;   /* mean iterations per solve */
+  int error_flags;        /* bit 0 NOCONV, bit 1 TIMEOUT, bit 2 NONFINITE */
+} pavg_stats;
+
+/* Synchronises the device, then fills *out. */
+int pavg_get_stats(pavg_ctx* ctx, pavg_stats* out);
+
+/* Clear the latched device error flags and the CG counters. */
+int pavg_reset_stats(pavg_ctx* ctx);
+
+/* Readable message of the last failure (static storage owned by the context). */
+const char* pavg_last_error(const pavg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAVG_H */

@@ -1,0 +1,647 @@
+// C-ABI of libpavg (declared in include/pavg.h): context lifetime, buffers and
+// the host-side sequencing of the kernels in device.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "device.h"
+
+using namespace pavg;
+
+namespace {
+
+struct AvgPlan {
+  double T = 0;
+  int M = 0;
+  int K = 0;                 // K_max over shifts
+  double* dA = nullptr;      // [M][K+1]  forward combine
+  double* dB = nullptr;      // [K+1][M]  backward combine
+  cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace
+
+struct pavg_ctx {
+  pavg_params p{};
+  Mesh mesh;
+  DeviceMesh dm;
+  CgWork cg;
+  CgParams cgp{};
+  double lam = 0;
+  int device = 0;
+  // scratch
+  double* ru = nullptr;         // [n_u] assembled velocity rhs
+  double* vec[6] = {};          // [n] general vectors
+  double* io_in = nullptr;      // [n] graph input
+  double* io_out = nullptr;     // [n] graph output
+  double* Q = nullptr;          // [(Kcap+1)][n] Chebyshev basis / backward coefficient vectors
+  double* Um = nullptr;         // [Mcap][n] shifted states
+  double* Rm = nullptr;         // [Mcap][n] weak-form N of the shifted states
+  int Kcap = -1, Mcap = 0;
+  double* host_part = nullptr;
+  double* dpart = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  std::map<std::pair<double, int>, AvgPlan> plans;
+  int last_degree = 0;
+  bool use_graphs = true;
+  std::string err;
+};
+
+namespace {
+
+int set_err(pavg_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return set_err(ctx, PAVG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
+}
+
+template <class T>
+cudaError_t upload(T** p, const std::vector<T>& v) {
+  cudaError_t e = dalloc(p, v.size());
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+}
+
+cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ---------------------------------------------------------------- building blocks
+// velocity part out_u = M1^{-1} b (scaled, plus add); eta part by the caller.
+int enq_cg(pavg_ctx* ctx, const double* b, double* out, double scale, const double* add, cudaStream_t st) {
+  CK(launch_cg(ctx->dm, ctx->cg, ctx->cgp, b, out, scale, add, st));
+  return PAVG_OK;
+}
+
+// out = M^{-1} R (both parts).
+int enq_mass_solve(pavg_ctx* ctx, const double* R, double* out, cudaStream_t st) {
+  const DeviceMesh& m = ctx->dm;
+  int rc = enq_cg(ctx, R, out, 1.0, nullptr, st);
+  if (rc) return rc;
+  CK(launch_m2inv(m, R + m.n_u, 0, out + m.n_u, 0, 1, st));
+  return PAVG_OK;
+}
+
+// One step of the Chebyshev / Clenshaw recurrences:
+//   out = M^{-1}(y + s Khat in) + z,   Khat = [[-C, g D^T], [-H D, 0]]
+// with in, y, z optional (null = 0).  L = M^{-1} Khat (Sec. 2.5).
+int enq_step(pavg_ctx* ctx, const double* in, double s, const double* y, const double* z, double* out,
+             cudaStream_t st) {
+  const DeviceMesh& m = ctx->dm;
+  const int64_t nu = m.n_u;
+  if (in) {
+    CK(cudaMemsetAsync(ctx->ru, 0, sizeof(double) * 3 * m.E, st));
+    CK(launch_apply_K(m, in, s, ctx->p.g, ctx->p.H, y, y ? y + nu : nullptr, z ? z + nu : nullptr, ctx->ru,
+                      out + nu, st));
+    return enq_cg(ctx, ctx->ru, out, 1.0, z, st);
+  }
+  // in == 0: out = M^{-1} y + z
+  if (!y) return set_err(ctx, PAVG_ERR_INVAL, "internal: empty recurrence step");
+  int rc = enq_cg(ctx, y, out, 1.0, z, st);
+  if (rc) return rc;
+  CK(launch_m2inv(m, y + nu, 0, out + nu, 0, 1, st));
+  if (z) CK(launch_lincomb(out + nu, 1.0, out + nu, 1.0, z + nu, 0.0, nullptr, m.n_eta, st));
+  return PAVG_OK;
+}
+
+int enq_linear(pavg_ctx* ctx, const double* U, double* out, cudaStream_t st) {
+  return enq_step(ctx, U, 1.0, nullptr, nullptr, out, st);
+}
+
+int enq_nonlinear(pavg_ctx* ctx, const double* U, double* out, double* scratch, cudaStream_t st) {
+  const DeviceMesh& m = ctx->dm;
+  CK(cudaMemsetAsync(scratch, 0, sizeof(double) * 3 * m.E, st));
+  CK(launch_nonlinear_rhs(m, U, scratch, 1, ctx->p.upwind_convention, st));
+  return enq_mass_solve(ctx, scratch, out, st);
+}
+
+// out = e^{tL} U (Sec. 2.4): X = sgn(t) L / lambda_max, Q_0 = U, Q_1 = X U,
+// Q_{k+1} = 2 X Q_k + Q_{k-1}; out = sum_k c_k(lambda |t|) Q_k.
+int enq_expL(pavg_ctx* ctx, double t, const double* U, double* out, cudaStream_t st) {
+  const int64_t n = ctx->dm.n;
+  if (t == 0.0) {
+    CK(cudaMemcpyAsync(out, U, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    ctx->last_degree = 0;
+    return PAVG_OK;
+  }
+  std::vector<double> c = cheb_coefficients(ctx->lam * std::fabs(t), ctx->p.cheb_tol);
+  const int K = (int)c.size() - 1;
+  ctx->last_degree = K;
+  const double sgn = t > 0 ? 1.0 : -1.0;
+  double* acc = ctx->vec[3];
+  CK(launch_lincomb(acc, c[0], U, 0.0, nullptr, 0.0, nullptr, n, st));
+  const double* qm1 = nullptr;
+  const double* qk = U;
+  double* bufs[3] = {ctx->vec[0], ctx->vec[1], ctx->vec[2]};
+  for (int k = 0; k < K; ++k) {
+    double* qn = bufs[k % 3];
+    int rc = enq_step(ctx, qk, (k == 0 ? 1.0 : 2.0) * sgn / ctx->lam, nullptr, qm1, qn, st);
+    if (rc) return rc;
+    CK(launch_lincomb(acc, 1.0, acc, c[k + 1], qn, 0.0, nullptr, n, st));
+    qm1 = qk;
+    qk = qn;
+  }
+  CK(cudaMemcpyAsync(out, acc, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  return PAVG_OK;
+}
+
+int ensure_avg_workspace(pavg_ctx* ctx, int K, int M) {
+  const int64_t n = ctx->dm.n;
+  if (K <= ctx->Kcap && M <= ctx->Mcap) return PAVG_OK;
+  // buffers move: drop every captured graph that refers to them
+  for (auto& kv : ctx->plans)
+    if (kv.second.exec) { cudaGraphExecDestroy(kv.second.exec); kv.second.exec = nullptr; }
+  cudaDeviceSynchronize();
+  int nk = std::max(K, ctx->Kcap), nm = std::max(M, ctx->Mcap);
+  cudaFree(ctx->Q); cudaFree(ctx->Um); cudaFree(ctx->Rm);
+  ctx->Q = ctx->Um = ctx->Rm = nullptr;
+  ctx->Kcap = -1; ctx->Mcap = 0;
+  if (dalloc(&ctx->Q, (size_t)(nk + 1) * n) != cudaSuccess || dalloc(&ctx->Um, (size_t)nm * n) != cudaSuccess ||
+      dalloc(&ctx->Rm, (size_t)nm * n) != cudaSuccess)
+    return set_err(ctx, PAVG_ERR_NOMEM, "averaged_rhs workspace allocation failed");
+  ctx->Kcap = nk;
+  ctx->Mcap = nm;
+  return PAVG_OK;
+}
+
+int get_plan(pavg_ctx* ctx, double T, int M, AvgPlan** out) {
+  auto key = std::make_pair(T, M);
+  auto it = ctx->plans.find(key);
+  if (it != ctx->plans.end()) { *out = &it->second; return PAVG_OK; }
+  std::vector<double> s, w;
+  int rc = shifts_weights(T, M, ctx->p.quad_rule, &s, &w);
+  if (rc) return set_err(ctx, rc, "invalid T / M / quadrature rule");
+  std::vector<std::vector<double>> cs(M);
+  int K = 0;
+  for (int m = 0; m < M; ++m) {
+    cs[m] = cheb_coefficients(ctx->lam * std::fabs(s[m]), ctx->p.cheb_tol);
+    K = std::max(K, (int)cs[m].size() - 1);
+  }
+  AvgPlan pl;
+  pl.T = T; pl.M = M; pl.K = K;
+  std::vector<double> A((size_t)M * (K + 1), 0.0), B((size_t)(K + 1) * M, 0.0);
+  for (int m = 0; m < M; ++m) {
+    double sg = s[m] >= 0 ? 1.0 : -1.0;
+    double fw = 1.0, bw = 1.0;  // sgn^k and (-sgn)^k
+    for (int k = 0; k <= K; ++k) {
+      double ck = k < (int)cs[m].size() ? cs[m][k] : 0.0;
+      A[(size_t)m * (K + 1) + k] = ck * fw;
+      B[(size_t)k * M + m] = w[m] * ck * bw;
+      fw *= sg;
+      bw *= -sg;
+    }
+  }
+  if (upload(&pl.dA, A) != cudaSuccess || upload(&pl.dB, B) != cudaSuccess)
+    return set_err(ctx, PAVG_ERR_NOMEM, "plan upload failed");
+  auto res = ctx->plans.emplace(key, pl);
+  *out = &res.first->second;
+  return PAVG_OK;
+}
+
+// Shared-basis averaged nonlinearity (Sec. 2.2, Eq. vt_discretised):
+//   U_m = sum_k c_k(lam|s_m|) sgn(s_m)^k Q_k,  Q_k = Q_k(L/lam) U      (forward)
+//   r_m = weak-form N(U_m)                                             (Sec. 2.5)
+//   y_k = sum_m w_m c_k(lam|s_m|) (-sgn s_m)^k r_m
+//   S   = sum_k Q_k(L/lam) M^{-1} y_k by Clenshaw:
+//         b_k = M^{-1}(y_k + (2/lam) Khat b_{k+1}) + b_{k+2},
+//         S   = M^{-1}(y_0 + Khat b_1 / lam) + b_2.
+// Equal to sum_m w_m e^{-s_m L} M^{-1} r_m term by term because every factor is
+// a polynomial in the one operator L.
+int enq_avg(pavg_ctx* ctx, const AvgPlan& pl, const double* U, double* out, cudaStream_t st) {
+  const DeviceMesh& m = ctx->dm;
+  const int64_t n = m.n;
+  const int K = pl.K, M = pl.M;
+  if (pl.T == 0.0) return enq_nonlinear(ctx, U, out, ctx->Rm, st);
+  double* Q = ctx->Q;
+  CK(cudaMemcpyAsync(Q, U, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  for (int k = 0; k < K; ++k) {
+    int rc = enq_step(ctx, Q + (int64_t)k * n, (k == 0 ? 1.0 : 2.0) / ctx->lam, nullptr,
+                      k == 0 ? nullptr : Q + (int64_t)(k - 1) * n, Q + (int64_t)(k + 1) * n, st);
+    if (rc) return rc;
+  }
+  CK(launch_combine(pl.dA, M, K + 1, Q, n, ctx->Um, n, n, st));
+  CK(cudaMemset2DAsync(ctx->Rm, sizeof(double) * n, 0, sizeof(double) * 3 * m.E, M, st));
+  CK(launch_nonlinear_rhs(m, ctx->Um, ctx->Rm, M, ctx->p.upwind_convention, st));
+  CK(launch_combine(pl.dB, K + 1, M, ctx->Rm, n, Q, n, n, st));  // y_k overwrite Q_k
+  double* b[3] = {ctx->vec[0], ctx->vec[1], ctx->vec[2]};
+  const double* b1 = nullptr;  // b_{k+1}
+  const double* b2 = nullptr;  // b_{k+2}
+  for (int k = K; k >= 1; --k) {
+    double* bk = b[k % 3];
+    int rc = enq_step(ctx, b1, 2.0 / ctx->lam, Q + (int64_t)k * n, b2, bk, st);
+    if (rc) return rc;
+    b2 = b1;
+    b1 = bk;
+  }
+  int rc = enq_step(ctx, b1, 1.0 / ctx->lam, Q, b2, out, st);
+  if (rc) return rc;
+  ctx->last_degree = K;
+  return PAVG_OK;
+}
+
+int run_avg(pavg_ctx* ctx, double T, int M, const double* U, double* out, cudaStream_t st) {
+  AvgPlan* pl = nullptr;
+  int rc = get_plan(ctx, T, M, &pl);
+  if (rc) return rc;
+  rc = ensure_avg_workspace(ctx, pl->K, M);
+  if (rc) return rc;
+  const int64_t n = ctx->dm.n;
+  if (!ctx->use_graphs) return enq_avg(ctx, *pl, U, out, st);
+  if (!pl->exec) {
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc2 = enq_avg(ctx, *pl, ctx->io_in, ctx->io_out, ctx->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    if (rc2) { if (graph) cudaGraphDestroy(graph); return rc2; }
+    if (e != cudaSuccess) return set_err(ctx, PAVG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&pl->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { pl->exec = nullptr; return set_err(ctx, PAVG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e)); }
+  }
+  CK(cudaMemcpyAsync(ctx->io_in, U, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  CK(cudaGraphLaunch(pl->exec, st));
+  CK(cudaMemcpyAsync(out, ctx->io_out, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  ctx->last_degree = pl->K;
+  return PAVG_OK;
+}
+
+double host_winner(pavg_ctx* ctx, const double* U, const double* V) {
+  int nb = 0;
+  if (launch_winner(ctx->dm, U, V, ctx->p.g, ctx->p.H, ctx->dpart, &nb, 0) != cudaSuccess) return NAN;
+  if (cudaMemcpy(ctx->host_part, ctx->dpart, sizeof(double) * nb, cudaMemcpyDeviceToHost) != cudaSuccess) return NAN;
+  double s = 0;
+  for (int i = 0; i < nb; ++i) s += ctx->host_part[i];
+  return s;
+}
+
+// Sec. 2.4 needs |lambda_max|; the paper does not say how it is found.  Power
+// iteration on -L^2 (self-adjoint, positive semi-definite in the energy inner
+// product) from a seeded random start; the Rayleigh quotient approaches
+// lambda_max^2 from below, so the estimate is widened by 2 %.
+int estimate_lambda(pavg_ctx* ctx) {
+  const int64_t n = ctx->dm.n;
+  std::mt19937_64 rng(7706);
+  std::normal_distribution<double> nd;
+  std::vector<double> h(n);
+  for (auto& x : h) x = nd(rng);
+  double *v = ctx->vec[4], *Lv = ctx->vec[5], *w = ctx->vec[3];
+  if (cudaMemcpy(v, h.data(), sizeof(double) * n, cudaMemcpyHostToDevice) != cudaSuccess)
+    return set_err(ctx, PAVG_ERR_CUDA, "lambda_max: upload failed");
+  double nv = std::sqrt(host_winner(ctx, v, v));
+  launch_lincomb(v, 1.0 / nv, v, 0, nullptr, 0, nullptr, n, 0);
+  double est = 0;
+  for (int it = 0; it < 400; ++it) {
+    int rc = enq_linear(ctx, v, Lv, 0);
+    if (rc) return rc;
+    double rq = host_winner(ctx, Lv, Lv);
+    rc = enq_linear(ctx, Lv, w, 0);
+    if (rc) return rc;
+    double nw = std::sqrt(host_winner(ctx, w, w));
+    if (!(nw > 0) || !std::isfinite(rq)) return set_err(ctx, PAVG_ERR_NONFINITE, "lambda_max: iteration failed");
+    launch_lincomb(v, -1.0 / nw, w, 0, nullptr, 0, nullptr, n, 0);
+    double nest = std::sqrt(rq);
+    if (est > 0 && std::fabs(nest - est) <= 1e-9 * nest) { est = nest; break; }
+    est = nest;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) return set_err(ctx, PAVG_ERR_CUDA, "lambda_max: sync failed");
+  ctx->lam = 1.02 * est;
+  return PAVG_OK;
+}
+
+int check_flags(pavg_ctx* ctx) {
+  int f = 0;
+  if (cudaMemcpy(&f, ctx->cg.flags, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return set_err(ctx, PAVG_ERR_CUDA, "reading device flags failed");
+  if (f & kFlagTimeout) return set_err(ctx, PAVG_ERR_TIMEOUT, "a bounded device-side wait timed out");
+  if (f & kFlagNonFinite) return set_err(ctx, PAVG_ERR_NONFINITE, "non-finite value detected");
+  if (f & kFlagNoConv) return set_err(ctx, PAVG_ERR_NOCONV, "M1 CG did not converge within cg_maxit");
+  return PAVG_OK;
+}
+
+void free_ctx(pavg_ctx* c) {
+  if (!c) return;
+  for (auto& kv : c->plans) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    cudaFree(kv.second.dA);
+    cudaFree(kv.second.dB);
+  }
+  DeviceMesh& m = c->dm;
+  cudaFree(m.cell_edges); cudaFree(m.cell_aligned); cudaFree(m.edge_plus); cudaFree(m.edge_minus);
+  cudaFree(m.edge_lpos); cudaFree(m.M1); cudaFree(m.C); cudaFree(m.det); cudaFree(m.G); cudaFree(m.dinv);
+  cudaFree(m.topo);
+  CgWork& w = c->cg;
+  cudaFree(w.x); cudaFree(w.r[0]); cudaFree(w.r[1]); cudaFree(w.s[0]); cudaFree(w.s[1]);
+  cudaFree(w.w[0]); cudaFree(w.w[1]); cudaFree(w.w[2]); cudaFree(w.p); cudaFree(w.partial);
+  cudaFree(w.bar); cudaFree(w.flags); cudaFree(w.stats);
+  cudaFree(c->ru);
+  for (auto* v : c->vec) cudaFree(v);
+  cudaFree(c->io_in); cudaFree(c->io_out); cudaFree(c->Q); cudaFree(c->Um); cudaFree(c->Rm);
+  cudaFree(c->dpart);
+  if (c->host_part) cudaFreeHost(c->host_part);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  delete c;
+}
+
+bool valid_params(const pavg_params* p) {
+  return p && p->refinement >= 0 && p->refinement <= 8 && p->radius > 0 && p->g > 0 && p->H > 0 &&
+         p->cheb_tol > 0 && p->cg_rtol > 0 && p->cg_maxit > 0 && p->lambda_max >= 0 && std::isfinite(p->omega) &&
+         (p->quad_rule == PAVG_QUAD_MIDPOINT || p->quad_rule == PAVG_QUAD_CLOSED) &&
+         (p->upwind_convention == PAVG_UPWIND_STANDARD || p->upwind_convention == PAVG_UPWIND_AS_PRINTED);
+}
+
+}  // namespace
+
+extern "C" {
+
+int pavg_default_params(pavg_params* p) {
+  if (!p) return PAVG_ERR_INVAL;
+  p->refinement = 3;
+  p->radius = 6.37122e6;
+  p->omega = 7.292e-5;
+  p->g = 9.80616;
+  p->H = 5000.0;
+  p->cheb_tol = 1e-6;
+  p->cg_rtol = 1e-14;
+  p->cg_maxit = 400;
+  p->lambda_max = 0.0;
+  p->quad_rule = PAVG_QUAD_MIDPOINT;
+  p->upwind_convention = PAVG_UPWIND_STANDARD;
+  return PAVG_OK;
+}
+
+int pavg_create(const pavg_params* p, pavg_ctx** out) {
+  if (!out) return PAVG_ERR_INVAL;
+  *out = nullptr;
+  if (!valid_params(p)) return PAVG_ERR_INVAL;
+  pavg_ctx* ctx = new pavg_ctx();
+  ctx->p = *p;
+  ctx->cgp.rtol = p->cg_rtol;
+  ctx->cgp.maxit = p->cg_maxit;
+  int rc = PAVG_OK;
+  try {
+    cudaGetDevice(&ctx->device);
+    build_mesh(p->refinement, p->radius, &ctx->mesh);
+    RefElement el;
+    build_reference_element(&el);
+    HostCellData hc;
+    ConstTables tab;
+    build_cell_data(ctx->mesh, el, p->omega, &hc, &tab);
+    if (upload_tables(tab) != cudaSuccess) { rc = set_err(ctx, PAVG_ERR_CUDA, "constant upload failed"); throw 0; }
+    const Mesh& ms = ctx->mesh;
+    DeviceMesh& m = ctx->dm;
+    m.F = ms.F(); m.E = ms.E(); m.n_u = 3 * m.E + 3 * m.F; m.n_eta = 3 * m.F; m.n = m.n_u + m.n_eta;
+    std::vector<int32_t> ce(3 * m.F);
+    for (int64_t c = 0; c < m.F; ++c)
+      for (int i = 0; i < 3; ++i) ce[i * m.F + c] = ms.cell_edges[3 * c + i];
+    bool ok = upload(&m.cell_edges, ce) == cudaSuccess && upload(&m.cell_aligned, ms.cell_aligned) == cudaSuccess &&
+              upload(&m.edge_plus, ms.edge_plus) == cudaSuccess && upload(&m.edge_minus, ms.edge_minus) == cudaSuccess &&
+              upload(&m.edge_lpos, ms.edge_lpos) == cudaSuccess && upload(&m.M1, hc.M1) == cudaSuccess &&
+              upload(&m.C, hc.C) == cudaSuccess && upload(&m.det, hc.det) == cudaSuccess &&
+              upload(&m.G, hc.G) == cudaSuccess && upload(&m.dinv, hc.dinv) == cudaSuccess &&
+              dalloc(&m.topo, m.n_eta) == cudaSuccess;
+    if (!ok) { rc = set_err(ctx, PAVG_ERR_NOMEM, "device upload failed"); throw 0; }
+    cudaMemset(m.topo, 0, sizeof(double) * m.n_eta);
+    CgWork& w = ctx->cg;
+    if (cg_configure(m.F, &w) != cudaSuccess) { rc = set_err(ctx, PAVG_ERR_CUDA, "CG configuration failed"); throw 0; }
+    ok = dalloc(&w.x, m.n_u) == cudaSuccess && dalloc(&w.r[0], m.n_u) == cudaSuccess &&
+         dalloc(&w.r[1], m.n_u) == cudaSuccess && dalloc(&w.s[0], m.n_u) == cudaSuccess &&
+         dalloc(&w.s[1], m.n_u) == cudaSuccess && dalloc(&w.w[0], m.n_u) == cudaSuccess &&
+         dalloc(&w.w[1], m.n_u) == cudaSuccess && dalloc(&w.w[2], m.n_u) == cudaSuccess &&
+         dalloc(&w.p, m.n_u) == cudaSuccess && dalloc(&w.partial, 6 * (size_t)w.nblocks) == cudaSuccess &&
+         dalloc(&w.bar, 2) == cudaSuccess && dalloc(&w.flags, 1) == cudaSuccess && dalloc(&w.stats, 3) == cudaSuccess &&
+         dalloc(&ctx->ru, m.n_u) == cudaSuccess && dalloc(&ctx->io_in, m.n) == cudaSuccess &&
+         dalloc(&ctx->io_out, m.n) == cudaSuccess && dalloc(&ctx->dpart, 4096) == cudaSuccess &&
+         cudaMallocHost((void**)&ctx->host_part, sizeof(double) * 4096) == cudaSuccess;
+    for (auto*& v : ctx->vec) ok = ok && dalloc(&v, m.n) == cudaSuccess;
+    if (!ok) { rc = set_err(ctx, PAVG_ERR_NOMEM, "workspace allocation failed"); throw 0; }
+    cudaMemset(w.bar, 0, 2 * sizeof(unsigned));
+    cudaMemset(w.flags, 0, sizeof(int));
+    cudaMemset(w.stats, 0, 3 * sizeof(unsigned long long));
+    if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      rc = set_err(ctx, PAVG_ERR_CUDA, "stream creation failed");
+      throw 0;
+    }
+    if (p->lambda_max > 0) {
+      ctx->lam = p->lambda_max;
+    } else {
+      rc = estimate_lambda(ctx);
+      if (rc) throw 0;
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) { rc = set_err(ctx, PAVG_ERR_CUDA, "setup failed"); throw 0; }
+    rc = check_flags(ctx);
+    if (rc) throw 0;
+  } catch (const std::exception& e) {
+    std::fprintf(stderr, "pavg_create: %s\n", e.what());
+    free_ctx(ctx);
+    return PAVG_ERR_INVAL;
+  } catch (int) {
+    std::fprintf(stderr, "pavg_create: %s\n", ctx->err.c_str());
+    free_ctx(ctx);
+    return rc ? rc : PAVG_ERR_CUDA;
+  }
+  *out = ctx;
+  return PAVG_OK;
+}
+
+int pavg_destroy(pavg_ctx* ctx) {
+  if (!ctx) return PAVG_ERR_INVAL;
+  cudaDeviceSynchronize();
+  free_ctx(ctx);
+  return PAVG_OK;
+}
+
+int pavg_sizes(const pavg_ctx* ctx, int64_t* n_u, int64_t* n_eta, int64_t* n_cells, int64_t* n_edges,
+               int64_t* n_verts) {
+  if (!ctx) return PAVG_ERR_INVAL;
+  if (n_u) *n_u = ctx->dm.n_u;
+  if (n_eta) *n_eta = ctx->dm.n_eta;
+  if (n_cells) *n_cells = ctx->dm.F;
+  if (n_edges) *n_edges = ctx->dm.E;
+  if (n_verts) *n_verts = ctx->mesh.V();
+  return PAVG_OK;
+}
+
+int pavg_mesh_export(const pavg_ctx* ctx, double* vert_xyz, int32_t* cell_verts) {
+  if (!ctx) return PAVG_ERR_INVAL;
+  if (vert_xyz) std::memcpy(vert_xyz, ctx->mesh.verts.data(), sizeof(double) * ctx->mesh.verts.size());
+  if (cell_verts) std::memcpy(cell_verts, ctx->mesh.cells.data(), sizeof(int32_t) * ctx->mesh.cells.size());
+  return PAVG_OK;
+}
+
+int pavg_set_topography(pavg_ctx* ctx, const double* b) {
+  if (!ctx || !b) return PAVG_ERR_INVAL;
+  CK(cudaMemcpy(ctx->dm.topo, b, sizeof(double) * ctx->dm.n_eta, cudaMemcpyDeviceToDevice));
+  return PAVG_OK;
+}
+
+int pavg_lambda_max(const pavg_ctx* ctx, double* out) {
+  if (!ctx || !out) return PAVG_ERR_INVAL;
+  *out = ctx->lam;
+  return PAVG_OK;
+}
+
+int pavg_linear(pavg_ctx* ctx, const double* U, double* LU, int B, void* stream) {
+  if (!ctx || !U || !LU || B < 0) return PAVG_ERR_INVAL;
+  const int64_t n = ctx->dm.n;
+  for (int b = 0; b < B; ++b) {
+    int rc = enq_linear(ctx, U + b * n, LU + b * n, S(stream));
+    if (rc) return rc;
+  }
+  return PAVG_OK;
+}
+
+int pavg_nonlinear(pavg_ctx* ctx, const double* U, double* NU, int B, void* stream) {
+  if (!ctx || !U || !NU || B < 0) return PAVG_ERR_INVAL;
+  const int64_t n = ctx->dm.n;
+  for (int b = 0; b < B; ++b) {
+    int rc = enq_nonlinear(ctx, U + b * n, NU + b * n, ctx->vec[5], S(stream));
+    if (rc) return rc;
+  }
+  return PAVG_OK;
+}
+
+int pavg_expL_apply(pavg_ctx* ctx, double t, const double* U, double* out, int B, void* stream) {
+  if (!ctx || !U || !out || B < 0 || !std::isfinite(t)) return PAVG_ERR_INVAL;
+  const int64_t n = ctx->dm.n;
+  for (int b = 0; b < B; ++b) {
+    int rc = enq_expL(ctx, t, U + b * n, out + b * n, S(stream));
+    if (rc) return rc;
+  }
+  return PAVG_OK;
+}
+
+int pavg_averaged_rhs(pavg_ctx* ctx, double T, int M, const double* U, double* out, void* stream) {
+  if (!ctx || !U || !out || M < 1 || !(T >= 0) || !std::isfinite(T)) return PAVG_ERR_INVAL;
+  return run_avg(ctx, T, M, U, out, S(stream));
+}
+
+int pavg_averaged_rhs_literal(pavg_ctx* ctx, double T, int M, const double* U, double* out, void* stream) {
+  if (!ctx || !U || !out || M < 1 || !(T >= 0) || !std::isfinite(T)) return PAVG_ERR_INVAL;
+  cudaStream_t st = S(stream);
+  const int64_t n = ctx->dm.n;
+  if (T == 0.0) return enq_nonlinear(ctx, U, out, ctx->vec[5], st);
+  std::vector<double> s, w;
+  int rc = shifts_weights(T, M, ctx->p.quad_rule, &s, &w);
+  if (rc) return set_err(ctx, rc, "invalid T / M / quadrature rule");
+  double* acc = ctx->io_out;
+  double* V = ctx->io_in;
+  double* term = ctx->vec[4];
+  CK(cudaMemsetAsync(acc, 0, sizeof(double) * n, st));
+  for (int m = 0; m < M; ++m) {
+    if (w[m] == 0.0) continue;
+    rc = enq_expL(ctx, s[m], U, V, st);
+    if (rc) return rc;
+    rc = enq_nonlinear(ctx, V, term, ctx->vec[5], st);
+    if (rc) return rc;
+    rc = enq_expL(ctx, -s[m], term, V, st);
+    if (rc) return rc;
+    CK(launch_lincomb(acc, 1.0, acc, w[m], V, 0.0, nullptr, n, st));
+  }
+  CK(cudaMemcpyAsync(out, acc, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  return PAVG_OK;
+}
+
+// Sec. 2.3 (Eqs. stage1_c to stage4), with E(t) = e^{tL} and N-bar the average:
+//   k1 = N-bar(U);  U1 = U + dt/2 k1;  k2 = N-bar(E(dt/2) U1);  U2 = E(dt/2) U + dt/2 k2
+//   k3 = N-bar(U2); U3 = E(dt/2) U + dt k3;  k4 = N-bar(E(dt/2) U3)
+//   U+ = E(dt) U + dt/6 [E(dt) k1 + 2 E(dt/2) k2 + 2 E(dt/2) k3 + k4]
+// evaluated as E(dt)(U + dt/6 k1) + dt/6 [2 E(dt/2)(k2 + k3) + k4] (E is linear).
+int pavg_timestep(pavg_ctx* ctx, double dt, double T, int M, double* U, int nsteps, void* stream) {
+  if (!ctx || !U || M < 1 || nsteps < 0 || !(T >= 0) || !std::isfinite(dt)) return PAVG_ERR_INVAL;
+  cudaStream_t st = S(stream);
+  const int64_t n = ctx->dm.n;
+  AvgPlan* pl = nullptr;
+  int rc = get_plan(ctx, T, M, &pl);
+  if (rc) return rc;
+  rc = ensure_avg_workspace(ctx, pl->K, M);
+  if (rc) return rc;
+  // stage vectors live in the Rm workspace when it is large enough, else extra buffers
+  static_assert(sizeof(double) == 8, "");
+  double *k1, *k2, *k3, *k4, *EhU, *tmp, *tmp2;
+  std::vector<double*> own;
+  auto getbuf = [&](double** p) -> bool {
+    double* b = nullptr;
+    if (cudaMalloc((void**)&b, sizeof(double) * n) != cudaSuccess) return false;
+    own.push_back(b);
+    *p = b;
+    return true;
+  };
+  if (!(getbuf(&k1) && getbuf(&k2) && getbuf(&k3) && getbuf(&k4) && getbuf(&EhU) && getbuf(&tmp) && getbuf(&tmp2))) {
+    for (auto* b : own) cudaFree(b);
+    return set_err(ctx, PAVG_ERR_NOMEM, "timestep buffers");
+  }
+  auto fin = [&](int code) { cudaStreamSynchronize(st); for (auto* b : own) cudaFree(b); return code; };
+  for (int step = 0; step < nsteps; ++step) {
+    if ((rc = run_avg(ctx, T, M, U, k1, st))) return fin(rc);
+    if ((rc = enq_expL(ctx, 0.5 * dt, U, EhU, st))) return fin(rc);
+    if (launch_lincomb(tmp, 1.0, U, 0.5 * dt, k1, 0, nullptr, n, st) != cudaSuccess) return fin(PAVG_ERR_CUDA);
+    if ((rc = enq_expL(ctx, 0.5 * dt, tmp, tmp2, st))) return fin(rc);
+    if ((rc = run_avg(ctx, T, M, tmp2, k2, st))) return fin(rc);
+    if (launch_lincomb(tmp, 1.0, EhU, 0.5 * dt, k2, 0, nullptr, n, st) != cudaSuccess) return fin(PAVG_ERR_CUDA);
+    if ((rc = run_avg(ctx, T, M, tmp, k3, st))) return fin(rc);
+    if (launch_lincomb(tmp, 1.0, EhU, dt, k3, 0, nullptr, n, st) != cudaSuccess) return fin(PAVG_ERR_CUDA);
+    if ((rc = enq_expL(ctx, 0.5 * dt, tmp, tmp2, st))) return fin(rc);
+    if ((rc = run_avg(ctx, T, M, tmp2, k4, st))) return fin(rc);
+    // U+ = E(dt)(U + dt/6 k1) + dt/6 [2 E(dt/2)(k2 + k3) + k4]
+    if (launch_lincomb(tmp, 1.0, k2, 1.0, k3, 0, nullptr, n, st) != cudaSuccess) return fin(PAVG_ERR_CUDA);
+    if ((rc = enq_expL(ctx, 0.5 * dt, tmp, tmp2, st))) return fin(rc);
+    if (launch_lincomb(tmp, 1.0, U, dt / 6.0, k1, 0, nullptr, n, st) != cudaSuccess) return fin(PAVG_ERR_CUDA);
+    if ((rc = enq_expL(ctx, dt, tmp, EhU, st))) return fin(rc);
+    if (launch_lincomb(U, 1.0, EhU, dt / 3.0, tmp2, dt / 6.0, k4, n, st) != cudaSuccess) return fin(PAVG_ERR_CUDA);
+  }
+  return fin(PAVG_OK);
+}
+
+int pavg_sync(pavg_ctx* ctx, void* stream) {
+  if (!ctx) return PAVG_ERR_INVAL;
+  CK(cudaStreamSynchronize(S(stream)));
+  return check_flags(ctx);
+}
+
+int pavg_get_stats(pavg_ctx* ctx, pavg_stats* out) {
+  if (!ctx || !out) return PAVG_ERR_INVAL;
+  CK(cudaDeviceSynchronize());
+  unsigned long long st[3];
+  int f = 0;
+  CK(cudaMemcpy(st, ctx->cg.stats, sizeof(st), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&f, ctx->cg.flags, sizeof(int), cudaMemcpyDeviceToHost));
+  out->lambda_max = ctx->lam;
+  out->last_degree = ctx->last_degree;
+  out->cg_solves = (int)st[0];
+  out->cg_iters_max = (int)st[2];
+  out->cg_iters_mean = st[0] ? (double)st[1] / (double)st[0] : 0.0;
+  out->error_flags = f;
+  return PAVG_OK;
+}
+
+int pavg_reset_stats(pavg_ctx* ctx) {
+  if (!ctx) return PAVG_ERR_INVAL;
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemset(ctx->cg.stats, 0, 3 * sizeof(unsigned long long)));
+  CK(cudaMemset(ctx->cg.flags, 0, sizeof(int)));
+  return PAVG_OK;
+}
+
+const char* pavg_last_error(const pavg_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,741 @@
+// CUDA kernels of libpavg for sm_103a (FP64 path).
+//
+// Layout: per-cell data in structure-of-arrays form ([k][F]) so that a warp of
+// consecutive cells reads consecutive addresses; element matrices carry the
+// orientation signs, so gathered global DOF values are used as they are.
+// Assembly of edge DOFs (shared by exactly two cells) uses atomicAdd into a
+// zeroed buffer: with exactly two contributions, 0 + a + b == 0 + b + a in IEEE
+// arithmetic, so the result does not depend on the order of arrival.
+#include <cuda_runtime.h>
+
+#include "device.h"
+
+namespace pavg {
+
+__constant__ ConstTables c_tab;
+
+cudaError_t upload_tables(const ConstTables& t) { return cudaMemcpyToSymbol(c_tab, &t, sizeof(t)); }
+
+namespace {
+
+constexpr long long kBarrierTimeoutCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+__host__ __device__ constexpr int psym(int i, int j) { return i * 12 - i * (i - 1) / 2 + (j - i); }
+__host__ __device__ constexpr int pasym(int i, int j) { return i * 11 - i * (i - 1) / 2 + (j - i - 1); }
+
+// Global DOF indices and orientation signs of the 12 velocity DOFs of cell c.
+__device__ __forceinline__ unsigned cell_dofs(const DeviceMesh& m, int64_t c, int dof[12], double sg[12]) {
+  unsigned al = m.cell_aligned[c];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    int e = m.cell_edges[i * m.F + c];
+    bool a = (al >> i) & 1u;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      dof[3 * i + j] = 3 * e + j;
+      sg[3 * i + j] = (a || j == 1) ? 1.0 : -1.0;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    dof[9 + j] = (int)(3 * m.E + 3 * c + j);
+    sg[9 + j] = 1.0;
+  }
+  return al;
+}
+
+// w = A_K u for the cell's packed symmetric 12x12 element matrix.
+__device__ __forceinline__ void spmv_cell(const double* __restrict__ M1, int64_t F, int64_t c,
+                                          const double u[12], double w[12]) {
+#pragma unroll
+  for (int i = 0; i < 12; ++i) w[i] = 0.0;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+#pragma unroll
+    for (int j = i; j < 12; ++j) {
+      double a = __ldg(&M1[psym(i, j) * F + c]);
+      w[i] = fma(a, u[j], w[i]);
+      if (j != i) w[j] = fma(a, u[i], w[j]);
+    }
+  }
+}
+
+template <int THREADS>
+__device__ __forceinline__ void block_sum3(double a, double b, double c, double out[3]) {
+  __shared__ double sh[3][THREADS / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+    c += __shfl_down_sync(0xffffffffu, c, o);
+  }
+  if (lane == 0) { sh[0][warp] = a; sh[1][warp] = b; sh[2][warp] = c; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int k = 0; k < THREADS / 32; ++k) { s0 += sh[0][k]; s1 += sh[1][k]; s2 += sh[2][k]; }
+    out[0] = s0; out[1] = s1; out[2] = s2;
+  }
+  __syncthreads();
+}
+
+// Sense-reversing grid barrier with a bounded wait.  Returns false (and latches
+// kFlagTimeout) when the wait gives up or another block already timed out.
+__device__ bool grid_barrier(unsigned* bar, int* flags) {
+  __shared__ int s_ok;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    unsigned gen = *vgen;
+    __threadfence();
+    unsigned arrived = atomicAdd(bar, 1u);
+    int ok = 1;
+    if (arrived == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long t0 = clock64();
+      while (*vgen == gen) {
+        if (clock64() - t0 > kBarrierTimeoutCycles) {
+          atomicOr(flags, kFlagTimeout);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    if (*((volatile int*)flags) & kFlagTimeout) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Deterministic sum of the per-block partials [3][nb] by every block.
+template <int THREADS>
+__device__ __forceinline__ void reduce_partials(const double* part, int nb, double out[3]) {
+  double a = 0, b = 0, c = 0;
+  for (int k = threadIdx.x; k < nb; k += THREADS) {
+    a += __ldcg(&part[k]);
+    b += __ldcg(&part[nb + k]);
+    c += __ldcg(&part[2 * nb + k]);
+  }
+  block_sum3<THREADS>(a, b, c, out);
+}
+
+constexpr int kCgThreads = 256;
+
+// Persistent conjugate gradients on M1 (Jacobi preconditioner), in the
+// single-reduction form of Chronopoulos and Gear: one grid barrier per
+// iteration.  M1 is applied cell by cell from the element matrices; the
+// inner products use u^T A u = sum_K u_K^T A_K u_K, so no assembled product is
+// needed before the reduction.  Every DOF has one owner cell (interior DOFs:
+// their cell; edge DOFs: the cell that runs the edge low -> high), which alone
+// writes its per-DOF vectors; shared values are recomputed identically by both
+// cells from double-buffered inputs.
+__global__ void __launch_bounds__(kCgThreads) k_cg(DeviceMesh m, CgWork w, CgParams cp,
+                                                   const double* __restrict__ b, double* out,
+                                                   double scale_x, const double* __restrict__ add) {
+  __shared__ double sc[3];
+  const int64_t F = m.F;
+  const int64_t nE = 3 * m.E;
+  const int nb = gridDim.x;
+  const int64_t g0 = (int64_t)blockIdx.x * kCgThreads + threadIdx.x;
+  const int64_t gs = (int64_t)nb * kCgThreads;
+  double pg = 0, pd = 0, pr = 0;
+
+  // ---- initial residual r0 = b (x0 = 0), u0 = P r0, w0 = A u0 into w[0]
+  for (int64_t c = g0; c < F; c += gs) {
+    int dof[12];
+    double sg[12];
+    unsigned al = cell_dofs(m, c, dof, sg);
+    double u[12], wl[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) u[k] = __ldg(&m.dinv[dof[k]]) * __ldg(&b[dof[k]]);
+    spmv_cell(m.M1, F, c, u, wl);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      pd = fma(u[k], wl[k], pd);
+      if (k < 9) atomicAdd(&w.w[0][dof[k]], wl[k]);
+      else w.w[0][dof[k]] = wl[k];
+      bool own = k >= 9 || ((al >> (k / 3)) & 1u);
+      if (own) {
+        double r0 = __ldg(&b[dof[k]]);
+        w.r[0][dof[k]] = r0;
+        pg = fma(r0, u[k], pg);
+        pr = fma(r0, r0, pr);
+        if (k < 9) w.w[1][dof[k]] = 0.0;
+      }
+    }
+  }
+  // The partials are double-buffered: a block may write the next round's
+  // partial before a slower block has finished reading this round's.
+  {
+    double s3[3];
+    block_sum3<kCgThreads>(pg, pd, pr, s3);
+    if (threadIdx.x == 0) {
+      w.partial[blockIdx.x] = s3[0];
+      w.partial[nb + blockIdx.x] = s3[1];
+      w.partial[2 * nb + blockIdx.x] = s3[2];
+    }
+  }
+  bool alive = grid_barrier(w.bar, w.flags);
+  {
+    double t[3];
+    reduce_partials<kCgThreads>(w.partial, nb, t);
+    if (threadIdx.x == 0) { sc[0] = t[0]; sc[1] = t[1]; sc[2] = t[2]; }
+    __syncthreads();
+  }
+  double gamma = sc[0], delta = sc[1];
+  const double bb = sc[2];
+  const double tol2 = cp.rtol * cp.rtol * bb;
+  double alpha = gamma / delta, beta = 0.0;
+  int it = 0;
+  bool done = !(bb > 0.0);
+  bool have_x = false;
+  if (!done && !(isfinite(alpha))) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(w.flags, kFlagNonFinite);
+    done = true;
+  }
+  for (; alive && !done && it < cp.maxit; ++it) {
+    const int i = it;
+    const double* rin = (i & 1) ? w.r[1] : w.r[0];
+    double* rout = (i & 1) ? w.r[0] : w.r[1];
+    const double* sin_ = (i & 1) ? w.s[0] : w.s[1];
+    double* sout = (i & 1) ? w.s[1] : w.s[0];
+    const int i3 = i % 3;
+    const double* win = i3 == 0 ? w.w[0] : (i3 == 1 ? w.w[1] : w.w[2]);
+    double* wacc = i3 == 0 ? w.w[1] : (i3 == 1 ? w.w[2] : w.w[0]);
+    double* wzero = i3 == 0 ? w.w[2] : (i3 == 1 ? w.w[0] : w.w[1]);
+    pg = pd = pr = 0.0;
+    for (int64_t c = g0; c < F; c += gs) {
+      int dof[12];
+      double sg[12];
+      unsigned al = cell_dofs(m, c, dof, sg);
+      double u[12], wl[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const int d = dof[k];
+        const double rold = __ldcg(&rin[d]);
+        const double winv = __ldcg(&win[d]);
+        const double s_i = i > 0 ? fma(beta, __ldcg(&sin_[d]), winv) : winv;
+        const double rn = fma(-alpha, s_i, rold);
+        const double dv = __ldg(&m.dinv[d]);
+        u[k] = dv * rn;
+        const bool own = k >= 9 || ((al >> (k / 3)) & 1u);
+        if (own) {
+          sout[d] = s_i;
+          rout[d] = rn;
+          const double ui = dv * rold;
+          const double pv = i > 0 ? fma(beta, __ldcg(&w.p[d]), ui) : ui;
+          w.p[d] = pv;
+          w.x[d] = i > 0 ? fma(alpha, pv, __ldcg(&w.x[d])) : alpha * pv;
+          if (k < 9) wzero[d] = 0.0;
+          pg = fma(rn, u[k], pg);
+          pr = fma(rn, rn, pr);
+        }
+      }
+      spmv_cell(m.M1, F, c, u, wl);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        pd = fma(u[k], wl[k], pd);
+        if (k < 9) atomicAdd(&wacc[dof[k]], wl[k]);
+        else wacc[dof[k]] = wl[k];
+      }
+    }
+    have_x = true;
+    double s3[3];
+    double* part = w.partial + ((i + 1) & 1) * 3 * nb;
+    block_sum3<kCgThreads>(pg, pd, pr, s3);
+    if (threadIdx.x == 0) {
+      part[blockIdx.x] = s3[0];
+      part[nb + blockIdx.x] = s3[1];
+      part[2 * nb + blockIdx.x] = s3[2];
+    }
+    alive = grid_barrier(w.bar, w.flags);
+    double t[3];
+    reduce_partials<kCgThreads>(part, nb, t);
+    if (threadIdx.x == 0) { sc[0] = t[0]; sc[1] = t[1]; sc[2] = t[2]; }
+    __syncthreads();
+    const double gnew = sc[0], dnew = sc[1], rr = sc[2];
+    if (!(isfinite(gnew) && isfinite(dnew) && isfinite(rr))) {
+      if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(w.flags, kFlagNonFinite);
+      ++it;
+      break;
+    }
+    if (rr <= tol2) { ++it; done = true; break; }
+    double bnew = gnew / gamma;
+    alpha = gnew / (dnew - bnew * gnew / alpha);
+    beta = bnew;
+    gamma = gnew;
+  }
+  if (alive && !done && it >= cp.maxit && threadIdx.x == 0 && blockIdx.x == 0) atomicOr(w.flags, kFlagNoConv);
+  // ---- out = scale_x x + add on owned DOFs
+  for (int64_t c = g0; c < F; c += gs) {
+    int dof[12];
+    double sg[12];
+    unsigned al = cell_dofs(m, c, dof, sg);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      bool own = k >= 9 || ((al >> (k / 3)) & 1u);
+      if (!own) continue;
+      const int d = dof[k];
+      double xv = have_x ? __ldcg(&w.x[d]) : 0.0;
+      double v = scale_x * xv;
+      if (add) v += __ldg(&add[d]);
+      out[d] = v;
+    }
+  }
+  (void)nE;
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    atomicAdd(&w.stats[0], 1ull);
+    atomicAdd(&w.stats[1], (unsigned long long)it);
+    atomicMax(&w.stats[2], (unsigned long long)it);
+  }
+}
+
+// ru = y_u + s (-C u + g D^T eta);  eta_out = M2^{-1}(y_eta + s (-H D u)) + z_eta.
+__global__ void __launch_bounds__(128) k_apply_K(DeviceMesh m, const double* __restrict__ U, double s,
+                                                 double g, double H, const double* __restrict__ y_u,
+                                                 const double* __restrict__ y_eta,
+                                                 const double* __restrict__ z_eta, double* ru,
+                                                 double* eta_out) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m.F) return;
+  const int64_t F = m.F;
+  int dof[12];
+  double sg[12];
+  unsigned al = cell_dofs(m, c, dof, sg);
+  double u[12], r[12], eta[3];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) { u[k] = __ldg(&U[dof[k]]); r[k] = 0.0; }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) eta[k] = __ldg(&U[m.n_u + 3 * c + k]);
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+#pragma unroll
+    for (int j = i + 1; j < 12; ++j) {
+      double a = __ldg(&m.C[pasym(i, j) * F + c]);
+      r[i] = fma(-a, u[j], r[i]);
+      r[j] = fma(a, u[i], r[j]);
+    }
+  }
+  double Du[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double t = 0.0;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) t = fma(c_tab.D[k][i] * sg[i], u[i], t);
+    Du[k] = t;
+  }
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) t = fma(c_tab.D[k][i], eta[k], t);
+    double v = s * fma(g * sg[i], t, r[i]);
+    bool own = i >= 9 || ((al >> (i / 3)) & 1u);
+    if (own && y_u) v += __ldg(&y_u[dof[i]]);
+    if (i < 9) atomicAdd(&ru[dof[i]], v);
+    else ru[dof[i]] = v;
+  }
+  const double idet = 1.0 / m.det[c];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double v = 0.0;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      double rl = s * (-H * Du[l]);
+      if (y_eta) rl += __ldg(&y_eta[3 * c + l]);
+      v = fma(c_tab.M2inv_ref[k][l], rl, v);
+    }
+    v *= idet;
+    if (z_eta) v += __ldg(&z_eta[3 * c + k]);
+    eta_out[3 * c + k] = v;
+  }
+}
+
+// ------------------------------------------------------------------ nonlinear operator
+struct Side {
+  double c[12];   // signed local coefficients
+  double h[3];    // eta - b at the local vertices
+  double det, G00, G01, G11;
+};
+
+__device__ __forceinline__ void load_side(const DeviceMesh& m, const double* __restrict__ U, int64_t cell,
+                                          Side& S) {
+  int dof[12];
+  double sg[12];
+  cell_dofs(m, cell, dof, sg);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) S.c[k] = sg[k] * __ldg(&U[dof[k]]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) S.h[k] = __ldg(&U[m.n_u + 3 * cell + k]) - __ldg(&m.topo[3 * cell + k]);
+  S.det = __ldg(&m.det[cell]);
+  S.G00 = __ldg(&m.G[cell]);
+  S.G01 = __ldg(&m.G[m.F + cell]);
+  S.G11 = __ldg(&m.G[2 * m.F + cell]);
+}
+
+struct FacetValues {
+  double flux;     // u+ . n+ ds / dtau
+  double tan;      // |e| (t . u~)
+  double hup;      // (eta - b)~
+  double up0, up1, um0, um1;
+};
+
+// Values shared by the two cells of a facet at point p, evaluated with
+// explicitly rounded operations so that both cells obtain identical bits.
+// Upwind: the side the flow leaves (flux > 0: plus); the printed rule of
+// Sec. 2.5 (u~ = u+ when u . n+ < 0) is the alternative for the velocity.
+__device__ __forceinline__ FacetValues facet_point(const Side& P, int lp, const Side& Mn, int lm, int p,
+                                                   int upwind) {
+  FacetValues f;
+  double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0, hp = 0.0, hm = 0.0;
+#pragma unroll
+  for (int j = 0; j < 12; ++j) {
+    a0 = __fma_rn(P.c[j], c_tab.fq_psi[0][lp][p][j][0], a0);
+    a1 = __fma_rn(P.c[j], c_tab.fq_psi[0][lp][p][j][1], a1);
+    b0 = __fma_rn(Mn.c[j], c_tab.fq_psi[1][lm][p][j][0], b0);
+    b1 = __fma_rn(Mn.c[j], c_tab.fq_psi[1][lm][p][j][1], b1);
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    hp = __fma_rn(P.h[k], c_tab.fq_phi[0][lp][p][k], hp);
+    hm = __fma_rn(Mn.h[k], c_tab.fq_phi[1][lm][p][k], hm);
+  }
+  const double dp0 = c_tab.edge_dir[lp][0], dp1 = c_tab.edge_dir[lp][1];
+  const double dm0 = c_tab.edge_dir[lm][0], dm1 = c_tab.edge_dir[lm][1];
+  const double flux = __dsub_rn(__dmul_rn(a0, dp1), __dmul_rn(a1, dp0));
+  const bool plus_up = flux > 0.0;
+  const bool plus_up_vel = upwind == PAVG_UPWIND_STANDARD ? plus_up : (flux < 0.0);
+  double tan;
+  if (plus_up_vel) {
+    double g0 = __fma_rn(P.G00, a0, __dmul_rn(P.G01, a1));
+    double g1 = __fma_rn(P.G01, a0, __dmul_rn(P.G11, a1));
+    tan = __ddiv_rn(__fma_rn(dp0, g0, __dmul_rn(dp1, g1)), P.det);
+  } else {
+    double g0 = __fma_rn(Mn.G00, b0, __dmul_rn(Mn.G01, b1));
+    double g1 = __fma_rn(Mn.G01, b0, __dmul_rn(Mn.G11, b1));
+    tan = -__ddiv_rn(__fma_rn(dm0, g0, __dmul_rn(dm1, g1)), Mn.det);
+  }
+  f.flux = flux;
+  f.tan = tan;
+  f.hup = plus_up ? hp : hm;
+  f.up0 = a0; f.up1 = a1; f.um0 = b0; f.um1 = b1;
+  return f;
+}
+
+// Weak-form right-hand side of N (Sec. 2.5) for one cell and one state:
+//   r_i  = int_K [u . grad_perp(u_perp . w_i) + div w_i |u|^2/2]
+//          - int_dK (+/-) (u_perp . w_i) (t . u~)          (velocity test w_i)
+//   re_k = int_K grad phi_k . u (eta - b) -/+ int_dK phi_k (u . n+) (eta - b)~
+// The cell integrand in reference form is, with v = G u_hat and the
+// derivative d_tau = v1 d/dx - v0 d/dy:
+//   [d_tau cross2(u_hat, psi_i) + div psi_i (u_hat . v) / 2] / det^2.
+__global__ void __launch_bounds__(128) k_nonlinear(DeviceMesh m, const double* __restrict__ Uall,
+                                                   double* Rall, int upwind) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m.F) return;
+  const int64_t n = m.n;
+  const double* U = Uall + (int64_t)blockIdx.y * n;
+  double* R = Rall + (int64_t)blockIdx.y * n;
+  Side own;
+  load_side(m, U, c, own);
+  double r[12], re[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int i = 0; i < 12; ++i) r[i] = 0.0;
+  // ---- cell terms
+#pragma unroll 1
+  for (int q = 0; q < kCellQ; ++q) {
+    double u0 = 0, u1 = 0, d00 = 0, d01 = 0, d10 = 0, d11 = 0;  // d_ca = d u_c / d x_a
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+      const double cj = own.c[j];
+      u0 = fma(cj, c_tab.cq_psi[q][j][0], u0);
+      u1 = fma(cj, c_tab.cq_psi[q][j][1], u1);
+      d00 = fma(cj, c_tab.cq_dpsi[q][j][0][0], d00);
+      d01 = fma(cj, c_tab.cq_dpsi[q][j][0][1], d01);
+      d10 = fma(cj, c_tab.cq_dpsi[q][j][1][0], d10);
+      d11 = fma(cj, c_tab.cq_dpsi[q][j][1][1], d11);
+    }
+    const double h = own.h[0] * c_tab.cq_phi[q][0] + own.h[1] * c_tab.cq_phi[q][1] + own.h[2] * c_tab.cq_phi[q][2];
+    const double v0 = own.G00 * u0 + own.G01 * u1;
+    const double v1 = own.G01 * u0 + own.G11 * u1;
+    const double wq = c_tab.cq_w[q];
+    const double half_ke = 0.5 * (u0 * v0 + u1 * v1);
+    const double t0 = v1 * d00 - v0 * d01;  // d_tau u_hat
+    const double t1 = v1 * d10 - v0 * d11;
+    // coefficients of psi_i0, psi_i1, d0 psi_i0, d1 psi_i0, d0 psi_i1, d1 psi_i1
+    const double k0 = -t1 * wq, k1 = t0 * wq;
+    const double k2 = (-u1 * v1 + half_ke) * wq, k3 = (u1 * v0) * wq;
+    const double k4 = (u0 * v1) * wq, k5 = (-u0 * v0 + half_ke) * wq;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+      double t = k0 * c_tab.cq_psi[q][i][0];
+      t = fma(k1, c_tab.cq_psi[q][i][1], t);
+      t = fma(k2, c_tab.cq_dpsi[q][i][0][0], t);
+      t = fma(k3, c_tab.cq_dpsi[q][i][0][1], t);
+      t = fma(k4, c_tab.cq_dpsi[q][i][1][0], t);
+      t = fma(k5, c_tab.cq_dpsi[q][i][1][1], t);
+      r[i] += t;
+    }
+    const double hw = h * wq;
+    re[0] -= (u0 + u1) * hw;
+    re[1] += u0 * hw;
+    re[2] += u1 * hw;
+  }
+  const double idet2 = 1.0 / (own.det * own.det);
+#pragma unroll
+  for (int i = 0; i < 12; ++i) r[i] *= idet2;
+  // ---- facet terms
+  const unsigned al = m.cell_aligned[c];
+#pragma unroll 1
+  for (int i = 0; i < 3; ++i) {
+    const int e = m.cell_edges[i * m.F + c];
+    const bool plus = (al >> i) & 1u;
+    const unsigned lpos = m.edge_lpos[e];
+    const int64_t nbr = plus ? m.edge_minus[e] : m.edge_plus[e];
+    const int nloc = plus ? (int)(lpos >> 2) : (int)(lpos & 3u);
+    Side nb;
+    load_side(m, U, nbr, nb);
+#pragma unroll 1
+    for (int p = 0; p < kFacetQ; ++p) {
+      const double wp = c_tab.fq_w[p];
+      if (plus) {
+        FacetValues f = facet_point(own, i, nb, nloc, p, upwind);
+        const double sc = -wp * f.tan / own.det;
+#pragma unroll
+        for (int j = 0; j < 12; ++j) {
+          double q = f.up0 * c_tab.fq_psi[0][i][p][j][1] - f.up1 * c_tab.fq_psi[0][i][p][j][0];
+          r[j] = fma(sc, q, r[j]);
+        }
+        const double fh = -wp * f.flux * f.hup;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) re[k] = fma(fh, c_tab.fq_phi[0][i][p][k], re[k]);
+      } else {
+        FacetValues f = facet_point(nb, nloc, own, i, p, upwind);
+        const double sc = wp * f.tan / own.det;
+#pragma unroll
+        for (int j = 0; j < 12; ++j) {
+          double q = f.um0 * c_tab.fq_psi[1][i][p][j][1] - f.um1 * c_tab.fq_psi[1][i][p][j][0];
+          r[j] = fma(sc, q, r[j]);
+        }
+        const double fh = wp * f.flux * f.hup;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) re[k] = fma(fh, c_tab.fq_phi[1][i][p][k], re[k]);
+      }
+    }
+  }
+  // ---- to global numbering
+  int dof[12];
+  double sg[12];
+  cell_dofs(m, c, dof, sg);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    double v = sg[k] * r[k];
+    if (k < 9) atomicAdd(&R[dof[k]], v);
+    else R[dof[k]] = v;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) R[m.n_u + 3 * c + k] = re[k];
+}
+
+__global__ void k_m2inv(DeviceMesh m, const double* __restrict__ r, int64_t rstride, double* out,
+                        int64_t ostride) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m.F) return;
+  const double* rb = r + blockIdx.y * rstride;
+  double* ob = out + blockIdx.y * ostride;
+  const double idet = 1.0 / m.det[c];
+  double v[3];
+#pragma unroll
+  for (int l = 0; l < 3; ++l) v[l] = rb[3 * c + l];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double t = 0.0;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) t = fma(c_tab.M2inv_ref[k][l], v[l], t);
+    ob[3 * c + k] = t * idet;
+  }
+}
+
+// out[m][j] = sum_k A[m][k] in[k][j]; MT output rows per block row.
+template <int MT>
+__global__ void __launch_bounds__(256) k_combine(const double* __restrict__ A, int Mo, int Ki,
+                                                 const double* __restrict__ in, int64_t in_stride,
+                                                 double* out, int64_t out_stride, int64_t len) {
+  extern __shared__ double sA[];  // [MT][Ki]
+  const int m0 = blockIdx.y * MT;
+  for (int t = threadIdx.x; t < MT * Ki; t += blockDim.x) {
+    int mm = m0 + t / Ki, k = t % Ki;
+    sA[t] = mm < Mo ? A[(int64_t)mm * Ki + k] : 0.0;
+  }
+  __syncthreads();
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < len; j += (int64_t)gridDim.x * blockDim.x) {
+    double acc[MT];
+#pragma unroll
+    for (int t = 0; t < MT; ++t) acc[t] = 0.0;
+    for (int k = 0; k < Ki; ++k) {
+      const double v = __ldg(&in[(int64_t)k * in_stride + j]);
+#pragma unroll
+      for (int t = 0; t < MT; ++t) acc[t] = fma(sA[t * Ki + k], v, acc[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < MT; ++t)
+      if (m0 + t < Mo) out[(int64_t)(m0 + t) * out_stride + j] = acc[t];
+  }
+}
+
+__global__ void k_lincomb(double* out, double a, const double* __restrict__ x, double b,
+                          const double* __restrict__ y, double c, const double* __restrict__ z, int64_t len) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < len; j += (int64_t)gridDim.x * blockDim.x) {
+    double v = a * x[j];
+    if (y) v = fma(b, y[j], v);
+    if (z) v = fma(c, z[j], v);
+    out[j] = v;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_winner(DeviceMesh m, const double* __restrict__ U,
+                                                const double* __restrict__ V, double g, double H,
+                                                double* part) {
+  double acc = 0.0;
+  for (int64_t c = (int64_t)blockIdx.x * 256 + threadIdx.x; c < m.F; c += (int64_t)gridDim.x * 256) {
+    int dof[12];
+    double sg[12];
+    cell_dofs(m, c, dof, sg);
+    double u[12], v[12], w[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) { u[k] = U[dof[k]]; v[k] = V[dof[k]]; }
+    spmv_cell(m.M1, m.F, c, v, w);
+    double su = 0.0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) su = fma(u[k], w[k], su);
+    double se = 0.0;
+    const double det = m.det[c];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+        se = fma(U[m.n_u + 3 * c + k] * c_tab.M2_ref[k][l] * det, V[m.n_u + 3 * c + l], se);
+    acc += H * su + g * se;
+  }
+  double s3[3];
+  block_sum3<256>(acc, 0.0, 0.0, s3);
+  if (threadIdx.x == 0) part[blockIdx.x] = s3[0];
+}
+
+__global__ void k_check_finite(const double* __restrict__ x, int64_t len, int* flags) {
+  bool bad = false;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < len; j += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(x[j])) bad = true;
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, kFlagNonFinite);
+}
+
+int grid_for(int64_t len, int threads, int cap = 152 * 16) {
+  int64_t g = (len + threads - 1) / threads;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+cudaError_t cg_configure(int64_t F, CgWork* w) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg, kCgThreads, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int64_t need = (F + kCgThreads - 1) / kCgThreads;
+  int64_t maxb = (int64_t)per_sm * sms;
+  w->nblocks = (int)(need < maxb ? need : maxb);
+  if (w->nblocks < 1) w->nblocks = 1;
+  w->threads = kCgThreads;
+  return cudaSuccess;
+}
+
+cudaError_t launch_cg(const DeviceMesh& m, const CgWork& w, const CgParams& cp, const double* b,
+                      double* out, double scale_x, const double* add, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(w.w[0], 0, sizeof(double) * 3 * m.E, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(w.bar, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(w.nblocks);
+  cfg.blockDim = dim3(kCgThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_cg, m, w, cp, b, out, scale_x, add);
+}
+
+cudaError_t launch_apply_K(const DeviceMesh& m, const double* U, double s, double g, double H,
+                           const double* y_u, const double* y_eta, const double* z_eta, double* ru,
+                           double* eta_out, cudaStream_t st) {
+  int g_ = (int)((m.F + 127) / 128);
+  k_apply_K<<<g_, 128, 0, st>>>(m, U, s, g, H, y_u, y_eta, z_eta, ru, eta_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nonlinear_rhs(const DeviceMesh& m, const double* U, double* r, int B, int upwind,
+                                 cudaStream_t st) {
+  dim3 grid((unsigned)((m.F + 127) / 128), (unsigned)B);
+  k_nonlinear<<<grid, 128, 0, st>>>(m, U, r, upwind);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_m2inv(const DeviceMesh& m, const double* r, int64_t rstride, double* out,
+                         int64_t ostride, int B, cudaStream_t st) {
+  dim3 grid((unsigned)((m.F + 255) / 256), (unsigned)B);
+  k_m2inv<<<grid, 256, 0, st>>>(m, r, rstride, out, ostride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine(const double* A, int Mo, int Ki, const double* in, int64_t in_stride,
+                           double* out, int64_t out_stride, int64_t len, cudaStream_t st) {
+  constexpr int MT = 8;
+  size_t smem = sizeof(double) * MT * Ki;
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_combine<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  dim3 grid((unsigned)grid_for(len, 256, 152 * 4), (unsigned)((Mo + MT - 1) / MT));
+  k_combine<MT><<<grid, 256, smem, st>>>(A, Mo, Ki, in, in_stride, out, out_stride, len);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lincomb(double* out, double a, const double* x, double b, const double* y, double c,
+                           const double* z, int64_t len, cudaStream_t st) {
+  k_lincomb<<<grid_for(len, 256), 256, 0, st>>>(out, a, x, b, y, c, z, len);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_winner(const DeviceMesh& m, const double* U, const double* V, double g, double H,
+                          double* part, int* nblocks, cudaStream_t st) {
+  int nb = grid_for(m.F, 256, 304);
+  k_winner<<<nb, 256, 0, st>>>(m, U, V, g, H, part);
+  *nblocks = nb;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(const double* x, int64_t len, int* flags, cudaStream_t st) {
+  k_check_finite<<<grid_for(len, 256, 304), 256, 0, st>>>(x, len, flags);
+  return cudaGetLastError();
+}
+
+}  // namespace pavg

@@ -1,0 +1,91 @@
+// Internal declarations of libpavg: host setup (setup.cpp) and device side (*.cu).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "pavg.h"
+
+namespace pavg {
+
+// Number of cell quadrature points used by the nonlinear kernels (degree-5
+// symmetric rule), facet points per edge (Gauss-Legendre, part of the method's
+// definition because the upwind choice is taken per point).
+constexpr int kCellQ = 7;
+constexpr int kFacetQ = 4;
+
+// Canonical icosahedral mesh (paper Sec. 3).
+struct Mesh {
+  int refinement = 0;
+  double radius = 0;
+  std::vector<double> verts;          // [V][3]
+  std::vector<int32_t> cells;         // [F][3] counter-clockwise from outside
+  std::vector<int32_t> edges;         // [E][2] low, high
+  std::vector<int32_t> cell_edges;    // [F][3] local edge i is opposite local vertex i
+  std::vector<uint8_t> cell_aligned;  // [F] bit i: cell runs local edge i low -> high
+  std::vector<int32_t> edge_plus;     // [E] cell running the edge low -> high
+  std::vector<int32_t> edge_minus;    // [E]
+  std::vector<uint8_t> edge_lpos;     // [E] local index in plus | (local index in minus) << 2
+  int64_t F() const { return (int64_t)cells.size() / 3; }
+  int64_t E() const { return (int64_t)edges.size() / 2; }
+  int64_t V() const { return (int64_t)verts.size() / 3; }
+};
+
+void build_mesh(int refinement, double radius, Mesh* m);
+
+// Reference BDM2 element: psi_i = sum_l coef[l][i] mono_l, 12 vector monomials.
+struct RefElement {
+  double coef[12][12];
+  void eval(double x, double y, double val[12][2]) const;
+  void eval_grad(double x, double y, double grad[12][2][2]) const;  // [i][component][d/dx, d/dy]
+};
+void build_reference_element(RefElement* el);
+
+// Gauss-Legendre on [0, 1].
+void gauss_legendre01(int n, double* x, double* w);
+
+// Tables copied to __constant__ memory for the kernels.
+struct ConstTables {
+  double D[3][12];             // int_ref phi_i div psi_j
+  double M2inv_ref[3][3];      // inverse of int_ref phi_i phi_j (M2^{-1} = M2inv_ref / det)
+  double M2_ref[3][3];         // int_ref phi_i phi_j (M2 = det * M2_ref)
+  // cell rule for N: points, weights and basis data
+  double cq_w[kCellQ];
+  double cq_psi[kCellQ][12][2];
+  double cq_dpsi[kCellQ][12][2][2];
+  double cq_phi[kCellQ][3];
+  // facet rule: for each local edge (3) and each point, the reference basis at
+  // tau (plus side: counter-clockwise parameter tau) and at 1 - tau (minus side)
+  double fq_w[kFacetQ];
+  double fq_psi[2][3][kFacetQ][12][2];   // [side][local edge][point]
+  double fq_phi[2][3][kFacetQ][3];
+  double edge_dir[3][2];
+};
+
+// Per-cell data in structure-of-arrays form.
+struct HostCellData {
+  std::vector<double> M1;      // [78][F] signed element mass matrices, packed upper triangle
+  std::vector<double> C;       // [66][F] signed Coriolis element matrices, packed strict upper
+  std::vector<double> det;     // [F]
+  std::vector<double> G;       // [3][F] metric J^T J: G00, G01, G11
+  std::vector<double> dinv;    // [n_u] 1 / diag(M1)
+};
+void build_cell_data(const Mesh& m, const RefElement& el, double omega, HostCellData* out,
+                     ConstTables* tab);
+
+// Chebyshev coefficients c_k of e^{tL} in the real recurrence (Sec. 2.4):
+// returns the truncated list (degree K = size - 1) for Lb = lambda_max |t|.
+std::vector<double> cheb_coefficients(double Lb, double tol);
+
+// Riemann-sum shifts and weights (Sec. 2.2).
+int shifts_weights(double T, int M, int rule, std::vector<double>* s, std::vector<double>* w);
+
+inline int packed_sym(int i, int j) {  // i <= j, row-major upper triangle of 12x12
+  return i * 12 - i * (i - 1) / 2 + (j - i);
+}
+inline int packed_asym(int i, int j) {  // i < j
+  return i * 11 - i * (i - 1) / 2 + (j - i - 1);
+}
+
+}  // namespace pavg

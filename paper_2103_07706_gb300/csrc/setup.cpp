@@ -1,0 +1,530 @@
+// Host-side setup of libpavg: canonical mesh, Gauss rules, reference BDM2/DG1
+// element, per-cell geometry and element matrices, Chebyshev coefficients and
+// Riemann-sum weights.  Compiled with -ffp-contract=off so that vertex
+// coordinates are rounded identically on every host.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <complex>
+#include <map>
+#include <stdexcept>
+#include <tuple>
+
+#include "pavg_internal.h"
+
+namespace pavg {
+
+// ---------------------------------------------------------------- mesh
+namespace {
+
+void scale_to(const double p[3], double radius, double out[3]) {
+  double nrm = std::sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+  double s = radius / nrm;
+  out[0] = p[0] * s;
+  out[1] = p[1] * s;
+  out[2] = p[2] * s;
+}
+
+}  // namespace
+
+// Paper Sec. 3: icosahedral grid.  Construction (the numbering both the
+// library and its tests rely on): the 12 icosahedron vertices sorted by
+// (x, y, z); faces = mutually adjacent triples, counter-clockwise from
+// outside, smallest index first, sorted; refinement splits face (a, b, c) into
+// (a, ab, ca), (ab, b, bc), (ca, bc, c), (ab, bc, ca) with midpoints projected
+// to the sphere and numbered on first visit (edges visited ab, bc, ca).
+void build_mesh(int refinement, double radius, Mesh* m) {
+  const double phi = (1.0 + std::sqrt(5.0)) / 2.0;
+  std::vector<std::array<double, 3>> raw;
+  for (double a : {-1.0, 1.0})
+    for (double b : {-1.0, 1.0}) {
+      raw.push_back({0.0, a, b * phi});
+      raw.push_back({a, b * phi, 0.0});
+      raw.push_back({a * phi, 0.0, b});
+    }
+  std::sort(raw.begin(), raw.end());
+  std::vector<std::array<int, 3>> faces;
+  auto d2 = [&](int i, int j) {
+    double s = 0;
+    for (int k = 0; k < 3; ++k) s += (raw[i][k] - raw[j][k]) * (raw[i][k] - raw[j][k]);
+    return s;
+  };
+  for (int i = 0; i < 12; ++i)
+    for (int j = i + 1; j < 12; ++j)
+      for (int k = j + 1; k < 12; ++k) {
+        if (std::fabs(d2(i, j) - 4) > 1e-9 || std::fabs(d2(j, k) - 4) > 1e-9 ||
+            std::fabs(d2(i, k) - 4) > 1e-9)
+          continue;
+        const auto &a = raw[i], &b = raw[j], &c = raw[k];
+        double cx = b[1] * c[2] - b[2] * c[1], cy = b[2] * c[0] - b[0] * c[2],
+               cz = b[0] * c[1] - b[1] * c[0];
+        double triple = a[0] * cx + a[1] * cy + a[2] * cz;
+        std::array<int, 3> f = triple > 0 ? std::array<int, 3>{i, j, k} : std::array<int, 3>{i, k, j};
+        int r = (int)(std::min_element(f.begin(), f.end()) - f.begin());
+        std::rotate(f.begin(), f.begin() + r, f.end());
+        faces.push_back(f);
+      }
+  std::sort(faces.begin(), faces.end());
+  if (faces.size() != 20) throw std::runtime_error("icosahedron construction failed");
+  std::vector<std::array<double, 3>> verts(12);
+  for (int i = 0; i < 12; ++i) scale_to(raw[i].data(), radius, verts[i].data());
+
+  for (int level = 0; level < refinement; ++level) {
+    std::map<std::pair<int, int>, int> mid;
+    auto midpoint = [&](int a, int b) {
+      auto key = std::make_pair(std::min(a, b), std::max(a, b));
+      auto it = mid.find(key);
+      if (it != mid.end()) return it->second;
+      double s[3] = {verts[a][0] + verts[b][0], verts[a][1] + verts[b][1], verts[a][2] + verts[b][2]};
+      std::array<double, 3> v;
+      scale_to(s, radius, v.data());
+      verts.push_back(v);
+      int id = (int)verts.size() - 1;
+      mid[key] = id;
+      return id;
+    };
+    std::vector<std::array<int, 3>> next;
+    next.reserve(faces.size() * 4);
+    for (const auto& f : faces) {
+      int a = f[0], b = f[1], c = f[2];
+      int ab = midpoint(a, b), bc = midpoint(b, c), ca = midpoint(c, a);
+      next.push_back({a, ab, ca});
+      next.push_back({ab, b, bc});
+      next.push_back({ca, bc, c});
+      next.push_back({ab, bc, ca});
+    }
+    faces.swap(next);
+  }
+
+  m->refinement = refinement;
+  m->radius = radius;
+  m->verts.resize(verts.size() * 3);
+  for (size_t i = 0; i < verts.size(); ++i)
+    for (int k = 0; k < 3; ++k) m->verts[3 * i + k] = verts[i][k];
+  const int64_t F = (int64_t)faces.size();
+  m->cells.resize(3 * F);
+  for (int64_t c = 0; c < F; ++c)
+    for (int k = 0; k < 3; ++k) m->cells[3 * c + k] = faces[c][k];
+
+  // edges: sorted (low, high) pairs
+  std::vector<std::pair<int, int>> ev;
+  ev.reserve(3 * F);
+  for (int64_t c = 0; c < F; ++c) {
+    int v[3] = {faces[c][0], faces[c][1], faces[c][2]};
+    for (int i = 0; i < 3; ++i) {
+      int p = v[(i + 1) % 3], q = v[(i + 2) % 3];
+      ev.emplace_back(std::min(p, q), std::max(p, q));
+    }
+  }
+  std::sort(ev.begin(), ev.end());
+  ev.erase(std::unique(ev.begin(), ev.end()), ev.end());
+  const int64_t E = (int64_t)ev.size();
+  m->edges.resize(2 * E);
+  for (int64_t e = 0; e < E; ++e) {
+    m->edges[2 * e] = ev[e].first;
+    m->edges[2 * e + 1] = ev[e].second;
+  }
+  m->cell_edges.assign(3 * F, -1);
+  m->cell_aligned.assign(F, 0);
+  m->edge_plus.assign(E, -1);
+  m->edge_minus.assign(E, -1);
+  m->edge_lpos.assign(E, 0);
+  for (int64_t c = 0; c < F; ++c) {
+    int v[3] = {faces[c][0], faces[c][1], faces[c][2]};
+    for (int i = 0; i < 3; ++i) {
+      // local edge i runs v[i+1] -> v[i+2] counter-clockwise
+      int p = v[(i + 1) % 3], q = v[(i + 2) % 3];
+      auto key = std::make_pair(std::min(p, q), std::max(p, q));
+      int64_t e = std::lower_bound(ev.begin(), ev.end(), key) - ev.begin();
+      m->cell_edges[3 * c + i] = (int32_t)e;
+      if (p < q) {
+        m->cell_aligned[c] |= (uint8_t)(1u << i);
+        if (m->edge_plus[e] >= 0) throw std::runtime_error("edge traversed twice low->high");
+        m->edge_plus[e] = (int32_t)c;
+        m->edge_lpos[e] |= (uint8_t)i;
+      } else {
+        if (m->edge_minus[e] >= 0) throw std::runtime_error("edge traversed twice high->low");
+        m->edge_minus[e] = (int32_t)c;
+        m->edge_lpos[e] |= (uint8_t)(i << 2);
+      }
+    }
+  }
+  for (int64_t e = 0; e < E; ++e)
+    if (m->edge_plus[e] < 0 || m->edge_minus[e] < 0) throw std::runtime_error("open edge in mesh");
+}
+
+// ---------------------------------------------------------------- quadrature
+void gauss_legendre01(int n, double* x, double* w) {
+  // Newton iteration on P_n from the Chebyshev-like initial guesses.
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      double pn = p1, pnm1 = p0;  // P_n, P_{n-1} (n >= 2)
+      dp = n * (z * pn - pnm1) / (z * z - 1.0);
+      double dz = pn / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-17) break;
+    }
+    x[n - 1 - i] = 0.5 * (z + 1.0);
+    w[n - 1 - i] = 1.0 / ((1.0 - z * z) * dp * dp);  // (2 / ((1-z^2) P'^2)) / 2
+  }
+}
+
+namespace {
+
+// Collapsed Gauss-Legendre rule on the reference triangle:
+// x = s, y = t (1 - s), weight w_s w_t (1 - s); exact to degree 2n - 2.
+void triangle_gl(int n, std::vector<double>* px, std::vector<double>* py, std::vector<double>* pw) {
+  std::vector<double> x(n), w(n);
+  gauss_legendre01(n, x.data(), w.data());
+  px->clear(); py->clear(); pw->clear();
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      px->push_back(x[i]);
+      py->push_back(x[j] * (1.0 - x[i]));
+      pw->push_back(w[i] * w[j] * (1.0 - x[i]));
+    }
+}
+
+// Symmetric 7-point rule of degree 5 on the reference triangle (area 1/2).
+void triangle_deg5(double px[7], double py[7], double pw[7]) {
+  const double r = std::sqrt(15.0);
+  const double a1 = (6.0 - r) / 21.0, b1 = (9.0 + 2.0 * r) / 21.0;
+  const double a2 = (6.0 + r) / 21.0, b2 = (9.0 - 2.0 * r) / 21.0;
+  const double w1 = (155.0 - r) / 2400.0, w2 = (155.0 + r) / 2400.0;
+  double x[7] = {1.0 / 3.0, a1, a1, b1, a2, a2, b2};
+  double y[7] = {1.0 / 3.0, a1, b1, a1, a2, b2, a2};
+  double w[7] = {9.0 / 80.0, w1, w1, w1, w2, w2, w2};
+  for (int i = 0; i < 7; ++i) { px[i] = x[i]; py[i] = y[i]; pw[i] = w[i]; }
+}
+
+const double kEdgeStart[3][2] = {{1.0, 0.0}, {0.0, 1.0}, {0.0, 0.0}};
+const double kEdgeDir[3][2] = {{-1.0, 1.0}, {0.0, -1.0}, {1.0, 0.0}};
+
+// scalar P2 monomials ordered 1, x, y, xx, xy, yy and their gradients
+void mono(double x, double y, double m[6]) {
+  m[0] = 1.0; m[1] = x; m[2] = y; m[3] = x * x; m[4] = x * y; m[5] = y * y;
+}
+void mono_grad(double x, double y, double g[6][2]) {
+  g[0][0] = 0; g[0][1] = 0;
+  g[1][0] = 1; g[1][1] = 0;
+  g[2][0] = 0; g[2][1] = 1;
+  g[3][0] = 2 * x; g[3][1] = 0;
+  g[4][0] = y; g[4][1] = x;
+  g[5][0] = 0; g[5][1] = 2 * y;
+}
+// vector monomial l (0..11): component l / 6 carries scalar monomial l % 6
+void vmono(double x, double y, double v[12][2]) {
+  double m[6];
+  mono(x, y, m);
+  for (int l = 0; l < 12; ++l) {
+    v[l][0] = l < 6 ? m[l] : 0.0;
+    v[l][1] = l < 6 ? 0.0 : m[l - 6];
+  }
+}
+double legendre01(int j, double t) {
+  if (j == 0) return 1.0;
+  if (j == 1) return 2.0 * t - 1.0;
+  return 6.0 * t * t - 6.0 * t + 1.0;
+}
+
+bool invert(int n, const double* A, double* out) {
+  std::vector<double> a(A, A + n * n), inv(n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[i * n + i] = 1.0;
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(a[r * n + col]) > std::fabs(a[piv * n + col])) piv = r;
+    if (std::fabs(a[piv * n + col]) < 1e-300) return false;
+    if (piv != col)
+      for (int k = 0; k < n; ++k) {
+        std::swap(a[piv * n + k], a[col * n + k]);
+        std::swap(inv[piv * n + k], inv[col * n + k]);
+      }
+    double d = a[col * n + col];
+    for (int k = 0; k < n; ++k) { a[col * n + k] /= d; inv[col * n + k] /= d; }
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      double f = a[r * n + col];
+      if (f == 0.0) continue;
+      for (int k = 0; k < n; ++k) { a[r * n + k] -= f * a[col * n + k]; inv[r * n + k] -= f * inv[col * n + k]; }
+    }
+  }
+  std::copy(inv.begin(), inv.end(), out);
+  return true;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- reference element
+// Degrees of freedom of BDM2 (paper Sec. 2.5: V1 = BDM2): Legendre moments of
+// the outward flux on each edge (counter-clockwise parameter), and interior
+// moments against (1,0), (0,1), (-y,x).  The basis is dual to them.
+void build_reference_element(RefElement* el) {
+  double V[12][12];  // V[k][l] = dof_k(vector monomial l)
+  double gx[6], gw[6];
+  gauss_legendre01(6, gx, gw);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      for (int l = 0; l < 12; ++l) {
+        double s = 0;
+        for (int q = 0; q < 6; ++q) {
+          double x = kEdgeStart[i][0] + gx[q] * kEdgeDir[i][0];
+          double y = kEdgeStart[i][1] + gx[q] * kEdgeDir[i][1];
+          double v[12][2];
+          vmono(x, y, v);
+          double flux = v[l][0] * kEdgeDir[i][1] - v[l][1] * kEdgeDir[i][0];
+          s += gw[q] * flux * legendre01(j, gx[q]);
+        }
+        V[3 * i + j][l] = s;
+      }
+  std::vector<double> tx, ty, tw;
+  triangle_gl(5, &tx, &ty, &tw);
+  for (int j = 0; j < 3; ++j)
+    for (int l = 0; l < 12; ++l) {
+      double s = 0;
+      for (size_t q = 0; q < tx.size(); ++q) {
+        double v[12][2];
+        vmono(tx[q], ty[q], v);
+        double qx = j == 0 ? 1.0 : (j == 1 ? 0.0 : -ty[q]);
+        double qy = j == 0 ? 0.0 : (j == 1 ? 1.0 : tx[q]);
+        s += tw[q] * (v[l][0] * qx + v[l][1] * qy);
+      }
+      V[9 + j][l] = s;
+    }
+  double inv[144];
+  if (!invert(12, &V[0][0], inv)) throw std::runtime_error("BDM2 Vandermonde is singular");
+  for (int l = 0; l < 12; ++l)
+    for (int i = 0; i < 12; ++i) el->coef[l][i] = inv[l * 12 + i];
+}
+
+void RefElement::eval(double x, double y, double val[12][2]) const {
+  double v[12][2];
+  vmono(x, y, v);
+  for (int i = 0; i < 12; ++i) {
+    double a = 0, b = 0;
+    for (int l = 0; l < 12; ++l) { a += coef[l][i] * v[l][0]; b += coef[l][i] * v[l][1]; }
+    val[i][0] = a;
+    val[i][1] = b;
+  }
+}
+
+void RefElement::eval_grad(double x, double y, double grad[12][2][2]) const {
+  double g[6][2];
+  mono_grad(x, y, g);
+  for (int i = 0; i < 12; ++i)
+    for (int c = 0; c < 2; ++c)
+      for (int d = 0; d < 2; ++d) {
+        double s = 0;
+        for (int p = 0; p < 6; ++p) s += coef[6 * c + p][i] * g[p][d];
+        grad[i][c][d] = s;
+      }
+}
+
+// ---------------------------------------------------------------- cell data
+// Element matrices of Sec. 2.5 on flat cells with the contravariant Piola map:
+//   M1_ij = int psi_i^T G psi_j / det,  C_ij = int f cross2(psi_j, psi_i)
+// (C_ij = int w_i . f (k x w_j) dx), f = 2 Omega z / R at the cell point;
+// D_ij = int phi_i div psi_j is the same on every cell.  Signs map the cell's
+// counter-clockwise edge DOFs to the global ones: (-1)^(j+1) for moment j on an
+// edge the cell runs high -> low.
+void build_cell_data(const Mesh& m, const RefElement& el, double omega, HostCellData* out,
+                     ConstTables* tab) {
+  const int64_t F = m.F(), E = m.E();
+  const int64_t n_u = 3 * E + 3 * F;
+  std::vector<double> qx, qy, qw;
+  triangle_gl(4, &qx, &qy, &qw);
+  const int Q = (int)qx.size();
+  std::vector<double> psi(Q * 24), dpsi(Q * 48), phi(Q * 3);
+  for (int q = 0; q < Q; ++q) {
+    el.eval(qx[q], qy[q], reinterpret_cast<double(*)[2]>(&psi[q * 24]));
+    el.eval_grad(qx[q], qy[q], reinterpret_cast<double(*)[2][2]>(&dpsi[q * 48]));
+    phi[q * 3 + 0] = 1.0 - qx[q] - qy[q];
+    phi[q * 3 + 1] = qx[q];
+    phi[q * 3 + 2] = qy[q];
+  }
+  // D (reference) and DG1 reference mass
+  double M2r[9] = {0};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 12; ++j) {
+      double s = 0;
+      for (int q = 0; q < Q; ++q) s += qw[q] * phi[q * 3 + i] * (dpsi[q * 48 + j * 4 + 0] + dpsi[q * 48 + j * 4 + 3]);
+      tab->D[i][j] = s;
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0;
+      for (int q = 0; q < Q; ++q) s += qw[q] * phi[q * 3 + i] * phi[q * 3 + j];
+      M2r[i * 3 + j] = s;
+    }
+  double M2i[9];
+  if (!invert(3, M2r, M2i)) throw std::runtime_error("DG1 mass singular");
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      tab->M2inv_ref[i][j] = M2i[i * 3 + j];
+      tab->M2_ref[i][j] = M2r[i * 3 + j];
+    }
+
+  out->M1.assign(78 * F, 0.0);
+  out->C.assign(66 * F, 0.0);
+  out->det.assign(F, 0.0);
+  out->G.assign(3 * F, 0.0);
+  std::vector<double> diag(n_u, 0.0);
+  for (int64_t c = 0; c < F; ++c) {
+    const double* a = &m.verts[3 * m.cells[3 * c + 0]];
+    const double* b = &m.verts[3 * m.cells[3 * c + 1]];
+    const double* d = &m.verts[3 * m.cells[3 * c + 2]];
+    double J0[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    double J1[3] = {d[0] - a[0], d[1] - a[1], d[2] - a[2]};
+    double cr[3] = {J0[1] * J1[2] - J0[2] * J1[1], J0[2] * J1[0] - J0[0] * J1[2], J0[0] * J1[1] - J0[1] * J1[0]};
+    double det = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+    double G00 = J0[0] * J0[0] + J0[1] * J0[1] + J0[2] * J0[2];
+    double G01 = J0[0] * J1[0] + J0[1] * J1[1] + J0[2] * J1[2];
+    double G11 = J1[0] * J1[0] + J1[1] * J1[1] + J1[2] * J1[2];
+    out->det[c] = det;
+    out->G[0 * F + c] = G00;
+    out->G[1 * F + c] = G01;
+    out->G[2 * F + c] = G11;
+    double sgn[12];
+    int dof[12];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        bool al = (m.cell_aligned[c] >> i) & 1;
+        sgn[3 * i + j] = al ? 1.0 : (j == 1 ? 1.0 : -1.0);
+        dof[3 * i + j] = 3 * m.cell_edges[3 * c + i] + j;
+      }
+    for (int j = 0; j < 3; ++j) { sgn[9 + j] = 1.0; dof[9 + j] = (int)(3 * E + 3 * c + j); }
+    double fz[64];
+    for (int q = 0; q < Q; ++q) {
+      double z = a[2] + J0[2] * qx[q] + J1[2] * qy[q];
+      fz[q] = 2.0 * omega * z / m.radius;
+    }
+    for (int i = 0; i < 12; ++i)
+      for (int j = i; j < 12; ++j) {
+        double sm = 0, sc = 0;
+        for (int q = 0; q < Q; ++q) {
+          const double* pi = &psi[q * 24 + 2 * i];
+          const double* pj = &psi[q * 24 + 2 * j];
+          sm += qw[q] * (pi[0] * (G00 * pj[0] + G01 * pj[1]) + pi[1] * (G01 * pj[0] + G11 * pj[1]));
+          sc += qw[q] * fz[q] * (pj[0] * pi[1] - pj[1] * pi[0]);
+        }
+        double ss = sgn[i] * sgn[j];
+        out->M1[(int64_t)packed_sym(i, j) * F + c] = ss * sm / det;
+        if (j > i) out->C[(int64_t)packed_asym(i, j) * F + c] = ss * sc;
+        if (i == j) diag[dof[i]] += sm / det;
+      }
+  }
+  out->dinv.resize(n_u);
+  for (int64_t k = 0; k < n_u; ++k) out->dinv[k] = 1.0 / diag[k];
+
+  // tables for the nonlinear kernels
+  double cx[7], cy[7], cw[7];
+  triangle_deg5(cx, cy, cw);
+  for (int q = 0; q < kCellQ; ++q) {
+    tab->cq_w[q] = cw[q];
+    el.eval(cx[q], cy[q], tab->cq_psi[q]);
+    el.eval_grad(cx[q], cy[q], tab->cq_dpsi[q]);
+    tab->cq_phi[q][0] = 1.0 - cx[q] - cy[q];
+    tab->cq_phi[q][1] = cx[q];
+    tab->cq_phi[q][2] = cy[q];
+  }
+  double fx[kFacetQ], fw[kFacetQ];
+  gauss_legendre01(kFacetQ, fx, fw);
+  for (int p = 0; p < kFacetQ; ++p) tab->fq_w[p] = fw[p];
+  for (int side = 0; side < 2; ++side)
+    for (int i = 0; i < 3; ++i)
+      for (int p = 0; p < kFacetQ; ++p) {
+        double t = side == 0 ? fx[p] : 1.0 - fx[p];
+        double x = kEdgeStart[i][0] + t * kEdgeDir[i][0];
+        double y = kEdgeStart[i][1] + t * kEdgeDir[i][1];
+        el.eval(x, y, tab->fq_psi[side][i][p]);
+        tab->fq_phi[side][i][p][0] = 1.0 - x - y;
+        tab->fq_phi[side][i][p][1] = x;
+        tab->fq_phi[side][i][p][2] = y;
+      }
+  for (int i = 0; i < 3; ++i) { tab->edge_dir[i][0] = kEdgeDir[i][0]; tab->edge_dir[i][1] = kEdgeDir[i][1]; }
+
+  // self-check of the degree-5 rule
+  for (int p = 0; p <= 5; ++p)
+    for (int q = 0; q + p <= 5; ++q) {
+      double s = 0;
+      for (int k = 0; k < 7; ++k) s += cw[k] * std::pow(cx[k], p) * std::pow(cy[k], q);
+      double fp = std::tgamma(p + 1.0), fq = std::tgamma(q + 1.0), fpq = std::tgamma(p + q + 3.0);
+      if (std::fabs(s - fp * fq / fpq) > 1e-15) throw std::runtime_error("degree-5 rule check failed");
+    }
+}
+
+// ---------------------------------------------------------------- Chebyshev coefficients
+// Sec. 2.4: coefficients of e^{i Lb y} = sum_k a_k T_k(y) from samples at the
+// Chebyshev-Lobatto points (a discrete cosine transform, evaluated directly),
+// then c_k = a_k i^{-k} for the real recurrence Q_{k+1} = 2 X Q_k + Q_{k-1};
+// truncation: the smallest K with sum_{j > K} |c_j| <= tol.
+std::vector<double> cheb_coefficients(double Lb, double tol) {
+  if (Lb == 0.0) return {1.0};
+  int N = 1;
+  while (N < Lb + 64.0) N <<= 1;
+  std::vector<double> cg(N + 1), sg(N + 1), ctab(2 * N);
+  for (int j = 0; j <= N; ++j) {
+    double y = std::cos(M_PI * j / N);
+    cg[j] = std::cos(Lb * y);
+    sg[j] = std::sin(Lb * y);
+  }
+  for (int k = 0; k < 2 * N; ++k) ctab[k] = std::cos(M_PI * k / N);
+  std::vector<double> c(N + 1);
+  for (int k = 0; k <= N; ++k) {
+    const std::vector<double>& g = (k % 2 == 0) ? cg : sg;
+    double s = 0.5 * (g[0] + g[N] * ctab[(int64_t)N * k % (2 * N)]);
+    for (int j = 1; j < N; ++j) s += g[j] * ctab[(int64_t)j * k % (2 * N)];
+    s *= 2.0 / N;
+    if (k == 0 || k == N) s *= 0.5;
+    int m = k / 2;
+    c[k] = (m % 2 == 0) ? s : -s;
+  }
+  int K = N;
+  double tail = 0.0;
+  while (K > 0 && tail + std::fabs(c[K]) <= tol) {
+    tail += std::fabs(c[K]);
+    --K;
+  }
+  c.resize(K + 1);
+  return c;
+}
+
+// Sec. 2.2: weights w_m = rho(s_m / T) / sum_j rho(s_j / T) with the C-infinity
+// bump rho(x) = exp(-1 / (1/4 - x^2)) on |x| < 1/2.
+int shifts_weights(double T, int M, int rule, std::vector<double>* s, std::vector<double>* w) {
+  if (M < 1 || T < 0) return PAVG_ERR_INVAL;
+  s->assign(M, 0.0);
+  w->assign(M, 0.0);
+  if (rule == PAVG_QUAD_MIDPOINT) {
+    for (int m = 0; m < M; ++m) (*s)[m] = -0.5 * T + (m + 0.5) * T / M;
+  } else if (rule == PAVG_QUAD_CLOSED) {
+    if (M < 3 || M % 2 == 0) return PAVG_ERR_INVAL;
+    int Nh = (M - 1) / 2;
+    for (int m = 0; m < M; ++m) (*s)[m] = (m - Nh) * (0.5 * T) / Nh;
+  } else {
+    return PAVG_ERR_INVAL;
+  }
+  if (T == 0.0) {
+    for (int m = 0; m < M; ++m) { (*s)[m] = 0.0; (*w)[m] = 1.0 / M; }
+    return PAVG_OK;
+  }
+  double tot = 0;
+  for (int m = 0; m < M; ++m) {
+    double x = (*s)[m] / T;
+    double r = std::fabs(x) < 0.5 ? std::exp(-1.0 / (0.25 - x * x)) : 0.0;
+    (*w)[m] = r;
+    tot += r;
+  }
+  for (int m = 0; m < M; ++m) (*w)[m] /= tot;
+  return PAVG_OK;
+}
+
+}  // namespace pavg

@@ -1,0 +1,241 @@
+"""Thin ctypes binding of libpavg.so (C-ABI declared in include/pavg.h).
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels.  States are torch float64 CUDA tensors laid out as in
+pavg.h ([n] or [B][n], u first then eta); torch supplies device memory and the
+current stream.  Importing this module loads the library and raises when it
+is missing or fails to load: there is no fallback path.
+"""
+
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpavg.so")
+
+PAVG_QUAD_MIDPOINT = 0
+PAVG_QUAD_CLOSED = 1
+PAVG_UPWIND_STANDARD = 0
+PAVG_UPWIND_AS_PRINTED = 1
+
+ERRORS = {
+    -1: "PAVG_ERR_INVAL", -2: "PAVG_ERR_NOMEM", -3: "PAVG_ERR_CUDA", -4: "PAVG_ERR_NOCONV",
+    -5: "PAVG_ERR_NONFINITE", -6: "PAVG_ERR_TIMEOUT",
+}
+
+EXPORTED = [
+    "pavg_default_params", "pavg_create", "pavg_destroy", "pavg_sizes", "pavg_mesh_export",
+    "pavg_set_topography", "pavg_lambda_max", "pavg_linear", "pavg_nonlinear", "pavg_expL_apply",
+    "pavg_averaged_rhs", "pavg_averaged_rhs_literal", "pavg_timestep", "pavg_sync", "pavg_get_stats",
+    "pavg_reset_stats", "pavg_last_error",
+]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("refinement", ctypes.c_int),
+        ("radius", ctypes.c_double),
+        ("omega", ctypes.c_double),
+        ("g", ctypes.c_double),
+        ("H", ctypes.c_double),
+        ("cheb_tol", ctypes.c_double),
+        ("cg_rtol", ctypes.c_double),
+        ("cg_maxit", ctypes.c_int),
+        ("lambda_max", ctypes.c_double),
+        ("quad_rule", ctypes.c_int),
+        ("upwind_convention", ctypes.c_int),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("lambda_max", ctypes.c_double),
+        ("last_degree", ctypes.c_int),
+        ("cg_solves", ctypes.c_int),
+        ("cg_iters_max", ctypes.c_int),
+        ("cg_iters_mean", ctypes.c_double),
+        ("error_flags", ctypes.c_int),
+    ]
+
+
+class PavgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def load(path=LIB_PATH):
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpavg.so not found at {path}: build it with "
+                           "`python -m paper_2103_07706_gb300.build` (no CPU fallback exists)")
+    lib = ctypes.CDLL(path)
+    P, D, I, I64, V = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
+    sig = {
+        "pavg_default_params": (I, [ctypes.POINTER(Params)]),
+        "pavg_create": (I, [ctypes.POINTER(Params), ctypes.POINTER(P)]),
+        "pavg_destroy": (I, [P]),
+        "pavg_sizes": (I, [P] + [ctypes.POINTER(I64)] * 5),
+        "pavg_mesh_export": (I, [P, P, P]),
+        "pavg_set_topography": (I, [P, P]),
+        "pavg_lambda_max": (I, [P, ctypes.POINTER(D)]),
+        "pavg_linear": (I, [P, P, P, I, V]),
+        "pavg_nonlinear": (I, [P, P, P, I, V]),
+        "pavg_expL_apply": (I, [P, D, P, P, I, V]),
+        "pavg_averaged_rhs": (I, [P, D, I, P, P, V]),
+        "pavg_averaged_rhs_literal": (I, [P, D, I, P, P, V]),
+        "pavg_timestep": (I, [P, D, D, I, P, I, V]),
+        "pavg_sync": (I, [P, V]),
+        "pavg_get_stats": (I, [P, ctypes.POINTER(Stats)]),
+        "pavg_reset_stats": (I, [P]),
+        "pavg_last_error": (ctypes.c_char_p, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_LIB = None
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        _LIB = load()
+    return _LIB
+
+
+def default_params(**overrides):
+    p = Params()
+    rc = lib().pavg_default_params(ctypes.byref(p))
+    if rc:
+        raise PavgError(rc, "pavg_default_params")
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(t, n, B=None):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    want = n if B is None else B * n
+    if t.numel() != want:
+        raise ValueError(f"expected {want} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Model:
+    """One library context: mesh, FE operators and workspace on the current device."""
+
+    def __init__(self, refinement=3, **params):
+        self._lib = lib()
+        torch.cuda.init()
+        p = default_params(refinement=refinement, **params)
+        h = ctypes.c_void_p()
+        rc = self._lib.pavg_create(ctypes.byref(p), ctypes.byref(h))
+        if rc:
+            raise PavgError(rc, "pavg_create failed")
+        self._h = h
+        self.params = p
+        vals = [ctypes.c_int64() for _ in range(5)]
+        self._check(self._lib.pavg_sizes(h, *[ctypes.byref(v) for v in vals]))
+        self.n_u, self.n_eta, self.n_cells, self.n_edges, self.n_verts = [v.value for v in vals]
+        self.n = self.n_u + self.n_eta
+
+    def _check(self, rc):
+        if rc:
+            raise PavgError(rc, self._lib.pavg_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pavg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- info
+    def mesh(self):
+        import numpy as np
+        verts = np.zeros((self.n_verts, 3))
+        cells = np.zeros((self.n_cells, 3), dtype=np.int32)
+        self._check(self._lib.pavg_mesh_export(self._h, verts.ctypes.data_as(ctypes.c_void_p),
+                                               cells.ctypes.data_as(ctypes.c_void_p)))
+        return verts, cells
+
+    @property
+    def lambda_max(self):
+        v = ctypes.c_double()
+        self._check(self._lib.pavg_lambda_max(self._h, ctypes.byref(v)))
+        return v.value
+
+    def stats(self):
+        s = Stats()
+        self._check(self._lib.pavg_get_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def reset_stats(self):
+        self._check(self._lib.pavg_reset_stats(self._h))
+
+    def sync(self):
+        self._check(self._lib.pavg_sync(self._h, _stream()))
+
+    def set_topography(self, b):
+        self._check(self._lib.pavg_set_topography(self._h, _ptr(b, self.n_eta)))
+
+    # ---------------------------------------------------------------- operators
+    def _out(self, U, out):
+        return torch.empty_like(U) if out is None else out
+
+    def _batch(self, U):
+        if U.numel() % self.n:
+            raise ValueError("state size is not a multiple of n")
+        return U.numel() // self.n
+
+    def linear(self, U, out=None):
+        out = self._out(U, out)
+        B = self._batch(U)
+        self._check(self._lib.pavg_linear(self._h, _ptr(U, self.n, B), _ptr(out, self.n, B), B, _stream()))
+        return out
+
+    def nonlinear(self, U, out=None):
+        out = self._out(U, out)
+        B = self._batch(U)
+        self._check(self._lib.pavg_nonlinear(self._h, _ptr(U, self.n, B), _ptr(out, self.n, B), B, _stream()))
+        return out
+
+    def expL(self, t, U, out=None):
+        out = self._out(U, out)
+        B = self._batch(U)
+        self._check(self._lib.pavg_expL_apply(self._h, float(t), _ptr(U, self.n, B), _ptr(out, self.n, B), B,
+                                              _stream()))
+        return out
+
+    def averaged_rhs(self, T, M, U, out=None):
+        out = self._out(U, out)
+        self._check(self._lib.pavg_averaged_rhs(self._h, float(T), int(M), _ptr(U, self.n), _ptr(out, self.n),
+                                                _stream()))
+        return out
+
+    def averaged_rhs_literal(self, T, M, U, out=None):
+        out = self._out(U, out)
+        self._check(self._lib.pavg_averaged_rhs_literal(self._h, float(T), int(M), _ptr(U, self.n),
+                                                        _ptr(out, self.n), _stream()))
+        return out
+
+    def timestep(self, dt, T, M, U, nsteps=1):
+        self._check(self._lib.pavg_timestep(self._h, float(dt), float(T), int(M), _ptr(U, self.n), int(nsteps),
+                                            _stream()))
+        return U
