@@ -1,0 +1,367 @@
+"""Benchmark: phase-averaged RHS evaluations per second on the refinement-6 mesh.
+
+One step = one averaged_rhs evaluation N-bar(U) = sum_m w_m e^{-s_m L} N(e^{s_m L} U)
+(81920 cells, n = 860160 FP64 DOFs, M = 64 shifts, T = 1 h) of a seeded
+balanced state, through the library's C-ABI (graph-replayed).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pavg|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank evaluates its
+own independent state (weak scaling, no collective on the data path).
+--impl reference times the FP64 CPU oracle (the plain literal per-shift form)
+on a bounded sample of the same workload and prints its own line.
+"""
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "phase-averaged RHS evals/sec (ref-6 mesh, M=64) and rel L2 err vs FP64 oracle"
+# lambda_max of L on the refinement-6 mesh with R, Omega, g, H below: the
+# library's power-iteration estimate (0.02289 s^-1) widened by 2 %; passed to
+# the library and to the oracle alike so both use the same Chebyshev degrees.
+LAMBDA_R6 = 0.02335
+CONFIG = {"refinement": 6, "cells": 81920, "M": 64, "T_s": 3600.0, "state": "harmonic l<=16 seed 2103+rank",
+          "R": 6.37122e6, "Omega": 7.292e-5, "g": 9.80616, "H": 5000.0, "cheb_tol": 1e-6, "cg_rtol": 1e-14,
+          "lambda_max": LAMBDA_R6}
+PARITY_CASE = {"refinement": 3, "M": 8, "T_s": 3600.0, "lambda_max": 0.00286, "lmax": 8, "seed": 2103}
+
+
+def _cg_flops(F, n_u, iters):
+    # element SpMV (12 x 12 per cell, 2 flops per entry) + 15 flops per velocity
+    # DOF of vector updates and the three inner products, per iteration, plus
+    # the initial residual pass
+    return (iters + 1.0) * (288.0 * F + 15.0 * n_u)
+
+
+# ----------------------------------------------------------------------------- CPU oracle leg
+def _oracle_worker(q, cfg, parity):
+    """Runs in a spawned process (no CUDA): oracle timing sample + parity case."""
+    try:
+        import numpy as np
+
+        from oracle import averaging
+        from oracle.model import OracleModel, OracleParams
+        from paper_2103_07706_gb300.inputs import harmonic_state
+        out = {}
+        # parity case: the small configuration the oracle finishes in seconds
+        pm = OracleModel(OracleParams(refinement=parity["refinement"], lambda_max=parity["lambda_max"]))
+        U, _ = harmonic_state(pm.mesh.verts, pm.mesh.cells, parity["seed"], parity["lmax"])
+        out["parity_ref"] = pm.averaged_rhs(parity["T_s"], parity["M"], U)
+        out["parity_M1"] = None
+        u = out["parity_ref"][: pm.n_u]
+        e = out["parity_ref"][pm.n_u:]
+        out["parity_norms"] = (float(np.sqrt(u @ (pm.ops.M1 @ u))), float(np.sqrt(e @ (pm.ops.M2 @ e))))
+        out["parity_n_u"] = pm.n_u
+        out["parity_M1_csr"] = (pm.ops.M1.data, pm.ops.M1.indices, pm.ops.M1.indptr)
+        out["parity_M2_csr"] = (pm.ops.M2.data, pm.ops.M2.indices, pm.ops.M2.indptr)
+        # timing sample at the benchmark configuration
+        t0 = time.time()
+        m = OracleModel(OracleParams(refinement=cfg["refinement"], lambda_max=cfg["lambda_max"],
+                                     g=cfg["g"], H=cfg["H"], omega=cfg["Omega"], radius=cfg["R"]))
+        out["setup_s"] = time.time() - t0
+        U, _ = harmonic_state(m.mesh.verts, m.mesh.cells, 2103, 16)
+        nl = 6
+        t0 = time.perf_counter()
+        V = U
+        for _ in range(nl):
+            V = m.L(V) * (1.0 / cfg["lambda_max"])
+        tL = (time.perf_counter() - t0) / nl
+        t0 = time.perf_counter()
+        m.N(U)
+        tN = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for _ in range(nl):
+            V = 2.0 * V + U
+        tax = (time.perf_counter() - t0) / nl
+        s, w = averaging.shifts_and_weights(cfg["T_s"], cfg["M"])
+        Ks = [m.degree(x) for x in s]
+        # literal form: per shift a forward and a backward chain of K_m L-applies
+        # and K_m vector updates each, one N with its mass solves, one weighted add
+        est = sum(2 * K * (tL + tax) + tN + tax for K in Ks)
+        out["cpu"] = {"value": 1.0 / est, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                      "sample": f"refinement-6 unit costs timed on this host: {nl} L applications "
+                                f"({tL:.3f} s each, sparse-LU mass solve), 1 N ({tN:.2f} s), {nl} vector updates; "
+                                f"scaled by the literal per-shift operation counts (sum_m 2 K_m = {2 * sum(Ks)} "
+                                f"L-applies, {cfg['M']} N) to one evaluation ({est:.0f} s); oracle setup "
+                                f"({out['setup_s']:.0f} s) excluded",
+                      "est_eval_s": est}
+        q.put(out)
+    except Exception as e:  # pragma: no cover - reported in the JSON line
+        q.put({"error": repr(e)})
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+
+    from oracle import averaging
+    from oracle.model import OracleModel, OracleParams
+    from paper_2103_07706_gb300.inputs import harmonic_state
+    cfg = CONFIG
+    m = OracleModel(OracleParams(refinement=cfg["refinement"], lambda_max=cfg["lambda_max"], g=cfg["g"], H=cfg["H"],
+                                 omega=cfg["Omega"], radius=cfg["R"]))
+    U, _ = harmonic_state(m.mesh.verts, m.mesh.cells, 2103, 16)
+    s, w = averaging.shifts_and_weights(cfg["T_s"], cfg["M"])
+    Ks = [m.degree(x) for x in s]
+    n_ops = sum(2 * K for K in Ks)
+
+    def sample():
+        # one step: 2 L-applies and one N of the literal form, scaled to an evaluation
+        t0 = time.perf_counter()
+        V = m.L(U)
+        V = m.L(V)
+        t1 = time.perf_counter()
+        m.N(U)
+        t2 = time.perf_counter()
+        return (t1 - t0) / 2.0 * n_ops + (t2 - t1) * cfg["M"]
+
+    for _ in range(args.warmup):
+        sample()
+    est = [sample() for _ in range(args.steps)]
+    eval_s = statistics.mean(est)
+    value = 1.0 / eval_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": eval_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "averaged_rhs r6 M64 T1h (oracle, literal per-shift form)", **cfg},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                             "sample": "each step: 2 L-applies and 1 N at refinement 6 timed, scaled by the literal "
+                                       f"form's {n_ops} L-applies and {cfg['M']} N per evaluation"},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_pavg(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    q = proc = None
+    if want_cpu:  # spawned before any CUDA call
+        ctxmp = mp.get_context("spawn")
+        q = ctxmp.Queue()
+        proc = ctxmp.Process(target=_oracle_worker, args=(q, CONFIG, PARITY_CASE), daemon=True)
+        proc.start()
+
+    import numpy as np
+    import torch
+
+    from paper_2103_07706_gb300 import pavg
+    from paper_2103_07706_gb300.inputs import harmonic_state
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    cfg = CONFIG
+    model = pavg.Model(cfg["refinement"], lambda_max=cfg["lambda_max"], g=cfg["g"], H=cfg["H"], omega=cfg["Omega"],
+                       radius=cfg["R"], cheb_tol=cfg["cheb_tol"], cg_rtol=cfg["cg_rtol"])
+    verts, cells = model.mesh()
+    U, info = harmonic_state(verts, cells, 2103 + rank, 16)
+    Ud = torch.from_numpy(U).cuda()
+    out = torch.empty_like(Ud)
+    T, M = cfg["T_s"], cfg["M"]
+    stream = torch.cuda.current_stream()
+    model.kernel_timing(True)
+    for _ in range(args.warmup):
+        model.averaged_rhs(T, M, Ud, out)
+    model.sync()
+    model.reset_stats()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        model.averaged_rhs(T, M, Ud, out)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    model.sync()
+    st = model.stats()
+    cg_ms, cg_n = model.kernel_time()
+    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * args.steps / (ms_max / 1e3)
+
+    # end to end through the C-ABI: pinned host input -> device, evaluate, result -> host
+    Uh = torch.from_numpy(U).pin_memory()
+    Oh = torch.empty_like(Uh).pin_memory()
+    barrier()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(args.steps):
+        Ud.copy_(Uh, non_blocking=True)
+        model.averaged_rhs(T, M, Ud, out)
+        Oh.copy_(out, non_blocking=True)
+    e3.record(stream)
+    barrier()
+    ms_e2e = e2.elapsed_time(e3)
+    t = torch.tensor([ms_e2e], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = world * args.steps / (float(t.item()) / 1e3)
+    model.sync()
+
+    # parity of the small configuration against the oracle (computed by the spawned leg)
+    cpu = None
+    parity = None
+    if proc is not None:
+        res = q.get(timeout=1800)
+        proc.join(timeout=60)
+        if "error" in res:
+            cpu = {"error": res["error"]}
+        else:
+            cpu = res["cpu"]
+            import scipy.sparse as sp
+            pm = pavg.Model(PARITY_CASE["refinement"], lambda_max=PARITY_CASE["lambda_max"])
+            pv, pc = pm.mesh()
+            Up, _ = harmonic_state(pv, pc, PARITY_CASE["seed"], PARITY_CASE["lmax"])
+            got = pm.averaged_rhs(PARITY_CASE["T_s"], PARITY_CASE["M"], torch.from_numpy(Up).cuda()).cpu().numpy()
+            pm.sync()
+            ref = res["parity_ref"]
+            nu = res["parity_n_u"]
+            M1 = sp.csr_matrix(res["parity_M1_csr"], shape=(nu, nu))
+            ne = len(ref) - nu
+            M2 = sp.csr_matrix(res["parity_M2_csr"], shape=(ne, ne))
+            du, de = got[:nu] - ref[:nu], got[nu:] - ref[nu:]
+            parity = {"case": "refinement 3, M=8, T=1h, harmonic l<=8 seed 2103",
+                      "rel_l2_u_M1": float(np.sqrt(du @ (M1 @ du))) / res["parity_norms"][0],
+                      "rel_l2_eta_M2": float(np.sqrt(de @ (M2 @ de))) / res["parity_norms"][1]}
+            pm.close()
+
+    peaks = _peaks()
+    F, n_u = model.n_cells, model.n_u
+    iters = st["cg_iters_mean"]
+    roof = None
+    if cg_n > 0:
+        dur_s = cg_ms / cg_n / 1e3
+        achieved = _cg_flops(F, n_u, iters) / dur_s / 1e12
+        peak = 1.25  # FP64 TFLOP/s, nominal GB300 figure (no measured FP64 peak in MEASURED_PEAKS.json)
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_cg (persistent M1 conjugate gradients, FP64)",
+                "launch_ms": cg_ms / cg_n, "launches_per_step": cg_n, "iters_per_launch": iters,
+                "share_of_step": cg_ms / (ms / args.steps), "peak_source": "nominal FP64 1.25 TFLOP/s"}
+    line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "averaged_rhs r6 M64 T1h FP64 shared-basis", **cfg,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "working set ~1.4 GB > L2 (no flush needed)", "rossby": info["rossby"],
+                       "K_max": st["last_degree"]},
+            "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": 8 * model.n,
+                    "d2h_bytes_per_step": 8 * model.n},
+            "gpu_launches": st["kernel_launches"] * args.steps,
+            "roofline": roof, "cpu_baseline": cpu, "parity": parity, "clocks": clk,
+            "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
+            "error_flags": st["error_flags"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pavg", choices=["pavg", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--refinement", type=int, default=None, help="smaller case (profiling only)")
+    ap.add_argument("--M", type=int, default=None, help="number of shifts (profiling only)")
+    args = ap.parse_args()
+    if args.refinement is not None or args.M is not None:
+        r = CONFIG["refinement"] if args.refinement is None else args.refinement
+        CONFIG.update({"refinement": r, "cells": 20 * 4 ** r, "M": args.M or CONFIG["M"],
+                       "lambda_max": LAMBDA_R6 / 2 ** (6 - r)})
+        args.no_cpu_baseline = True
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_pavg(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -138,10 +138,11 @@ int pavg_sync(pavg_ctx* ctx, void* stream);
 typedef struct {
   double lambda_max;      /* in use */
   int last_degree;        /* Chebyshev degree K of the last exponential / K_max of the last average */
-  int cg_solves;          /* M1 solves since create */
+  int cg_solves;          /* M1 solves since create (or the last reset) */
   int cg_iters_max;       /* largest iteration count of one solve */
   double cg_iters_mean;   /* mean iterations per solve */
   int error_flags;        /* bit 0 NOCONV, bit 1 TIMEOUT, bit 2 NONFINITE */
+  int kernel_launches;    /* kernels enqueued by the last API call (graph replays: kernels in the graph) */
 } pavg_stats;
 
 /* Synchronises the device, then fills *out. */
@@ -149,6 +150,16 @@ int pavg_get_stats(pavg_ctx* ctx, pavg_stats* out);
 
 /* Clear the latched device error flags and the CG counters. */
 int pavg_reset_stats(pavg_ctx* ctx);
+
+/* Measurement aid: when enabled, every M1 CG launch (the dominant kernel) is
+ * bracketed by CUDA events on its stream, also inside captured graphs (plans
+ * captured with the other setting are re-captured).  Off by default. */
+int pavg_kernel_timing(pavg_ctx* ctx, int enable);
+
+/* Sum of the bracketed CG durations of the most recent API call and their
+ * count (host outputs; synchronises on the last event).  0 / 0 when timing
+ * was off. */
+int pavg_kernel_time(pavg_ctx* ctx, double* total_ms, int* launches);
 
 /* Readable message of the last failure (static storage owned by the context). */
 const char* pavg_last_error(const pavg_ctx* ctx);

@@ -18,6 +18,8 @@ using namespace pavg;
 
 namespace {
 
+using EventPair = std::pair<cudaEvent_t, cudaEvent_t>;
+
 struct AvgPlan {
   double T = 0;
   int M = 0;
@@ -25,6 +27,9 @@ struct AvgPlan {
   double* dA = nullptr;      // [M][K+1]  forward combine
   double* dB = nullptr;      // [K+1][M]  backward combine
   cudaGraphExec_t exec = nullptr;
+  bool timed = false;        // captured with CG event brackets
+  int launches = 0;          // kernels in the captured graph
+  std::vector<EventPair> pairs;   // CG event brackets inside the graph (owned)
 };
 
 }  // namespace
@@ -53,6 +58,13 @@ struct pavg_ctx {
   int last_degree = 0;
   bool use_graphs = true;
   std::string err;
+  // measurement: kernel launches and CG event brackets of the current / last call
+  int launches = 0, last_launches = 0;
+  bool timing = false;
+  AvgPlan* capturing = nullptr;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<EventPair> cur_pairs, last_pairs;
 };
 
 namespace {
@@ -83,10 +95,61 @@ cudaError_t upload(T** p, const std::vector<T>& v) {
 
 cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Counts one of this library's kernels and checks its launch.
+#define KL(call)          \
+  do {                    \
+    ++ctx->launches;      \
+    CK(call);             \
+  } while (0)
+
+void begin_call(pavg_ctx* ctx) {
+  ctx->launches = 0;
+  ctx->cur_pairs.clear();
+  ctx->ev_used = 0;
+}
+
+void end_call(pavg_ctx* ctx) {
+  ctx->last_launches = ctx->launches;
+  ctx->last_pairs = ctx->cur_pairs;
+}
+
+struct CallScope {
+  pavg_ctx* ctx;
+  explicit CallScope(pavg_ctx* c) : ctx(c) { begin_call(c); }
+  ~CallScope() { end_call(ctx); }
+};
+
+cudaEvent_t next_event(pavg_ctx* ctx) {
+  cudaEvent_t e = nullptr;
+  if (ctx->capturing) {  // owned by the plan: replays re-record it
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+  if (ctx->ev_used < ctx->ev_pool.size()) return ctx->ev_pool[ctx->ev_used++];
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  ctx->ev_pool.push_back(e);
+  ctx->ev_used = ctx->ev_pool.size();
+  return e;
+}
+
 // ---------------------------------------------------------------- building blocks
 // velocity part out_u = M1^{-1} b (scaled, plus add); eta part by the caller.
 int enq_cg(pavg_ctx* ctx, const double* b, double* out, double scale, const double* add, cudaStream_t st) {
-  CK(launch_cg(ctx->dm, ctx->cg, ctx->cgp, b, out, scale, add, st));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ctx->timing) {
+    e0 = next_event(ctx);
+    e1 = next_event(ctx);
+    if (!e0 || !e1) return set_err(ctx, PAVG_ERR_CUDA, "event creation failed");
+    // inside a stream capture an event becomes a graph record node only with
+    // cudaEventRecordExternal (a plain record is a capture dependency)
+    CK(cudaEventRecordWithFlags(e0, st, ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
+  }
+  KL(launch_cg(ctx->dm, ctx->cg, ctx->cgp, b, out, scale, add, st));
+  if (ctx->timing) {
+    CK(cudaEventRecordWithFlags(e1, st, ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
+    ctx->cur_pairs.emplace_back(e0, e1);
+    if (ctx->capturing) ctx->capturing->pairs.emplace_back(e0, e1);
+  }
   return PAVG_OK;
 }
 
@@ -95,7 +158,7 @@ int enq_mass_solve(pavg_ctx* ctx, const double* R, double* out, cudaStream_t st)
   const DeviceMesh& m = ctx->dm;
   int rc = enq_cg(ctx, R, out, 1.0, nullptr, st);
   if (rc) return rc;
-  CK(launch_m2inv(m, R + m.n_u, 0, out + m.n_u, 0, 1, st));
+  KL(launch_m2inv(m, R + m.n_u, 0, out + m.n_u, 0, 1, st));
   return PAVG_OK;
 }
 
@@ -108,7 +171,7 @@ int enq_step(pavg_ctx* ctx, const double* in, double s, const double* y, const d
   const int64_t nu = m.n_u;
   if (in) {
     CK(cudaMemsetAsync(ctx->ru, 0, sizeof(double) * 3 * m.E, st));
-    CK(launch_apply_K(m, in, s, ctx->p.g, ctx->p.H, y, y ? y + nu : nullptr, z ? z + nu : nullptr, ctx->ru,
+    KL(launch_apply_K(m, in, s, ctx->p.g, ctx->p.H, y, y ? y + nu : nullptr, z ? z + nu : nullptr, ctx->ru,
                       out + nu, st));
     return enq_cg(ctx, ctx->ru, out, 1.0, z, st);
   }
@@ -116,8 +179,8 @@ int enq_step(pavg_ctx* ctx, const double* in, double s, const double* y, const d
   if (!y) return set_err(ctx, PAVG_ERR_INVAL, "internal: empty recurrence step");
   int rc = enq_cg(ctx, y, out, 1.0, z, st);
   if (rc) return rc;
-  CK(launch_m2inv(m, y + nu, 0, out + nu, 0, 1, st));
-  if (z) CK(launch_lincomb(out + nu, 1.0, out + nu, 1.0, z + nu, 0.0, nullptr, m.n_eta, st));
+  KL(launch_m2inv(m, y + nu, 0, out + nu, 0, 1, st));
+  if (z) KL(launch_lincomb(out + nu, 1.0, out + nu, 1.0, z + nu, 0.0, nullptr, m.n_eta, st));
   return PAVG_OK;
 }
 
@@ -128,7 +191,7 @@ int enq_linear(pavg_ctx* ctx, const double* U, double* out, cudaStream_t st) {
 int enq_nonlinear(pavg_ctx* ctx, const double* U, double* out, double* scratch, cudaStream_t st) {
   const DeviceMesh& m = ctx->dm;
   CK(cudaMemsetAsync(scratch, 0, sizeof(double) * 3 * m.E, st));
-  CK(launch_nonlinear_rhs(m, U, scratch, 1, ctx->p.upwind_convention, st));
+  KL(launch_nonlinear_rhs(m, U, scratch, 1, ctx->p.upwind_convention, st));
   return enq_mass_solve(ctx, scratch, out, st);
 }
 
@@ -146,7 +209,7 @@ int enq_expL(pavg_ctx* ctx, double t, const double* U, double* out, cudaStream_t
   ctx->last_degree = K;
   const double sgn = t > 0 ? 1.0 : -1.0;
   double* acc = ctx->vec[3];
-  CK(launch_lincomb(acc, c[0], U, 0.0, nullptr, 0.0, nullptr, n, st));
+  KL(launch_lincomb(acc, c[0], U, 0.0, nullptr, 0.0, nullptr, n, st));
   const double* qm1 = nullptr;
   const double* qk = U;
   double* bufs[3] = {ctx->vec[0], ctx->vec[1], ctx->vec[2]};
@@ -154,7 +217,7 @@ int enq_expL(pavg_ctx* ctx, double t, const double* U, double* out, cudaStream_t
     double* qn = bufs[k % 3];
     int rc = enq_step(ctx, qk, (k == 0 ? 1.0 : 2.0) * sgn / ctx->lam, nullptr, qm1, qn, st);
     if (rc) return rc;
-    CK(launch_lincomb(acc, 1.0, acc, c[k + 1], qn, 0.0, nullptr, n, st));
+    KL(launch_lincomb(acc, 1.0, acc, c[k + 1], qn, 0.0, nullptr, n, st));
     qm1 = qk;
     qk = qn;
   }
@@ -162,13 +225,20 @@ int enq_expL(pavg_ctx* ctx, double t, const double* U, double* out, cudaStream_t
   return PAVG_OK;
 }
 
+void drop_graph(AvgPlan* pl) {
+  if (pl->exec) cudaGraphExecDestroy(pl->exec);
+  pl->exec = nullptr;
+  for (auto& pr : pl->pairs) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+  pl->pairs.clear();
+  pl->launches = 0;
+}
+
 int ensure_avg_workspace(pavg_ctx* ctx, int K, int M) {
   const int64_t n = ctx->dm.n;
   if (K <= ctx->Kcap && M <= ctx->Mcap) return PAVG_OK;
   // buffers move: drop every captured graph that refers to them
-  for (auto& kv : ctx->plans)
-    if (kv.second.exec) { cudaGraphExecDestroy(kv.second.exec); kv.second.exec = nullptr; }
   cudaDeviceSynchronize();
+  for (auto& kv : ctx->plans) drop_graph(&kv.second);
   int nk = std::max(K, ctx->Kcap), nm = std::max(M, ctx->Mcap);
   cudaFree(ctx->Q); cudaFree(ctx->Um); cudaFree(ctx->Rm);
   ctx->Q = ctx->Um = ctx->Rm = nullptr;
@@ -236,10 +306,10 @@ int enq_avg(pavg_ctx* ctx, const AvgPlan& pl, const double* U, double* out, cuda
                       k == 0 ? nullptr : Q + (int64_t)(k - 1) * n, Q + (int64_t)(k + 1) * n, st);
     if (rc) return rc;
   }
-  CK(launch_combine(pl.dA, M, K + 1, Q, n, ctx->Um, n, n, st));
+  KL(launch_combine(pl.dA, M, K + 1, Q, n, ctx->Um, n, n, st));
   CK(cudaMemset2DAsync(ctx->Rm, sizeof(double) * n, 0, sizeof(double) * 3 * m.E, M, st));
-  CK(launch_nonlinear_rhs(m, ctx->Um, ctx->Rm, M, ctx->p.upwind_convention, st));
-  CK(launch_combine(pl.dB, K + 1, M, ctx->Rm, n, Q, n, n, st));  // y_k overwrite Q_k
+  KL(launch_nonlinear_rhs(m, ctx->Um, ctx->Rm, M, ctx->p.upwind_convention, st));
+  KL(launch_combine(pl.dB, K + 1, M, ctx->Rm, n, Q, n, n, st));  // y_k overwrite Q_k
   double* b[3] = {ctx->vec[0], ctx->vec[1], ctx->vec[2]};
   const double* b1 = nullptr;  // b_{k+1}
   const double* b2 = nullptr;  // b_{k+2}
@@ -264,10 +334,16 @@ int run_avg(pavg_ctx* ctx, double T, int M, const double* U, double* out, cudaSt
   if (rc) return rc;
   const int64_t n = ctx->dm.n;
   if (!ctx->use_graphs) return enq_avg(ctx, *pl, U, out, st);
+  if (pl->exec && pl->timed != ctx->timing) drop_graph(pl);
   if (!pl->exec) {
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    ctx->capturing = pl;
+    ctx->launches = 0;
     int rc2 = enq_avg(ctx, *pl, ctx->io_in, ctx->io_out, ctx->cap_stream);
+    ctx->capturing = nullptr;
+    pl->launches = ctx->launches;
+    pl->timed = ctx->timing;
     cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
     if (rc2) { if (graph) cudaGraphDestroy(graph); return rc2; }
     if (e != cudaSuccess) return set_err(ctx, PAVG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
@@ -279,6 +355,8 @@ int run_avg(pavg_ctx* ctx, double T, int M, const double* U, double* out, cudaSt
   CK(cudaGraphLaunch(pl->exec, st));
   CK(cudaMemcpyAsync(out, ctx->io_out, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   ctx->last_degree = pl->K;
+  ctx->launches += pl->launches;
+  ctx->cur_pairs.insert(ctx->cur_pairs.end(), pl->pairs.begin(), pl->pairs.end());
   return PAVG_OK;
 }
 
@@ -338,7 +416,7 @@ int check_flags(pavg_ctx* ctx) {
 void free_ctx(pavg_ctx* c) {
   if (!c) return;
   for (auto& kv : c->plans) {
-    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    drop_graph(&kv.second);
     cudaFree(kv.second.dA);
     cudaFree(kv.second.dB);
   }
@@ -356,6 +434,7 @@ void free_ctx(pavg_ctx* c) {
   cudaFree(c->dpart);
   if (c->host_part) cudaFreeHost(c->host_part);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
   delete c;
 }
 
@@ -499,6 +578,7 @@ int pavg_lambda_max(const pavg_ctx* ctx, double* out) {
 
 int pavg_linear(pavg_ctx* ctx, const double* U, double* LU, int B, void* stream) {
   if (!ctx || !U || !LU || B < 0) return PAVG_ERR_INVAL;
+  CallScope scope_(ctx);
   const int64_t n = ctx->dm.n;
   for (int b = 0; b < B; ++b) {
     int rc = enq_linear(ctx, U + b * n, LU + b * n, S(stream));
@@ -509,6 +589,7 @@ int pavg_linear(pavg_ctx* ctx, const double* U, double* LU, int B, void* stream)
 
 int pavg_nonlinear(pavg_ctx* ctx, const double* U, double* NU, int B, void* stream) {
   if (!ctx || !U || !NU || B < 0) return PAVG_ERR_INVAL;
+  CallScope scope_(ctx);
   const int64_t n = ctx->dm.n;
   for (int b = 0; b < B; ++b) {
     int rc = enq_nonlinear(ctx, U + b * n, NU + b * n, ctx->vec[5], S(stream));
@@ -519,6 +600,7 @@ int pavg_nonlinear(pavg_ctx* ctx, const double* U, double* NU, int B, void* stre
 
 int pavg_expL_apply(pavg_ctx* ctx, double t, const double* U, double* out, int B, void* stream) {
   if (!ctx || !U || !out || B < 0 || !std::isfinite(t)) return PAVG_ERR_INVAL;
+  CallScope scope_(ctx);
   const int64_t n = ctx->dm.n;
   for (int b = 0; b < B; ++b) {
     int rc = enq_expL(ctx, t, U + b * n, out + b * n, S(stream));
@@ -529,11 +611,13 @@ int pavg_expL_apply(pavg_ctx* ctx, double t, const double* U, double* out, int B
 
 int pavg_averaged_rhs(pavg_ctx* ctx, double T, int M, const double* U, double* out, void* stream) {
   if (!ctx || !U || !out || M < 1 || !(T >= 0) || !std::isfinite(T)) return PAVG_ERR_INVAL;
+  CallScope scope_(ctx);
   return run_avg(ctx, T, M, U, out, S(stream));
 }
 
 int pavg_averaged_rhs_literal(pavg_ctx* ctx, double T, int M, const double* U, double* out, void* stream) {
   if (!ctx || !U || !out || M < 1 || !(T >= 0) || !std::isfinite(T)) return PAVG_ERR_INVAL;
+  CallScope scope_(ctx);
   cudaStream_t st = S(stream);
   const int64_t n = ctx->dm.n;
   if (T == 0.0) return enq_nonlinear(ctx, U, out, ctx->vec[5], st);
@@ -552,7 +636,7 @@ int pavg_averaged_rhs_literal(pavg_ctx* ctx, double T, int M, const double* U, d
     if (rc) return rc;
     rc = enq_expL(ctx, -s[m], term, V, st);
     if (rc) return rc;
-    CK(launch_lincomb(acc, 1.0, acc, w[m], V, 0.0, nullptr, n, st));
+    KL(launch_lincomb(acc, 1.0, acc, w[m], V, 0.0, nullptr, n, st));
   }
   CK(cudaMemcpyAsync(out, acc, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   return PAVG_OK;
@@ -565,6 +649,7 @@ int pavg_averaged_rhs_literal(pavg_ctx* ctx, double T, int M, const double* U, d
 // evaluated as E(dt)(U + dt/6 k1) + dt/6 [2 E(dt/2)(k2 + k3) + k4] (E is linear).
 int pavg_timestep(pavg_ctx* ctx, double dt, double T, int M, double* U, int nsteps, void* stream) {
   if (!ctx || !U || M < 1 || nsteps < 0 || !(T >= 0) || !std::isfinite(dt)) return PAVG_ERR_INVAL;
+  CallScope scope_(ctx);
   cudaStream_t st = S(stream);
   const int64_t n = ctx->dm.n;
   AvgPlan* pl = nullptr;
@@ -628,6 +713,27 @@ int pavg_get_stats(pavg_ctx* ctx, pavg_stats* out) {
   out->cg_iters_max = (int)st[2];
   out->cg_iters_mean = st[0] ? (double)st[1] / (double)st[0] : 0.0;
   out->error_flags = f;
+  out->kernel_launches = ctx->last_launches;
+  return PAVG_OK;
+}
+
+int pavg_kernel_timing(pavg_ctx* ctx, int enable) {
+  if (!ctx) return PAVG_ERR_INVAL;
+  ctx->timing = enable != 0;
+  return PAVG_OK;
+}
+
+int pavg_kernel_time(pavg_ctx* ctx, double* total_ms, int* launches) {
+  if (!ctx || !total_ms || !launches) return PAVG_ERR_INVAL;
+  double tot = 0.0;
+  for (auto& pr : ctx->last_pairs) {
+    CK(cudaEventSynchronize(pr.second));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, pr.first, pr.second));
+    tot += ms;
+  }
+  *total_ms = tot;
+  *launches = (int)ctx->last_pairs.size();
   return PAVG_OK;
 }
 

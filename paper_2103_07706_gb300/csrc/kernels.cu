@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg(DeviceMesh m, CgWork w, CgPar
   int it = 0;
   bool done = !(bb > 0.0);
   bool have_x = false;
-  if (!done && !(isfinite(alpha))) {
+  if (!isfinite(bb) || (!done && !isfinite(alpha))) {
     if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(w.flags, kFlagNonFinite);
     done = true;
   }

@@ -101,10 +101,10 @@ def harmonic_state(verts, cells, seed, lmax, eta_rms=100.0, g=9.80616, omega=7.2
 
     u = np.zeros(3 * E + 3 * F)
     # edge moments: -int_0^1 psi'(tau) p_j(tau) dtau by parts
-    tau, wt = _gl01(8)
+    tau, wt = _gl01(6)
     xlo, xhi = verts[edges[:, 0]], verts[edges[:, 1]]
     pts = xlo[:, None, :] + tau[None, :, None] * (xhi - xlo)[:, None, :]
-    ps = psi(pts)                                           # (E, 8)
+    ps = psi(pts)                                           # (E, 6)
     p0, p1 = psi(xlo), psi(xhi)
     u[0:3 * E:3] = -(p1 - p0)
     u[1:3 * E:3] = -p1 - p0 + 2.0 * ps @ wt
@@ -118,18 +118,18 @@ def harmonic_state(verts, cells, seed, lmax, eta_rms=100.0, g=9.80616, omega=7.2
     dirs = np.array([[-1.0, 1.0], [0.0, -1.0], [1.0, 0.0]])
     mom = np.zeros((F, 3))
     for i in range(3):
-        xi = starts[i][None, :] + tau[:, None] * dirs[i][None, :]          # (8, 2)
+        xi = starts[i][None, :] + tau[:, None] * dirs[i][None, :]          # (6, 2)
         x = a[:, None, :] + xi[None, :, 0:1] * J0[:, None, :] + xi[None, :, 1:2] * J1[:, None, :]
-        pv = psi(x)                                                         # (F, 8)
+        pv = psi(x)                                                         # (F, 6)
         d = dirs[i]
         q = np.stack([np.full(len(tau), d[0]),                              # d . (1, 0)
                       np.full(len(tau), d[1]),                              # d . (0, 1)
                       -xi[:, 1] * d[0] + xi[:, 0] * d[1]], axis=1)          # d . (-y, x)
         mom += pv @ (wt[:, None] * q)
     # -int psi_hat rot(q): rot = 0, 0, 2 ; collapsed Gauss rule on the triangle
-    s, ws = _gl01(8)
-    t, wt2 = _gl01(8)
-    xi = np.stack([np.repeat(s, 8), (np.outer(1.0 - s, t)).reshape(-1)], axis=1)
+    s, ws = _gl01(4)
+    t, wt2 = _gl01(4)
+    xi = np.stack([np.repeat(s, 4), (np.outer(1.0 - s, t)).reshape(-1)], axis=1)
     wtri = (np.outer(ws * (1.0 - s), wt2)).reshape(-1)
     x = a[:, None, :] + xi[None, :, 0:1] * J0[:, None, :] + xi[None, :, 1:2] * J1[:, None, :]
     mom[:, 2] -= 2.0 * psi(x) @ wtri

@@ -29,7 +29,7 @@ EXPORTED = [
     "pavg_default_params", "pavg_create", "pavg_destroy", "pavg_sizes", "pavg_mesh_export",
     "pavg_set_topography", "pavg_lambda_max", "pavg_linear", "pavg_nonlinear", "pavg_expL_apply",
     "pavg_averaged_rhs", "pavg_averaged_rhs_literal", "pavg_timestep", "pavg_sync", "pavg_get_stats",
-    "pavg_reset_stats", "pavg_last_error",
+    "pavg_reset_stats", "pavg_last_error", "pavg_kernel_timing", "pavg_kernel_time",
 ]
 
 
@@ -57,6 +57,7 @@ class Stats(ctypes.Structure):
         ("cg_iters_max", ctypes.c_int),
         ("cg_iters_mean", ctypes.c_double),
         ("error_flags", ctypes.c_int),
+        ("kernel_launches", ctypes.c_int),
     ]
 
 
@@ -90,6 +91,8 @@ def load(path=LIB_PATH):
         "pavg_get_stats": (I, [P, ctypes.POINTER(Stats)]),
         "pavg_reset_stats": (I, [P]),
         "pavg_last_error": (ctypes.c_char_p, [P]),
+        "pavg_kernel_timing": (I, [P, I]),
+        "pavg_kernel_time": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -185,6 +188,15 @@ class Model:
         s = Stats()
         self._check(self._lib.pavg_get_stats(self._h, ctypes.byref(s)))
         return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def kernel_timing(self, enable=True):
+        self._check(self._lib.pavg_kernel_timing(self._h, 1 if enable else 0))
+
+    def kernel_time(self):
+        """(total ms, launches) of the CG launches of the most recent call."""
+        ms, k = ctypes.c_double(), ctypes.c_int()
+        self._check(self._lib.pavg_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(k)))
+        return ms.value, k.value
 
     def reset_stats(self):
         self._check(self._lib.pavg_reset_stats(self._h))

@@ -1,0 +1,235 @@
+"""GPU (CUDA, through the C-ABI) versus the FP64 CPU oracle.
+
+Tolerance: relative L2 error per field in the finite element norms
+(||e_u||_M1 / ||u||_M1 and ||e_eta||_M2 / ||eta||_M2, the paper's error norms
+of Sec. 3 without the divergence part) of at most 1e-12 for the FP64 path.
+Both sides get the same seeded input and the same lambda_max.
+"""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+LAM = {0: 0.00036, 1: 0.00072, 2: 0.00142, 3: 0.00286, 4: 0.0057}
+_GPU = {}
+
+
+def gpu(r, **kw):
+    from paper_2103_07706_gb300 import pavg
+    kw.setdefault("lambda_max", LAM[r])
+    key = (r, tuple(sorted(kw.items())))
+    if key not in _GPU:
+        _GPU[key] = pavg.Model(r, **kw)
+    return _GPU[key]
+
+
+def orc(r, **kw):
+    from tests.conftest import oracle_model
+    kw.setdefault("lambda_max", LAM[r])
+    m = oracle_model(r, **kw)
+    m.lam = kw["lambda_max"]
+    return m
+
+
+def dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def state(m, seed=2103, lmax=8, eta_noise=0.0):
+    from paper_2103_07706_gb300.inputs import harmonic_state
+    U, _ = harmonic_state(m.mesh.verts, m.mesh.cells, seed, lmax)
+    if eta_noise:
+        U[m.n_u:] += eta_noise * np.random.default_rng(seed).standard_normal(m.n_eta)
+    return U
+
+
+def rel(m, got, want):
+    ops = m.ops
+    nu = ops.n_u
+    eu, ee = got[:nu] - want[:nu], got[nu:] - want[nu:]
+    wu, we = want[:nu], want[nu:]
+    return (np.sqrt(eu @ (ops.M1 @ eu) / (wu @ (ops.M1 @ wu))), np.sqrt(ee @ (ops.M2 @ ee) / (we @ (ops.M2 @ we))))
+
+
+def assert_close(m, got, want, tol=RTOL):
+    ru, re = rel(m, got, want)
+    assert ru <= tol and re <= tol, (ru, re)
+
+
+@pytest.mark.parametrize("r", [0, 1, 2, 3, 4])
+def test_mesh_matches_oracle(r):
+    g, o = gpu(r), orc(r)
+    v, c = g.mesh()
+    assert np.array_equal(c, o.mesh.cells)
+    assert np.abs(v - o.mesh.verts).max() <= 1e-15 * 6.37122e6
+    assert (g.n_u, g.n_eta) == (o.n_u, o.n_eta)
+
+
+@pytest.mark.parametrize("r", [2, 3, 4])
+def test_linear_parity(r):
+    g, o = gpu(r), orc(r)
+    U = np.random.default_rng(r).standard_normal(o.n) * 1e6
+    U[o.n_u:] *= 1e-4
+    assert_close(o, g.linear(dev(U)).cpu().numpy(), o.L(U))
+    g.sync()
+
+
+@pytest.mark.parametrize("r,upwind", [(2, 0), (3, 0), (4, 0), (3, 1)])
+def test_nonlinear_parity(r, upwind):
+    g, o = gpu(r, upwind_convention=upwind), orc(r, upwind=upwind)
+    U = state(o, eta_noise=20.0)
+    assert_close(o, g.nonlinear(dev(U)).cpu().numpy(), o.N(U))
+    g.sync()
+
+
+def test_nonlinear_with_topography():
+    g, o = gpu(3), orc(3)
+    b = 300.0 * np.random.default_rng(9).random(o.n_eta)
+    U = state(o)
+    g.set_topography(dev(b))
+    o.ops.set_topography(b)
+    try:
+        assert_close(o, g.nonlinear(dev(U)).cpu().numpy(), o.N(U))
+    finally:
+        g.set_topography(dev(np.zeros(o.n_eta)))
+        o.ops.set_topography(np.zeros(o.n_eta))
+
+
+@pytest.mark.parametrize("r,t", [(2, 900.0), (2, -3600.0), (3, 7200.0), (3, -450.0), (4, 3600.0)])
+def test_expL_parity(r, t):
+    g, o = gpu(r), orc(r)
+    U = state(o)
+    assert_close(o, g.expL(t, dev(U)).cpu().numpy(), o.expL(t, U))
+    g.sync()
+
+
+@pytest.mark.parametrize("r,T,M", [(2, 3600.0, 8), (3, 3600.0, 8), (3, 1800.0, 5), (4, 7200.0, 16)])
+def test_averaged_rhs_parity(r, T, M):
+    """Shared-basis GPU form versus the oracle's literal per-shift sum."""
+    g, o = gpu(r), orc(r)
+    U = state(o, eta_noise=5.0)
+    want = o.averaged_rhs(T, M, U)
+    assert_close(o, g.averaged_rhs(T, M, dev(U)).cpu().numpy(), want)
+    assert_close(o, g.averaged_rhs_literal(T, M, dev(U)).cpu().numpy(), want)
+    g.sync()
+
+
+def test_averaged_rhs_closed_rule_parity():
+    g = gpu(2, quad_rule=1)
+    o = orc(2, quad_rule=1)
+    U = state(o)
+    assert_close(o, g.averaged_rhs(3600.0, 7, dev(U)).cpu().numpy(), o.averaged_rhs(3600.0, 7, U))
+
+
+def test_timestep_parity_refinement3_ten_steps():
+    """Small configuration: refinement 3, M = 8, T = 1 h, 10 steps of 900 s."""
+    g, o = gpu(3), orc(3)
+    U = state(o)
+    want = o.timestep(900.0, 3600.0, 8, U, 10)
+    Ud = dev(U)
+    g.timestep(900.0, 3600.0, 8, Ud, 10)
+    assert_close(o, Ud.cpu().numpy(), want)
+    g.sync()
+
+
+def test_edge_cases():
+    g, o = gpu(2), orc(2)
+    U = state(o)
+    Ud = dev(U)
+    N = g.nonlinear(Ud).cpu().numpy()
+    # T = 0 is N itself; one midpoint shift is s = 0
+    assert np.array_equal(g.averaged_rhs(0.0, 8, Ud).cpu().numpy(), N)
+    assert_close(o, g.averaged_rhs(3600.0, 1, Ud).cpu().numpy(), N, 1e-15)
+    # rest state: zero average
+    rest = np.zeros(o.n)
+    rest[o.n_u:] = 4.0
+    assert np.abs(g.averaged_rhs(3600.0, 4, dev(rest)).cpu().numpy()).max() < 1e-13
+    # t = 0 exponential copies
+    assert np.array_equal(g.expL(0.0, Ud).cpu().numpy(), U)
+    # batches equal single calls
+    B = np.stack([U, 2 * U, -U]).reshape(-1)
+    Lb = g.linear(dev(B)).cpu().numpy().reshape(3, -1)
+    L1 = g.linear(Ud).cpu().numpy()
+    assert np.array_equal(Lb[0], L1)
+    E = g.expL(600.0, dev(B)).cpu().numpy().reshape(3, -1)
+    assert np.array_equal(E[2], -E[0]) or np.abs(E[2] + E[0]).max() <= 1e-15 * np.abs(E[0]).max()
+    # mass conservation of the average
+    S = g.averaged_rhs(3600.0, 8, Ud).cpu().numpy()
+    assert abs(o.ops.mass(S)) <= 1e-14 * np.abs(o.ops.M2 @ S[o.n_u:]).sum()
+    g.sync()
+
+
+def test_determinism_and_graph_replay():
+    g, o = gpu(3), orc(3)
+    U = dev(state(o))
+    a = g.averaged_rhs(3600.0, 8, U).cpu().numpy()
+    b = g.averaged_rhs(3600.0, 8, U).cpu().numpy()
+    assert np.array_equal(a, b)
+    g.sync()
+
+
+def test_kernel_timing_and_launch_count():
+    g, o = gpu(2), orc(2)
+    U = dev(state(o))
+    g.kernel_timing(True)
+    try:
+        g.averaged_rhs(1800.0, 4, U)
+        ms, k = g.kernel_time()
+        st = g.stats()
+        assert k > 0 and ms > 0.0
+        assert st["kernel_launches"] >= k
+    finally:
+        g.kernel_timing(False)
+
+
+def test_error_paths_are_reported():
+    """Host-induced failures: an iteration cap too small, a NaN in the input."""
+    from paper_2103_07706_gb300 import pavg
+    g = pavg.Model(2, lambda_max=LAM[2], cg_maxit=2)
+    o = orc(2)
+    U = dev(state(o))
+    g.linear(U)
+    with pytest.raises(pavg.PavgError) as e:
+        g.sync()
+    assert e.value.code == -4
+    g.close()
+    g = pavg.Model(2, lambda_max=LAM[2])
+    bad = state(o)
+    bad[5] = np.nan
+    g.linear(dev(bad))
+    with pytest.raises(pavg.PavgError) as e:
+        g.sync()
+    assert e.value.code == -5
+    g.close()
+
+
+def test_full_size_properties():
+    """Refinement 6, M = 64, T = 1 h (the benchmark configuration): properties
+    that hold at any size: shared-basis equals the literal sum, mass is
+    conserved, T -> 0 recovers N at second order, no device error."""
+    import torch
+    from paper_2103_07706_gb300 import pavg
+    from paper_2103_07706_gb300.inputs import harmonic_state
+    g = pavg.Model(6, lambda_max=0.02335)
+    v, c = g.mesh()
+    U, _ = harmonic_state(v, c, 2103, 16)
+    Ud = dev(U)
+    S = g.averaged_rhs(3600.0, 64, Ud)
+    L = g.averaged_rhs_literal(3600.0, 64, Ud)
+    g.sync()
+    S, L = S.cpu().numpy(), L.cpu().numpy()
+    assert np.isfinite(S).all()
+    nu = g.n_u
+    du = np.linalg.norm(S[:nu] - L[:nu]) / np.linalg.norm(L[:nu])
+    de = np.linalg.norm(S[nu:] - L[nu:]) / np.linalg.norm(L[nu:])
+    assert du <= RTOL and de <= RTOL, (du, de)
+    N = g.nonlinear(Ud).cpu().numpy()
+    d1 = np.linalg.norm(g.averaged_rhs(20.0, 2, Ud).cpu().numpy() - N)
+    d2 = np.linalg.norm(g.averaged_rhs(2.0, 2, Ud).cpu().numpy() - N)
+    assert 60.0 < d1 / d2 < 140.0
+    assert g.stats()["error_flags"] == 0
+    del torch
+    g.close()
