@@ -16,56 +16,10 @@
 
 using namespace pavg;
 
-namespace {
+#include "context.h"
 
-using EventPair = std::pair<cudaEvent_t, cudaEvent_t>;
-
-struct AvgPlan {
-  double T = 0;
-  int M = 0;
-  int K = 0;                 // K_max over shifts
-  double* dA = nullptr;      // [M][K+1]  forward combine
-  double* dB = nullptr;      // [K+1][M]  backward combine
-  cudaGraphExec_t exec = nullptr;
-  bool timed = false;        // captured with CG event brackets
-  int launches = 0;          // kernels in the captured graph
-  std::vector<EventPair> pairs;   // CG event brackets inside the graph (owned)
-};
-
-}  // namespace
-
-struct pavg_ctx {
-  pavg_params p{};
-  Mesh mesh;
-  DeviceMesh dm;
-  CgWork cg;
-  CgParams cgp{};
-  double lam = 0;
-  int device = 0;
-  // scratch
-  double* ru = nullptr;         // [n_u] assembled velocity rhs
-  double* vec[6] = {};          // [n] general vectors
-  double* io_in = nullptr;      // [n] graph input
-  double* io_out = nullptr;     // [n] graph output
-  double* Q = nullptr;          // [(Kcap+1)][n] Chebyshev basis / backward coefficient vectors
-  double* Um = nullptr;         // [Mcap][n] shifted states
-  double* Rm = nullptr;         // [Mcap][n] weak-form N of the shifted states
-  int Kcap = -1, Mcap = 0;
-  double* host_part = nullptr;
-  double* dpart = nullptr;
-  cudaStream_t cap_stream = nullptr;
-  std::map<std::pair<double, int>, AvgPlan> plans;
-  int last_degree = 0;
-  bool use_graphs = true;
-  std::string err;
-  // measurement: kernel launches and CG event brackets of the current / last call
-  int launches = 0, last_launches = 0;
-  bool timing = false;
-  AvgPlan* capturing = nullptr;
-  std::vector<cudaEvent_t> ev_pool;
-  size_t ev_used = 0;
-  std::vector<EventPair> cur_pairs, last_pairs;
-};
+using pavg_detail::AvgPlan;
+using pavg_detail::EventPair;
 
 namespace {
 
