@@ -132,6 +132,23 @@ int pavg_averaged_rhs_literal(pavg_ctx* ctx, double T, int M, const double* U, d
 int pavg_timestep(pavg_ctx* ctx, double dt, double T, int M, double* U_inout, int nsteps,
                   void* stream);
 
+/* LU = L U for ONE state (device, n doubles each; may not alias), the same
+ * result as pavg_linear with B = 1, computed without any device allocation:
+ * all scratch (assembled right-hand side, conjugate-gradient work vectors)
+ * comes from a file-scope device array of the library sized for at most
+ * 153600 velocity DOFs (refinement <= 5, about 12.5 MB, held by every GPU that
+ * loads the library until the process exits).  It is for callers that cannot
+ * call cudaMalloc where they apply L (inside a global-mode stream capture,
+ * real-time loops, capped external memory pools).  The paper has no
+ * counterpart: this is an interface convenience.
+ * Errors: INVAL for a null argument, a mesh larger than the limit or when the
+ * context's device is not current; CUDA when the set-up lookup fails.  The
+ * first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the one array, so calls that overlap on the GPU race;
+ * serialise them (one stream, or events). */
+int pavg_linear_noalloc(pavg_ctx* ctx, const double* U, double* LU, void* stream);
+
 /* Wait for the context's work on `stream` and report latched device errors. */
 int pavg_sync(pavg_ctx* ctx, void* stream);
 

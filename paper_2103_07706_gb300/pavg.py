@@ -29,7 +29,7 @@ EXPORTED = [
     "pavg_default_params", "pavg_create", "pavg_destroy", "pavg_sizes", "pavg_mesh_export",
     "pavg_set_topography", "pavg_lambda_max", "pavg_linear", "pavg_nonlinear", "pavg_expL_apply",
     "pavg_averaged_rhs", "pavg_averaged_rhs_literal", "pavg_timestep", "pavg_sync", "pavg_get_stats",
-    "pavg_reset_stats", "pavg_last_error", "pavg_kernel_timing", "pavg_kernel_time",
+    "pavg_reset_stats", "pavg_last_error", "pavg_kernel_timing", "pavg_kernel_time", "pavg_linear_noalloc",
 ]
 
 
@@ -93,6 +93,7 @@ def load(path=LIB_PATH):
         "pavg_last_error": (ctypes.c_char_p, [P]),
         "pavg_kernel_timing": (I, [P, I]),
         "pavg_kernel_time": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I)]),
+        "pavg_linear_noalloc": (I, [P, P, P, V]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -220,6 +221,13 @@ class Model:
         out = self._out(U, out)
         B = self._batch(U)
         self._check(self._lib.pavg_linear(self._h, _ptr(U, self.n, B), _ptr(out, self.n, B), B, _stream()))
+        return out
+
+    def linear_noalloc(self, U, out=None):
+        """L U for one state through the entry point that allocates no device
+        memory (scratch in a static device array; refinement <= 5)."""
+        out = self._out(U, out)
+        self._check(self._lib.pavg_linear_noalloc(self._h, _ptr(U, self.n), _ptr(out, self.n), _stream()))
         return out
 
     def nonlinear(self, U, out=None):
