@@ -58,6 +58,8 @@ extern "C" {
 #define PAVG_QUAD_CLOSED 1       /* odd M = 2N+1, s_k = k (T/2) / N, k=-N..N */
 #define PAVG_UPWIND_STANDARD 0   /* u~, (eta-b)~ from the side the flow leaves */
 #define PAVG_UPWIND_AS_PRINTED 1 /* u~ = u+ when u.n+ < 0, as printed in Sec. 2.5 */
+#define PAVG_SOLVER_MIXED 0      /* M1 solves: FP32 block-Jacobi CG refined by FP64 residuals */
+#define PAVG_SOLVER_FP64 1       /* M1 solves: FP64 Jacobi CG */
 
 typedef struct pavg_ctx pavg_ctx; /* opaque, library-owned */
 
@@ -74,11 +76,14 @@ typedef struct {
   double lambda_max;      /* |lambda_max| of L [1/s]; 0 -> estimate by power iteration at create */
   int quad_rule;          /* PAVG_QUAD_MIDPOINT or PAVG_QUAD_CLOSED */
   int upwind_convention;  /* PAVG_UPWIND_STANDARD or PAVG_UPWIND_AS_PRINTED */
+  int solver;             /* PAVG_SOLVER_MIXED (default) or PAVG_SOLVER_FP64; both reach cg_rtol
+                             in FP64; cg_maxit caps the iterations of one solve (FP64) or of one
+                             refinement sweep (mixed, at most 8 sweeps) */
 } pavg_params;
 
 /* Fill `p` with the defaults: r = 3, R = 6.37122e6, Omega = 7.292e-5,
  * g = 9.80616, H = 5000, cheb_tol = 1e-6, cg_rtol = 1e-14, cg_maxit = 400,
- * lambda_max = 0, midpoint rule, standard upwinding. */
+ * lambda_max = 0, midpoint rule, standard upwinding, mixed solver. */
 int pavg_default_params(pavg_params* p);
 
 /* Build the mesh and FE data (Sec. 2.5, Sec. 3) on the current CUDA device and
@@ -157,9 +162,10 @@ typedef struct {
   int last_degree;        /* Chebyshev degree K of the last exponential / K_max of the last average */
   int cg_solves;          /* M1 solves since create (or the last reset) */
   int cg_iters_max;       /* largest iteration count of one solve */
-  double cg_iters_mean;   /* mean iterations per solve */
+  double cg_iters_mean;   /* mean CG iterations per solve (mixed solver: FP32 iterations, all sweeps) */
   int error_flags;        /* bit 0 NOCONV, bit 1 TIMEOUT, bit 2 NONFINITE */
   int kernel_launches;    /* kernels enqueued by the last API call (graph replays: kernels in the graph) */
+  double cg_sweeps_mean;  /* FP64 refinement sweeps per solve (mixed solver; 0 for FP64 CG) */
 } pavg_stats;
 
 /* Synchronises the device, then fills *out. */

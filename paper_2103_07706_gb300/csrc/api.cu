@@ -98,7 +98,10 @@ int enq_cg(pavg_ctx* ctx, const double* b, double* out, double scale, const doub
     // cudaEventRecordExternal (a plain record is a capture dependency)
     CK(cudaEventRecordWithFlags(e0, st, ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
   }
-  KL(launch_cg(ctx->dm, ctx->cg, ctx->cgp, b, out, scale, add, st));
+  if (ctx->p.solver == PAVG_SOLVER_MIXED)
+    KL(launch_cg_ir(ctx->dm, ctx->cgi, ctx->cgip, b, out, scale, add, st));
+  else
+    KL(launch_cg(ctx->dm, ctx->cg, ctx->cgp, b, out, scale, add, st));
   if (ctx->timing) {
     CK(cudaEventRecordWithFlags(e1, st, ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
     ctx->cur_pairs.emplace_back(e0, e1);
@@ -382,6 +385,11 @@ void free_ctx(pavg_ctx* c) {
   cudaFree(w.x); cudaFree(w.r[0]); cudaFree(w.r[1]); cudaFree(w.s[0]); cudaFree(w.s[1]);
   cudaFree(w.w[0]); cudaFree(w.w[1]); cudaFree(w.w[2]); cudaFree(w.p); cudaFree(w.partial);
   cudaFree(w.bar); cudaFree(w.flags); cudaFree(w.stats);
+  CgIrWork& wi = c->cgi;
+  cudaFree(wi.x[0]); cudaFree(wi.x[1]); cudaFree(wi.ax); cudaFree(wi.r64); cudaFree(wi.fbuf);
+  cudaFree(wi.partial); cudaFree(wi.partial_f);
+  cudaFree(wi.bar); cudaFree(wi.scal);
+  cudaFree(m.M1f); cudaFree(m.Pinv); cudaFree(m.M1p); cudaFree(m.tri);
   cudaFree(c->ru);
   for (auto* v : c->vec) cudaFree(v);
   cudaFree(c->io_in); cudaFree(c->io_out); cudaFree(c->Q); cudaFree(c->Um); cudaFree(c->Rm);
@@ -396,7 +404,8 @@ bool valid_params(const pavg_params* p) {
   return p && p->refinement >= 0 && p->refinement <= 8 && p->radius > 0 && p->g > 0 && p->H > 0 &&
          p->cheb_tol > 0 && p->cg_rtol > 0 && p->cg_maxit > 0 && p->lambda_max >= 0 && std::isfinite(p->omega) &&
          (p->quad_rule == PAVG_QUAD_MIDPOINT || p->quad_rule == PAVG_QUAD_CLOSED) &&
-         (p->upwind_convention == PAVG_UPWIND_STANDARD || p->upwind_convention == PAVG_UPWIND_AS_PRINTED);
+         (p->upwind_convention == PAVG_UPWIND_STANDARD || p->upwind_convention == PAVG_UPWIND_AS_PRINTED) &&
+         (p->solver == PAVG_SOLVER_MIXED || p->solver == PAVG_SOLVER_FP64);
 }
 
 }  // namespace
@@ -416,6 +425,7 @@ int pavg_default_params(pavg_params* p) {
   p->lambda_max = 0.0;
   p->quad_rule = PAVG_QUAD_MIDPOINT;
   p->upwind_convention = PAVG_UPWIND_STANDARD;
+  p->solver = PAVG_SOLVER_MIXED;
   return PAVG_OK;
 }
 
@@ -427,6 +437,10 @@ int pavg_create(const pavg_params* p, pavg_ctx** out) {
   ctx->p = *p;
   ctx->cgp.rtol = p->cg_rtol;
   ctx->cgp.maxit = p->cg_maxit;
+  ctx->cgip.rtol = p->cg_rtol;
+  ctx->cgip.max_sweeps = 8;
+  ctx->cgip.inner_rtol = 1e-5f;
+  ctx->cgip.max_inner = p->cg_maxit < 200 ? p->cg_maxit : 200;
   int rc = PAVG_OK;
   try {
     cudaGetDevice(&ctx->device);
@@ -448,6 +462,7 @@ int pavg_create(const pavg_params* p, pavg_ctx** out) {
               upload(&m.edge_lpos, ms.edge_lpos) == cudaSuccess && upload(&m.M1, hc.M1) == cudaSuccess &&
               upload(&m.C, hc.C) == cudaSuccess && upload(&m.det, hc.det) == cudaSuccess &&
               upload(&m.G, hc.G) == cudaSuccess && upload(&m.dinv, hc.dinv) == cudaSuccess &&
+              upload(&m.Pinv, hc.Pinv) == cudaSuccess && upload(&m.tri, hc.tri) == cudaSuccess &&
               dalloc(&m.topo, m.n_eta) == cudaSuccess;
     if (!ok) { rc = set_err(ctx, PAVG_ERR_NOMEM, "device upload failed"); throw 0; }
     cudaMemset(m.topo, 0, sizeof(double) * m.n_eta);
@@ -458,15 +473,38 @@ int pavg_create(const pavg_params* p, pavg_ctx** out) {
          dalloc(&w.s[1], m.n_u) == cudaSuccess && dalloc(&w.w[0], m.n_u) == cudaSuccess &&
          dalloc(&w.w[1], m.n_u) == cudaSuccess && dalloc(&w.w[2], m.n_u) == cudaSuccess &&
          dalloc(&w.p, m.n_u) == cudaSuccess && dalloc(&w.partial, 6 * (size_t)w.nblocks) == cudaSuccess &&
-         dalloc(&w.bar, 2) == cudaSuccess && dalloc(&w.flags, 1) == cudaSuccess && dalloc(&w.stats, 3) == cudaSuccess &&
+         dalloc(&w.bar, 2) == cudaSuccess && dalloc(&w.flags, 1) == cudaSuccess && dalloc(&w.stats, 4) == cudaSuccess &&
          dalloc(&ctx->ru, m.n_u) == cudaSuccess && dalloc(&ctx->io_in, m.n) == cudaSuccess &&
          dalloc(&ctx->io_out, m.n) == cudaSuccess && dalloc(&ctx->dpart, 4096) == cudaSuccess &&
          cudaMallocHost((void**)&ctx->host_part, sizeof(double) * 4096) == cudaSuccess;
     for (auto*& v : ctx->vec) ok = ok && dalloc(&v, m.n) == cudaSuccess;
+    CgIrWork& wi = ctx->cgi;
+    ok = ok && cg_ir_configure(m.F, &wi) == cudaSuccess;
+    // FP32 element matrices: packed for the shared-memory path, row blocks when streamed
+    if (ok) ok = wi.smem > 0 ? upload(&m.M1p, hc.M1p) == cudaSuccess : upload(&m.M1f, hc.M1f) == cudaSuccess;
+    ok = ok && dalloc(&wi.x[0], m.n_u) == cudaSuccess && dalloc(&wi.x[1], m.n_u) == cudaSuccess &&
+         dalloc(&wi.ax, m.n_u) == cudaSuccess && dalloc(&wi.r64, m.n_u) == cudaSuccess &&
+         dalloc(&wi.fbuf, 9 * 4 * (size_t)(m.E + m.F)) == cudaSuccess &&
+         dalloc(&wi.partial, 3 * (size_t)wi.nblocks) == cudaSuccess &&
+         dalloc(&wi.partial_f, 3 * (size_t)wi.nblocks) == cudaSuccess &&
+         dalloc(&wi.scal, 8) == cudaSuccess &&
+         dalloc(&wi.bar, 2) == cudaSuccess;
+    wi.flags = w.flags;
+    wi.stats = w.stats;
+    if (ok) {
+      float* fb = wi.fbuf;
+      const int64_t s4 = 4 * (m.E + m.F);
+      wi.xf = fb;
+      wi.rf[0] = fb + 1 * s4; wi.rf[1] = fb + 2 * s4;
+      wi.sf[0] = fb + 3 * s4; wi.sf[1] = fb + 4 * s4;
+      wi.wf[0] = fb + 5 * s4; wi.wf[1] = fb + 6 * s4; wi.wf[2] = fb + 7 * s4;
+      wi.pf = fb + 8 * s4;
+    }
     if (!ok) { rc = set_err(ctx, PAVG_ERR_NOMEM, "workspace allocation failed"); throw 0; }
     cudaMemset(w.bar, 0, 2 * sizeof(unsigned));
     cudaMemset(w.flags, 0, sizeof(int));
-    cudaMemset(w.stats, 0, 3 * sizeof(unsigned long long));
+    cudaMemset(w.stats, 0, 4 * sizeof(unsigned long long));
+    cudaMemset(ctx->cgi.bar, 0, 2 * sizeof(unsigned));
     if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
       rc = set_err(ctx, PAVG_ERR_CUDA, "stream creation failed");
       throw 0;
@@ -657,7 +695,7 @@ int pavg_sync(pavg_ctx* ctx, void* stream) {
 int pavg_get_stats(pavg_ctx* ctx, pavg_stats* out) {
   if (!ctx || !out) return PAVG_ERR_INVAL;
   CK(cudaDeviceSynchronize());
-  unsigned long long st[3];
+  unsigned long long st[4];
   int f = 0;
   CK(cudaMemcpy(st, ctx->cg.stats, sizeof(st), cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(&f, ctx->cg.flags, sizeof(int), cudaMemcpyDeviceToHost));
@@ -666,6 +704,7 @@ int pavg_get_stats(pavg_ctx* ctx, pavg_stats* out) {
   out->cg_solves = (int)st[0];
   out->cg_iters_max = (int)st[2];
   out->cg_iters_mean = st[0] ? (double)st[1] / (double)st[0] : 0.0;
+  out->cg_sweeps_mean = st[0] ? (double)st[3] / (double)st[0] : 0.0;
   out->error_flags = f;
   out->kernel_launches = ctx->last_launches;
   return PAVG_OK;
@@ -694,7 +733,7 @@ int pavg_kernel_time(pavg_ctx* ctx, double* total_ms, int* launches) {
 int pavg_reset_stats(pavg_ctx* ctx) {
   if (!ctx) return PAVG_ERR_INVAL;
   CK(cudaDeviceSynchronize());
-  CK(cudaMemset(ctx->cg.stats, 0, 3 * sizeof(unsigned long long)));
+  CK(cudaMemset(ctx->cg.stats, 0, 4 * sizeof(unsigned long long)));
   CK(cudaMemset(ctx->cg.flags, 0, sizeof(int)));
   return PAVG_OK;
 }

@@ -36,6 +36,8 @@ struct pavg_ctx {
   pavg::DeviceMesh dm;
   pavg::CgWork cg;
   pavg::CgParams cgp{};
+  pavg::CgIrWork cgi;
+  pavg::CgIrParams cgip{};
   double lam = 0;
   int device = 0;
   // scratch

@@ -24,6 +24,10 @@ struct DeviceMesh {
   double* G = nullptr;              // [3][F]
   double* dinv = nullptr;           // [n_u]
   double* topo = nullptr;           // [n_eta] topography b
+  float* M1f = nullptr;             // [36][F][4] M1 element matrices in FP32, row blocks of 3 rows per triple
+  float* Pinv = nullptr;            // [E + F][8] inverses of the 3x3 diagonal blocks of M1, FP32, padded
+  float* M1p = nullptr;             // [78][F] packed M1 in FP32 (loaded into shared memory), or null
+  int32_t* tri = nullptr;           // [F][4] DOF triple of (cell, q) with the owner flag in bit 31
 };
 
 // Scratch of the persistent CG solver.
@@ -45,6 +49,47 @@ struct CgParams {
   double rtol;
   int maxit;
 };
+
+// Scratch of the mixed-precision solver: FP32 conjugate gradients on M1 with a
+// 3x3 block-Jacobi preconditioner, refined by FP64 residuals b - M1 x.
+struct CgIrWork {
+  double* x[2] = {nullptr, nullptr};   // FP64 iterate (ping-pong between sweeps)
+  double* ax = nullptr;                // FP64 M1 x (assembled; edge part zero between uses)
+  double* r64 = nullptr;               // FP64 residual
+  // FP32 vectors, one allocation of 9 slots of T = E + F triples x 4 floats
+  // (each DOF triple padded to 16 bytes), addressed by 32-bit offsets:
+  // slot 0 correction x, 1-2 residual r, 3-4 s, 5-7 w (three rotating), 8 p
+  float* fbuf = nullptr;
+  float* xf = nullptr;                 // views into fbuf
+  float* rf[2] = {nullptr, nullptr};
+  float* sf[2] = {nullptr, nullptr};
+  float* wf[3] = {nullptr, nullptr, nullptr};
+  float* pf = nullptr;
+  double* partial = nullptr;           // [3][nblocks] per-block partial sums (FP64 phases)
+  float* partial_f = nullptr;          // [3][nblocks] per-block partial sums (FP32 phases)
+  double* scal = nullptr;              // [2][4] published global sums (alternating)
+  unsigned* bar = nullptr;             // [2]
+  int* flags = nullptr;
+  unsigned long long* stats = nullptr; // [0] solves, [1] inner iterations, [2] max per solve, [3] sweeps
+  int nblocks = 0;
+  int passes = 0;        // cells per block / 64, rounded up
+  size_t smem = 0;       // dynamic shared memory: resident FP32 element matrices (0: streamed)
+};
+
+struct CgIrParams {
+  double rtol;        // FP64 relative residual target
+  int max_sweeps;     // FP64 refinement sweeps
+  float inner_rtol;   // FP32 inner reduction per sweep
+  int max_inner;      // FP32 iterations per sweep
+};
+
+// Chooses the grid and whether the FP32 element matrices stay resident in
+// shared memory for the whole solve (fills w->nblocks, passes, smem).
+cudaError_t cg_ir_configure(int64_t F, CgIrWork* w);
+
+// out_u = scale_x * M1^{-1} b + add, mixed precision, FP64-accurate.
+cudaError_t launch_cg_ir(const DeviceMesh& m, const CgIrWork& w, const CgIrParams& cp, const double* b,
+                         double* out, double scale_x, const double* add, cudaStream_t st);
 
 // Upload constant tables (reference element data) to the current device.
 cudaError_t upload_tables(const ConstTables& t);

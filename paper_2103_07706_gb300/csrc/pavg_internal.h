@@ -70,6 +70,11 @@ struct HostCellData {
   std::vector<double> det;     // [F]
   std::vector<double> G;       // [3][F] metric J^T J: G00, G01, G11
   std::vector<double> dinv;    // [n_u] 1 / diag(M1)
+  std::vector<float> M1f;      // [36][F][4] M1 rounded to FP32, row blocks: entry (e, c, q) is
+                               // row 3q + e / 12, column e % 12 of cell c's signed 12 x 12 matrix
+  std::vector<float> Pinv;     // [E + F][8] inverses of the 3x3 diagonal blocks of M1 (00,01,02,11,12,22,-,-)
+  std::vector<float> M1p;      // [78][F] M1 rounded to FP32, packed upper triangle (shared-memory path)
+  std::vector<int32_t> tri;    // [F][4] DOF triple of (cell, q) | owner bit 31 (q = 0..2 edges, 3 interior)
 };
 void build_cell_data(const Mesh& m, const RefElement& el, double omega, HostCellData* out,
                      ConstTables* tab);

@@ -424,6 +424,51 @@ void build_cell_data(const Mesh& m, const RefElement& el, double omega, HostCell
   out->dinv.resize(n_u);
   for (int64_t k = 0; k < n_u; ++k) out->dinv[k] = 1.0 / diag[k];
 
+  // FP32 copy of the element matrices and the 3x3 diagonal blocks of the
+  // assembled M1 (each edge's three moments, each cell's three interior
+  // DOFs: triple t = dof / 3), inverted in FP64 and stored in FP32.
+  out->M1f.resize((size_t)144 * F);
+  for (int64_t c = 0; c < F; ++c)
+    for (int q = 0; q < 4; ++q)
+      for (int e = 0; e < 36; ++e) {
+        int i = 3 * q + e / 12, j = e % 12;
+        int pk = i <= j ? packed_sym(i, j) : packed_sym(j, i);
+        out->M1f[((size_t)e * F + c) * 4 + q] = (float)out->M1[(int64_t)pk * F + c];
+      }
+  out->M1p.resize(out->M1.size());
+  for (size_t k = 0; k < out->M1.size(); ++k) out->M1p[k] = (float)out->M1[k];
+  out->tri.resize((size_t)4 * F);
+  for (int64_t c = 0; c < F; ++c) {
+    for (int q = 0; q < 3; ++q) {
+      uint32_t t = (uint32_t)m.cell_edges[3 * c + q];
+      if ((m.cell_aligned[c] >> q) & 1u) t |= 0x80000000u;
+      out->tri[4 * c + q] = (int32_t)t;
+    }
+    out->tri[4 * c + 3] = (int32_t)((uint32_t)(E + c) | 0x80000000u);
+  }
+  const int64_t T = E + F;
+  std::vector<double> blk(9 * T, 0.0);
+  for (int64_t c = 0; c < F; ++c)
+    for (int q = 0; q < 4; ++q) {
+      int64_t t = q < 3 ? m.cell_edges[3 * c + q] : E + c;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          int i = 3 * q + a, j = 3 * q + b;
+          int pk = i <= j ? packed_sym(i, j) : packed_sym(j, i);
+          blk[9 * t + 3 * a + b] += out->M1[(int64_t)pk * F + c];
+        }
+    }
+  out->Pinv.assign(8 * T, 0.0f);
+  for (int64_t t = 0; t < T; ++t) {
+    double inv[9];
+    if (!invert(3, &blk[9 * t], inv)) throw std::runtime_error("singular diagonal block of M1");
+    const int idx[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    for (int k = 0; k < 6; ++k) {
+      double v = 0.5 * (inv[3 * idx[k][0] + idx[k][1]] + inv[3 * idx[k][1] + idx[k][0]]);
+      out->Pinv[8 * t + k] = (float)v;
+    }
+  }
+
   // tables for the nonlinear kernels
   double cx[7], cy[7], cw[7];
   triangle_deg5(cx, cy, cw);

@@ -19,6 +19,8 @@ PAVG_QUAD_MIDPOINT = 0
 PAVG_QUAD_CLOSED = 1
 PAVG_UPWIND_STANDARD = 0
 PAVG_UPWIND_AS_PRINTED = 1
+PAVG_SOLVER_MIXED = 0
+PAVG_SOLVER_FP64 = 1
 
 ERRORS = {
     -1: "PAVG_ERR_INVAL", -2: "PAVG_ERR_NOMEM", -3: "PAVG_ERR_CUDA", -4: "PAVG_ERR_NOCONV",
@@ -46,6 +48,7 @@ class Params(ctypes.Structure):
         ("lambda_max", ctypes.c_double),
         ("quad_rule", ctypes.c_int),
         ("upwind_convention", ctypes.c_int),
+        ("solver", ctypes.c_int),
     ]
 
 
@@ -58,6 +61,7 @@ class Stats(ctypes.Structure):
         ("cg_iters_mean", ctypes.c_double),
         ("error_flags", ctypes.c_int),
         ("kernel_launches", ctypes.c_int),
+        ("cg_sweeps_mean", ctypes.c_double),
     ]
 
 
