@@ -388,7 +388,7 @@ void free_ctx(pavg_ctx* c) {
   CgIrWork& wi = c->cgi;
   cudaFree(wi.x[0]); cudaFree(wi.x[1]); cudaFree(wi.ax); cudaFree(wi.r64); cudaFree(wi.fbuf);
   cudaFree(wi.partial); cudaFree(wi.partial_f);
-  cudaFree(wi.bar); cudaFree(wi.scal);
+  cudaFree(wi.bar); cudaFree(wi.scal); cudaFree(wi.tag);
   cudaFree(m.M1f); cudaFree(m.Pinv); cudaFree(m.M1p); cudaFree(m.tri);
   cudaFree(c->ru);
   for (auto* v : c->vec) cudaFree(v);
@@ -487,7 +487,7 @@ int pavg_create(const pavg_params* p, pavg_ctx** out) {
          dalloc(&wi.fbuf, 9 * 4 * (size_t)(m.E + m.F)) == cudaSuccess &&
          dalloc(&wi.partial, 3 * (size_t)wi.nblocks) == cudaSuccess &&
          dalloc(&wi.partial_f, 3 * (size_t)wi.nblocks) == cudaSuccess &&
-         dalloc(&wi.scal, 8) == cudaSuccess &&
+         dalloc(&wi.scal, 8) == cudaSuccess && dalloc(&wi.tag, 4) == cudaSuccess &&
          dalloc(&wi.bar, 2) == cudaSuccess;
     wi.flags = w.flags;
     wi.stats = w.stats;

@@ -51,6 +51,7 @@ struct GridSync {
   double* partial;
   float* partial_f;
   double* scal;
+  unsigned long long* tag;
   unsigned* bar;
   int* flags;
 };
@@ -58,14 +59,27 @@ struct GridSync {
 __device__ __forceinline__ float* part_of(const GridSync& g, float) { return g.partial_f; }
 __device__ __forceinline__ double* part_of(const GridSync& g, double) { return g.partial; }
 
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
+  unsigned long long r;
+  asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(r) : "l"(p) : "memory");
+  return r;
+}
+
 // Grid-wide sum of three per-thread values, deterministic, one barrier.
+// `epoch` counts the grid sums of this launch (identical in every block).
+// The last block to arrive publishes each sum as a 64-bit word tagged with
+// the epoch (FP32 sums: tag in the high half, value in the low half; FP64
+// sums: the values first, then a tag word), so waiting blocks learn that the
+// barrier is open and read the sums with the same loads.
 template <typename Tv>
-__device__ __forceinline__ bool grid_sum3(GridSync g, Tv a, Tv b, Tv c, double out[3]) {
+__device__ __forceinline__ bool grid_sum3(GridSync g, unsigned& epoch, Tv a, Tv b, Tv c, double out[3]) {
   __shared__ Tv sh[3][kIrThreads / 32];
   __shared__ double s_out[3];
   __shared__ int s_last, s_ok;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nb = gridDim.x;
+  const bool fp32 = sizeof(Tv) == 4;
   Tv* part = part_of(g, Tv(0));
+  ++epoch;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_down_sync(0xffffffffu, a, o);
@@ -74,7 +88,6 @@ __device__ __forceinline__ bool grid_sum3(GridSync g, Tv a, Tv b, Tv c, double o
   }
   if (lane == 0) { sh[0][warp] = a; sh[1][warp] = b; sh[2][warp] = c; }
   __syncthreads();
-  unsigned gen = 0;
   if (threadIdx.x == 0) {
     Tv s0 = 0, s1 = 0, s2 = 0;
 #pragma unroll
@@ -82,7 +95,6 @@ __device__ __forceinline__ bool grid_sum3(GridSync g, Tv a, Tv b, Tv c, double o
     part[blockIdx.x] = s0;
     part[nb + blockIdx.x] = s1;
     part[2 * nb + blockIdx.x] = s2;
-    gen = ld_acquire(g.bar + 1);
     const unsigned arrived = atom_add_acq_rel(g.bar, 1u);  // releases this block's writes
     s_last = arrived == (unsigned)(nb - 1);
     s_ok = 1;
@@ -109,29 +121,46 @@ __device__ __forceinline__ bool grid_sum3(GridSync g, Tv a, Tv b, Tv c, double o
       Tv s0 = 0, s1 = 0, s2 = 0;
 #pragma unroll
       for (int k = 0; k < kIrThreads / 32; ++k) { s0 += sh[0][k]; s1 += sh[1][k]; s2 += sh[2][k]; }
-      g.scal[0] = (double)s0;
-      g.scal[1] = (double)s1;
-      g.scal[2] = (double)s2;
+      s_out[0] = (double)s0;
+      s_out[1] = (double)s1;
+      s_out[2] = (double)s2;
       *((volatile unsigned*)g.bar) = 0u;
-      red_add_release(g.bar + 1, 1u);  // publishes the sums and the reset counter
+      const unsigned long long hi = (unsigned long long)epoch << 32;
+      if (fp32) {
+        __threadfence();
+        volatile unsigned long long* t = g.tag;
+        t[0] = hi | __float_as_uint((float)s0);
+        t[1] = hi | __float_as_uint((float)s1);
+        t[2] = hi | __float_as_uint((float)s2);
+      } else {
+        g.scal[0] = (double)s0;
+        g.scal[1] = (double)s1;
+        g.scal[2] = (double)s2;
+        __threadfence();
+        *((volatile unsigned long long*)&g.tag[3]) = hi;
+      }
     }
   } else if (threadIdx.x == 0) {
     const long long t_start = clock64();
-    while (ld_acquire(g.bar + 1) == gen) {
-      if (clock64() - t_start > kBarrierTimeoutCycles) {
-        atomicOr(g.flags, kFlagTimeout);
-        s_ok = 0;
-        break;
+    const int k0 = fp32 ? 0 : 3, k1 = fp32 ? 2 : 3;
+    for (int k = k0; k <= k1 && s_ok; ++k) {
+      unsigned long long v;
+      while (((v = ld_acquire64(&g.tag[k])) >> 32) != epoch) {
+        if (clock64() - t_start > kBarrierTimeoutCycles) {
+          atomicOr(g.flags, kFlagTimeout);
+          s_ok = 0;
+          break;
+        }
+        __nanosleep(16);
       }
-      __nanosleep(16);
+      if (fp32) s_out[k] = (double)__uint_as_float((unsigned)(v & 0xffffffffu));
     }
-    __threadfence();
-  }
-  if (threadIdx.x == 0) {
+    if (!fp32) {
+      s_out[0] = __ldcg(&g.scal[0]);
+      s_out[1] = __ldcg(&g.scal[1]);
+      s_out[2] = __ldcg(&g.scal[2]);
+    }
     if (*((volatile int*)g.flags) & kFlagTimeout) s_ok = 0;
-    s_out[0] = __ldcg(&g.scal[0]);
-    s_out[1] = __ldcg(&g.scal[1]);
-    s_out[2] = __ldcg(&g.scal[2]);
   }
   __syncthreads();
   out[0] = s_out[0];
@@ -234,9 +263,12 @@ __device__ __forceinline__ void rows3_d(const double* __restrict__ M1, int64_t F
   }
 }
 
-// DOF triple of thread (c, q): DOFs 3t .. 3t+2, and whether the cell owns it.
-__device__ __forceinline__ int triple(const int32_t* __restrict__ tri, int64_t c, int q, bool& own) {
-  const int v = __ldg(&tri[4 * c + q]);
+// DOF triple of thread (c, q) in pass p: DOFs 3t .. 3t+2, and whether the
+// cell owns it (from shared memory on the resident path).
+template <bool RES>
+__device__ __forceinline__ int triple(const int32_t* __restrict__ tri, const int* s_tri, int p, int64_t c, int q,
+                                      bool& own) {
+  const int v = RES ? s_tri[p * kIrThreads + threadIdx.x] : __ldg(&tri[4 * c + q]);
   own = v < 0;
   return v & 0x7fffffff;
 }
@@ -250,36 +282,44 @@ __global__ void __launch_bounds__(kIrThreads, 3) k_cg_ir(DeviceMesh m, CgIrWork 
   __shared__ float s_f[2];  // alpha, beta of the current FP32 iteration
   __shared__ int s_state;   // 0 continue, 1 converged, 2 non-finite
   const int64_t F = m.F, T = m.E + m.F;
-  const GridSync gsync = {w.partial, w.partial_f, w.scal, w.bar, w.flags};
+  const GridSync gsync = {w.partial, w.partial_f, w.scal, w.tag, w.bar, w.flags};
+  unsigned epoch = 0;
   const int q = threadIdx.x & 3, cl = threadIdx.x >> 2;
   const int64_t cbase0 = (int64_t)blockIdx.x * kIrCells, cstride = (int64_t)gridDim.x * kIrCells;
   const int S4 = 4 * (int)T;  // floats per FP32 vector slot
   float* __restrict__ FB = w.fbuf;
   double red[3];
 
-  if (RES) {  // this block's FP32 element matrices, kept for the whole solve
-    int p = 0;
-    for (int64_t cb = cbase0; cb < F; cb += cstride, ++p)
+  // resident path: this block's FP32 element matrices and DOF triples, kept
+  // in shared memory for the whole solve
+  int* s_tri = reinterpret_cast<int*>(s_mat + (size_t)w.passes * kIrCells * kMatStride);
+  if (RES) {
+    int pp = 0;
+    for (int64_t cb = cbase0; cb < F; cb += cstride, ++pp) {
       for (int t = threadIdx.x; t < 78 * kIrCells; t += kIrThreads) {
         const int idx = t / kIrCells, k = t % kIrCells;
         const int64_t c = cb + k;
-        s_mat[(p * kIrCells + k) * kMatStride + idx] = c < F ? __ldg(&m.M1p[(int64_t)idx * F + c]) : 0.f;
+        s_mat[(pp * kIrCells + k) * kMatStride + idx] = c < F ? __ldg(&m.M1p[(int64_t)idx * F + c]) : 0.f;
       }
+      const int64_t c = cb + cl;
+      s_tri[pp * kIrThreads + threadIdx.x] = c < F ? __ldg(&m.tri[4 * c + q]) : 0;
+    }
     __syncthreads();
   }
 
   // ---- ||b||^2 (owners of each triple)
   double pb = 0.0;
-  for (int64_t cb = cbase0; cb < F; cb += cstride) {
+  int p = 0;
+  for (int64_t cb = cbase0; cb < F; cb += cstride, ++p) {
     const int64_t c = cb + cl;
     if (c >= F) continue;
     bool own = false;
-    const int t = triple(m.tri, c, q, own);
+    const int t = triple<RES>(m.tri, s_tri, p, c, q, own);
     if (own)
 #pragma unroll
       for (int j = 0; j < 3; ++j) { const double v = __ldg(&b[3 * t + j]); pb = fma(v, v, pb); }
   }
-  bool alive = grid_sum3<double>(gsync, pb, 0.0, 0.0, red);
+  bool alive = grid_sum3<double>(gsync, epoch, pb, 0.0, 0.0, red);
   const double bb = red[0];
   const double tol2 = cp.rtol * cp.rtol * bb;
   bool bad = !isfinite(bb);
@@ -295,7 +335,7 @@ __global__ void __launch_bounds__(kIrThreads, 3) k_cg_ir(DeviceMesh m, CgIrWork 
     // ---- FP32 start: r0 = r / ||r||, u0 = P r0, w0 = A u0 (into slot 5, zero on entry)
     float pg = 0.f, pd = 0.f, pr = 0.f;
     {
-      int p = 0;
+      p = 0;
       for (int64_t cb = cbase0; cb < F; cb += cstride, ++p) {
         const int64_t c = cb + cl;
         const bool active = c < F;
@@ -303,7 +343,7 @@ __global__ void __launch_bounds__(kIrThreads, 3) k_cg_ir(DeviceMesh m, CgIrWork 
         int t = 0;
         float r0[3] = {0.f, 0.f, 0.f}, u[3] = {0.f, 0.f, 0.f}, wl[3], pb3[6];
         if (active) {
-          t = triple(m.tri, c, q, own);
+          t = triple<RES>(m.tri, s_tri, p, c, q, own);
           load_P(m.Pinv, t, pb3);
 #pragma unroll
           for (int j = 0; j < 3; ++j) r0[j] = (float)(__ldcg(&rsrc[3 * t + j]) * scale);
@@ -326,7 +366,7 @@ __global__ void __launch_bounds__(kIrThreads, 3) k_cg_ir(DeviceMesh m, CgIrWork 
         }
       }
     }
-    alive = grid_sum3<float>(gsync, pg, pd, pr, red);
+    alive = grid_sum3<float>(gsync, epoch, pg, pd, pr, red);
     if (threadIdx.x == 0) {
       s_gamma = red[0];
       s_rr0 = red[2];
@@ -347,7 +387,7 @@ __global__ void __launch_bounds__(kIrThreads, 3) k_cg_ir(DeviceMesh m, CgIrWork 
       const int o_p = 8 * S4;
       const float fa = s_f[0], fb = s_f[1];
       pg = pd = pr = 0.f;
-      int p = 0;
+      p = 0;
       for (int64_t cb = cbase0; cb < F; cb += cstride, ++p) {
         const int64_t c = cb + cl;
         const bool active = c < F;
@@ -356,7 +396,7 @@ __global__ void __launch_bounds__(kIrThreads, 3) k_cg_ir(DeviceMesh m, CgIrWork 
         float rold[3] = {0.f, 0.f, 0.f}, rn[3] = {0.f, 0.f, 0.f}, sv[3] = {0.f, 0.f, 0.f};
         float u[3] = {0.f, 0.f, 0.f}, wl[3], pb3[6], pold[3] = {0.f, 0.f, 0.f}, xold[3] = {0.f, 0.f, 0.f};
         if (active) {
-          t = triple(m.tri, c, q, own);
+          t = triple<RES>(m.tri, s_tri, p, c, q, own);
           // every load of this pass first, then arithmetic, then every store
           load_P(m.Pinv, t, pb3);
           float wv[3], sp[3] = {0.f, 0.f, 0.f};
@@ -398,7 +438,7 @@ __global__ void __launch_bounds__(kIrThreads, 3) k_cg_ir(DeviceMesh m, CgIrWork 
           }
         }
       }
-      alive = grid_sum3<float>(gsync, pg, pd, pr, red);
+      alive = grid_sum3<float>(gsync, epoch, pg, pd, pr, red);
       // the recurrence scalars live in shared memory, updated by thread 0
       if (threadIdx.x == 0) {
         const double gnew = red[0], dnew = red[1], rrf = red[2];
@@ -427,14 +467,15 @@ __global__ void __launch_bounds__(kIrThreads, 3) k_cg_ir(DeviceMesh m, CgIrWork 
     const double* xold = xcur ? w.x[1] : w.x[0];
     double* xnew = xcur ? w.x[0] : w.x[1];
     const double inv = 1.0 / scale;
-    for (int64_t cb = cbase0; cb < F; cb += cstride) {
+    p = 0;
+    for (int64_t cb = cbase0; cb < F; cb += cstride, ++p) {
       const int64_t c = cb + cl;
       const bool active = c < F;
       bool own = false;
       int t = 0;
       double xn[3] = {0.0, 0.0, 0.0}, ax[3];
       if (active) {
-        t = triple(m.tri, c, q, own);
+        t = triple<RES>(m.tri, s_tri, p, c, q, own);
         double xo[3] = {0.0, 0.0, 0.0};
         float dxf[3];
         ld3(FB, t, dxf);
@@ -463,15 +504,16 @@ __global__ void __launch_bounds__(kIrThreads, 3) k_cg_ir(DeviceMesh m, CgIrWork 
         }
       }
     }
-    alive = grid_sum3<double>(gsync, 0.0, 0.0, 0.0, red);
+    alive = grid_sum3<double>(gsync, epoch, 0.0, 0.0, 0.0, red);
     if (!alive) break;
     // ---- r = b - A x (FP64) by the owners; clear ax for the next sweep
     double prr = 0.0;
-    for (int64_t cb = cbase0; cb < F; cb += cstride) {
+    p = 0;
+    for (int64_t cb = cbase0; cb < F; cb += cstride, ++p) {
       const int64_t c = cb + cl;
       if (c >= F) continue;
       bool own = false;
-      const int t = triple(m.tri, c, q, own);
+      const int t = triple<RES>(m.tri, s_tri, p, c, q, own);
       if (!own) continue;
       double bv[3], av[3];
 #pragma unroll
@@ -485,7 +527,7 @@ __global__ void __launch_bounds__(kIrThreads, 3) k_cg_ir(DeviceMesh m, CgIrWork 
         prr = fma(r, r, prr);
       }
     }
-    alive = grid_sum3<double>(gsync, prr, 0.0, 0.0, red);
+    alive = grid_sum3<double>(gsync, epoch, prr, 0.0, 0.0, red);
     rr64 = red[0];
     xcur ^= 1;
     have_x = true;
@@ -499,11 +541,12 @@ __global__ void __launch_bounds__(kIrThreads, 3) k_cg_ir(DeviceMesh m, CgIrWork 
   }
   // ---- out = scale_x x + add on owned DOFs
   const double* xfin = xcur ? w.x[1] : w.x[0];
-  for (int64_t cb = cbase0; cb < F; cb += cstride) {
+  p = 0;
+  for (int64_t cb = cbase0; cb < F; cb += cstride, ++p) {
     const int64_t c = cb + cl;
     if (c >= F) continue;
     bool own = false;
-    const int t = triple(m.tri, c, q, own);
+    const int t = triple<RES>(m.tri, s_tri, p, c, q, own);
     if (!own) continue;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -536,7 +579,7 @@ cudaError_t cg_ir_configure(int64_t F, CgIrWork* w) {
   for (int bps = 3; bps >= 2; --bps) {
     const int64_t nb = need < (int64_t)bps * sms ? need : (int64_t)bps * sms;
     const int64_t passes = (need + nb - 1) / nb;
-    const size_t smem = sizeof(float) * (size_t)passes * kIrCells * kMatStride;
+    const size_t smem = sizeof(float) * (size_t)passes * kIrCells * kMatStride + sizeof(int) * (size_t)passes * kIrThreads;
     if (smem > 200 * 1024) continue;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_ir<true>, kIrThreads, smem);
@@ -568,6 +611,7 @@ cudaError_t launch_cg_ir(const DeviceMesh& m, const CgIrWork& w, const CgIrParam
     e = cudaMemsetAsync(w.fbuf + (size_t)s * 4 * (m.E + m.F), 0, sizeof(float) * 4 * m.E, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.ax, 0, sizeof(double) * 3 * m.E, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.bar, 0, sizeof(unsigned), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.tag, 0, 4 * sizeof(unsigned long long), st);  // epochs start at 1
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(w.nblocks);

@@ -67,7 +67,8 @@ struct CgIrWork {
   float* pf = nullptr;
   double* partial = nullptr;           // [3][nblocks] per-block partial sums (FP64 phases)
   float* partial_f = nullptr;          // [3][nblocks] per-block partial sums (FP32 phases)
-  double* scal = nullptr;              // [2][4] published global sums (alternating)
+  double* scal = nullptr;              // [4] published global sums (FP64 phases)
+  unsigned long long* tag = nullptr;   // [4] published sums tagged with their barrier epoch
   unsigned* bar = nullptr;             // [2]
   int* flags = nullptr;
   unsigned long long* stats = nullptr; // [0] solves, [1] inner iterations, [2] max per solve, [3] sweeps
