@@ -223,19 +223,35 @@ int get_plan(pavg_ctx* ctx, double T, int M, AvgPlan** out) {
   }
   AvgPlan pl;
   pl.T = T; pl.M = M; pl.K = K;
+  // Shifts ordered by decreasing degree K_m: each 8-row tile of the forward
+  // table then uses a prefix of the k range, and each 8-row tile of the
+  // backward table a prefix of the shifts; the contractions skip the zeros.
+  std::vector<int> ord(M);
+  for (int m = 0; m < M; ++m) ord[m] = m;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cs[a].size() > cs[b].size(); });
   std::vector<double> A((size_t)M * (K + 1), 0.0), B((size_t)(K + 1) * M, 0.0);
-  for (int m = 0; m < M; ++m) {
+  for (int r = 0; r < M; ++r) {
+    const int m = ord[r];
     double sg = s[m] >= 0 ? 1.0 : -1.0;
     double fw = 1.0, bw = 1.0;  // sgn^k and (-sgn)^k
     for (int k = 0; k <= K; ++k) {
       double ck = k < (int)cs[m].size() ? cs[m][k] : 0.0;
-      A[(size_t)m * (K + 1) + k] = ck * fw;
-      B[(size_t)k * M + m] = w[m] * ck * bw;
+      A[(size_t)r * (K + 1) + k] = ck * fw;
+      B[(size_t)k * M + r] = w[m] * ck * bw;
       fw *= sg;
       bw *= -sg;
     }
   }
-  if (upload(&pl.dA, A) != cudaSuccess || upload(&pl.dB, B) != cudaSuccess)
+  const int tile = combine_tile();
+  std::vector<int> limA((M + tile - 1) / tile), limB((K + 1 + tile - 1) / tile);
+  for (size_t j = 0; j < limA.size(); ++j) limA[j] = (int)cs[ord[j * tile]].size();
+  for (size_t j = 0; j < limB.size(); ++j) {
+    int cnt = 0;
+    for (int r = 0; r < M; ++r) cnt += (int)cs[ord[r]].size() > (int)(j * tile) ? 1 : 0;
+    limB[j] = cnt;
+  }
+  if (upload(&pl.dA, A) != cudaSuccess || upload(&pl.dB, B) != cudaSuccess || upload(&pl.dlimA, limA) != cudaSuccess ||
+      upload(&pl.dlimB, limB) != cudaSuccess)
     return set_err(ctx, PAVG_ERR_NOMEM, "plan upload failed");
   auto res = ctx->plans.emplace(key, pl);
   *out = &res.first->second;
@@ -263,10 +279,10 @@ int enq_avg(pavg_ctx* ctx, const AvgPlan& pl, const double* U, double* out, cuda
                       k == 0 ? nullptr : Q + (int64_t)(k - 1) * n, Q + (int64_t)(k + 1) * n, st);
     if (rc) return rc;
   }
-  KL(launch_combine(pl.dA, M, K + 1, Q, n, ctx->Um, n, n, st));
+  KL(launch_combine(pl.dA, M, K + 1, pl.dlimA, Q, n, ctx->Um, n, n, st));
   CK(cudaMemset2DAsync(ctx->Rm, sizeof(double) * n, 0, sizeof(double) * 3 * m.E, M, st));
   KL(launch_nonlinear_rhs(m, ctx->Um, ctx->Rm, M, ctx->p.upwind_convention, st));
-  KL(launch_combine(pl.dB, K + 1, M, ctx->Rm, n, Q, n, n, st));  // y_k overwrite Q_k
+  KL(launch_combine(pl.dB, K + 1, M, pl.dlimB, ctx->Rm, n, Q, n, n, st));  // y_k overwrite Q_k
   double* b[3] = {ctx->vec[0], ctx->vec[1], ctx->vec[2]};
   const double* b1 = nullptr;  // b_{k+1}
   const double* b2 = nullptr;  // b_{k+2}
@@ -374,6 +390,8 @@ void free_ctx(pavg_ctx* c) {
   if (!c) return;
   for (auto& kv : c->plans) {
     drop_graph(&kv.second);
+    cudaFree(kv.second.dlimA);
+    cudaFree(kv.second.dlimB);
     cudaFree(kv.second.dA);
     cudaFree(kv.second.dB);
   }

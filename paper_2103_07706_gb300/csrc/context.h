@@ -20,6 +20,8 @@ struct AvgPlan {
   int K = 0;                 // K_max over shifts
   double* dA = nullptr;      // [M][K+1]  forward combine
   double* dB = nullptr;      // [K+1][M]  backward combine
+  int* dlimA = nullptr;      // per 8-row tile of A: number of k with a nonzero entry
+  int* dlimB = nullptr;      // per 8-row tile of B: number of (reordered) shifts with a nonzero entry
   cudaGraphExec_t exec = nullptr;
   bool timed = false;        // captured with CG event brackets
   int launches = 0;          // kernels in the captured graph

@@ -120,9 +120,11 @@ cudaError_t launch_nonlinear_rhs(const DeviceMesh& m, const double* U, double* r
 cudaError_t launch_m2inv(const DeviceMesh& m, const double* r, int64_t rstride, double* out,
                          int64_t ostride, int B, cudaStream_t st);
 
-// out[m][j] = sum_k A[m][k] in[k][j] (+ beta out[m][j] when accumulate), j < len.
-// A is [Mo][Ki] in device memory.
-cudaError_t launch_combine(const double* A, int Mo, int Ki, const double* in, int64_t in_stride,
+// out[m][j] = sum_k A[m][k] in[k][j], j < len.  A is [Mo][Ki] in device
+// memory; rows are processed in tiles of combine_tile(), and when lim is not
+// null tile t only uses k < lim[t] (the rest of its rows being zero).
+int combine_tile();
+cudaError_t launch_combine(const double* A, int Mo, int Ki, const int* lim, const double* in, int64_t in_stride,
                            double* out, int64_t out_stride, int64_t len, cudaStream_t st);
 
 // out = a x + b y (+ c z); any of y, z may be null.

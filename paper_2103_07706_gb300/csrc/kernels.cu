@@ -457,13 +457,15 @@ __global__ void k_m2inv(DeviceMesh m, const double* __restrict__ r, int64_t rstr
   }
 }
 
-// out[m][j] = sum_k A[m][k] in[k][j]; MT output rows per block row.
+// out[m][j] = sum_k A[m][k] in[k][j]; MT output rows per block row, whose
+// nonzero k range is k < lim[tile] when lim is given.
 template <int MT>
 __global__ void __launch_bounds__(256) k_combine(const double* __restrict__ A, int Mo, int Ki,
-                                                 const double* __restrict__ in, int64_t in_stride,
-                                                 double* out, int64_t out_stride, int64_t len) {
+                                                 const int* __restrict__ lim, const double* __restrict__ in,
+                                                 int64_t in_stride, double* out, int64_t out_stride, int64_t len) {
   extern __shared__ double sA[];  // [MT][Ki]
   const int m0 = blockIdx.y * MT;
+  const int kn = lim ? lim[blockIdx.y] : Ki;
   for (int t = threadIdx.x; t < MT * Ki; t += blockDim.x) {
     int mm = m0 + t / Ki, k = t % Ki;
     sA[t] = mm < Mo ? A[(int64_t)mm * Ki + k] : 0.0;
@@ -473,7 +475,7 @@ __global__ void __launch_bounds__(256) k_combine(const double* __restrict__ A, i
     double acc[MT];
 #pragma unroll
     for (int t = 0; t < MT; ++t) acc[t] = 0.0;
-    for (int k = 0; k < Ki; ++k) {
+    for (int k = 0; k < kn; ++k) {
       const double v = __ldg(&in[(int64_t)k * in_stride + j]);
 #pragma unroll
       for (int t = 0; t < MT; ++t) acc[t] = fma(sA[t * Ki + k], v, acc[t]);
@@ -597,7 +599,9 @@ cudaError_t launch_m2inv(const DeviceMesh& m, const double* r, int64_t rstride, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_combine(const double* A, int Mo, int Ki, const double* in, int64_t in_stride,
+int combine_tile() { return 8; }
+
+cudaError_t launch_combine(const double* A, int Mo, int Ki, const int* lim, const double* in, int64_t in_stride,
                            double* out, int64_t out_stride, int64_t len, cudaStream_t st) {
   constexpr int MT = 8;
   size_t smem = sizeof(double) * MT * Ki;
@@ -608,7 +612,7 @@ cudaError_t launch_combine(const double* A, int Mo, int Ki, const double* in, in
     attr_set = true;
   }
   dim3 grid((unsigned)grid_for(len, 256, 152 * 4), (unsigned)((Mo + MT - 1) / MT));
-  k_combine<MT><<<grid, 256, smem, st>>>(A, Mo, Ki, in, in_stride, out, out_stride, len);
+  k_combine<MT><<<grid, 256, smem, st>>>(A, Mo, Ki, lim, in, in_stride, out, out_stride, len);
   return cudaGetLastError();
 }
 
