@@ -54,6 +54,40 @@ def _cg_flops(F, n_u, iters, sweeps):
     return iters * 530.0 * F, sweeps * (288.0 * F + 6.0 * n_u)
 
 
+def _mixed_mode(pavg, cfg, Ud, ref, args, stream):
+    """Times the PAVG_PRECISION_MIXED path on the bench state and states its
+    relative L2 error per field against the FP64 GPU result `ref`."""
+    import torch
+    m = pavg.Model(cfg["refinement"], lambda_max=cfg["lambda_max"], g=cfg["g"], H=cfg["H"], omega=cfg["Omega"],
+                   radius=cfg["R"], cheb_tol=cfg["cheb_tol"], cg_rtol=cfg["cg_rtol"],
+                   precision=pavg.PAVG_PRECISION_MIXED)
+    o = torch.empty_like(Ud)
+    T, M = cfg["T_s"], cfg["M"]
+    for _ in range(args.warmup):
+        m.averaged_rhs(T, M, Ud, o)
+    m.sync()
+    m.reset_stats()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        m.averaged_rhs(T, M, Ud, o)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    m.sync()
+    st = m.stats()
+    nu = m.n_u
+    err = lambda sl: float((o[sl] - ref[sl]).norm() / ref[sl].norm())
+    res = {"value": 1e3 / ms, "unit": "evals/s", "ms_per_step": ms, "dtype": "f32 N and forward combine, "
+           "f32 CG in f64 refinement, f64 recurrences and shift sum",
+           "rel_l2_u_vs_fp64": err(slice(0, nu)), "rel_l2_eta_vs_fp64": err(slice(nu, None)),
+           "stated_bound": {"u": 1e-5, "eta": 5e-4}, "cg_sweeps_mean": st["cg_sweeps_mean"],
+           "cg_iters_mean": st["cg_iters_mean"], "error_flags": st["error_flags"]}
+    m.close()
+    return res
+
+
 # ----------------------------------------------------------------------------- CPU oracle leg
 def _oracle_worker(q, cfg, parity):
     """Runs in a spawned process (no CUDA): oracle timing sample + parity case."""
@@ -294,6 +328,9 @@ def run_pavg(args):
     e2e_value = world * args.steps / (float(t.item()) / 1e3)
     model.sync()
 
+    # mixed-precision mode on the same state: throughput and error against the FP64 result above
+    mixed = _mixed_mode(pavg, cfg, Ud, out, args, stream)
+
     # parity of the small configuration against the oracle (computed by the spawned leg)
     cpu = None
     parity = None
@@ -347,7 +384,7 @@ def run_pavg(args):
             "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": 8 * model.n,
                     "d2h_bytes_per_step": 8 * model.n},
             "gpu_launches": st["kernel_launches"] * args.steps,
-            "roofline": roof, "cpu_baseline": cpu, "parity": parity, "clocks": clk,
+            "roofline": roof, "cpu_baseline": cpu, "parity": parity, "precision_mixed": mixed, "clocks": clk,
             "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
             "error_flags": st["error_flags"]}
     if rank == 0:

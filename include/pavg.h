@@ -60,6 +60,11 @@ extern "C" {
 #define PAVG_UPWIND_AS_PRINTED 1 /* u~ = u+ when u.n+ < 0, as printed in Sec. 2.5 */
 #define PAVG_SOLVER_MIXED 0      /* M1 solves: FP32 block-Jacobi CG refined by FP64 residuals */
 #define PAVG_SOLVER_FP64 1       /* M1 solves: FP64 Jacobi CG */
+#define PAVG_PRECISION_FP64 0    /* every result FP64-accurate (mass solves to cg_rtol) */
+#define PAVG_PRECISION_MIXED 1   /* N and the forward shift contraction in FP32 arithmetic (FP64 sums
+                                    over quadrature points), mass solves to max(cg_rtol, 1e-5) (one FP32
+                                    CG sweep, FP64 residual); the weighted sum over shifts, state
+                                    vectors, recurrences and timestep updates stay FP64 */
 
 typedef struct pavg_ctx pavg_ctx; /* opaque, library-owned */
 
@@ -79,11 +84,12 @@ typedef struct {
   int solver;             /* PAVG_SOLVER_MIXED (default) or PAVG_SOLVER_FP64; both reach cg_rtol
                              in FP64; cg_maxit caps the iterations of one solve (FP64) or of one
                              refinement sweep (mixed, at most 8 sweeps) */
+  int precision;          /* PAVG_PRECISION_FP64 (default) or PAVG_PRECISION_MIXED */
 } pavg_params;
 
 /* Fill `p` with the defaults: r = 3, R = 6.37122e6, Omega = 7.292e-5,
  * g = 9.80616, H = 5000, cheb_tol = 1e-6, cg_rtol = 1e-14, cg_maxit = 400,
- * lambda_max = 0, midpoint rule, standard upwinding, mixed solver. */
+ * lambda_max = 0, midpoint rule, standard upwinding, mixed solver, FP64 precision. */
 int pavg_default_params(pavg_params* p);
 
 /* Build the mesh and FE data (Sec. 2.5, Sec. 3) on the current CUDA device and

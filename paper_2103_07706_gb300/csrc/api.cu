@@ -23,6 +23,12 @@ using pavg_detail::EventPair;
 
 namespace {
 
+#ifndef PAVG_MIXED_SOLVE_RTOL
+#define PAVG_MIXED_SOLVE_RTOL 1e-5
+#endif
+// Relative residual at which mass solves stop in mixed precision.
+constexpr double kMixedSolveRtol = PAVG_MIXED_SOLVE_RTOL;
+
 int set_err(pavg_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
   return code;
@@ -148,7 +154,8 @@ int enq_linear(pavg_ctx* ctx, const double* U, double* out, cudaStream_t st) {
 int enq_nonlinear(pavg_ctx* ctx, const double* U, double* out, double* scratch, cudaStream_t st) {
   const DeviceMesh& m = ctx->dm;
   CK(cudaMemsetAsync(scratch, 0, sizeof(double) * 3 * m.E, st));
-  KL(launch_nonlinear_rhs(m, U, scratch, 1, ctx->p.upwind_convention, st));
+  KL(launch_nonlinear_rhs(m, U, scratch, 1, ctx->p.upwind_convention, st,
+                          ctx->p.precision == PAVG_PRECISION_MIXED));
   return enq_mass_solve(ctx, scratch, out, st);
 }
 
@@ -279,9 +286,12 @@ int enq_avg(pavg_ctx* ctx, const AvgPlan& pl, const double* U, double* out, cuda
                       k == 0 ? nullptr : Q + (int64_t)(k - 1) * n, Q + (int64_t)(k + 1) * n, st);
     if (rc) return rc;
   }
-  KL(launch_combine(pl.dA, M, K + 1, pl.dlimA, Q, n, ctx->Um, n, n, st));
+  const bool fp32 = ctx->p.precision == PAVG_PRECISION_MIXED;
+  KL(launch_combine(pl.dA, M, K + 1, pl.dlimA, Q, n, ctx->Um, n, n, st, fp32));
   CK(cudaMemset2DAsync(ctx->Rm, sizeof(double) * n, 0, sizeof(double) * 3 * m.E, M, st));
-  KL(launch_nonlinear_rhs(m, ctx->Um, ctx->Rm, M, ctx->p.upwind_convention, st));
+  KL(launch_nonlinear_rhs(m, ctx->Um, ctx->Rm, M, ctx->p.upwind_convention, st, fp32));
+  // the weighted sum over shifts stays FP64 in every precision: the average
+  // cancels most of the oscillating terms, so rounding here is amplified
   KL(launch_combine(pl.dB, K + 1, M, pl.dlimB, ctx->Rm, n, Q, n, n, st));  // y_k overwrite Q_k
   double* b[3] = {ctx->vec[0], ctx->vec[1], ctx->vec[2]};
   const double* b1 = nullptr;  // b_{k+1}
@@ -423,7 +433,8 @@ bool valid_params(const pavg_params* p) {
          p->cheb_tol > 0 && p->cg_rtol > 0 && p->cg_maxit > 0 && p->lambda_max >= 0 && std::isfinite(p->omega) &&
          (p->quad_rule == PAVG_QUAD_MIDPOINT || p->quad_rule == PAVG_QUAD_CLOSED) &&
          (p->upwind_convention == PAVG_UPWIND_STANDARD || p->upwind_convention == PAVG_UPWIND_AS_PRINTED) &&
-         (p->solver == PAVG_SOLVER_MIXED || p->solver == PAVG_SOLVER_FP64);
+         (p->solver == PAVG_SOLVER_MIXED || p->solver == PAVG_SOLVER_FP64) &&
+         (p->precision == PAVG_PRECISION_FP64 || p->precision == PAVG_PRECISION_MIXED);
 }
 
 }  // namespace
@@ -444,6 +455,7 @@ int pavg_default_params(pavg_params* p) {
   p->quad_rule = PAVG_QUAD_MIDPOINT;
   p->upwind_convention = PAVG_UPWIND_STANDARD;
   p->solver = PAVG_SOLVER_MIXED;
+  p->precision = PAVG_PRECISION_FP64;
   return PAVG_OK;
 }
 
@@ -455,9 +467,11 @@ int pavg_create(const pavg_params* p, pavg_ctx** out) {
   ctx->p = *p;
   ctx->cgp.rtol = p->cg_rtol;
   ctx->cgp.maxit = p->cg_maxit;
-  ctx->cgip.rtol = p->cg_rtol;
+  const bool mixed = p->precision == PAVG_PRECISION_MIXED;
+  if (mixed) ctx->cgp.rtol = std::max(p->cg_rtol, kMixedSolveRtol);
+  ctx->cgip.rtol = mixed ? std::max(p->cg_rtol, kMixedSolveRtol) : p->cg_rtol;
   ctx->cgip.max_sweeps = 8;
-  ctx->cgip.inner_rtol = 1e-5f;
+  ctx->cgip.inner_rtol = mixed ? 1e-6f : 1e-5f;
   ctx->cgip.max_inner = p->cg_maxit < 200 ? p->cg_maxit : 200;
   int rc = PAVG_OK;
   try {

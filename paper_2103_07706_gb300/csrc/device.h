@@ -113,8 +113,9 @@ cudaError_t launch_apply_K(const DeviceMesh& m, const double* U, double s, doubl
 
 // Weak-form right-hand side of N for B states [B][n] -> r [B][n]
 // (r's velocity edge DOFs must be zeroed first).
+// fp32: FP32 arithmetic per quadrature point, FP64 sums over the points.
 cudaError_t launch_nonlinear_rhs(const DeviceMesh& m, const double* U, double* r, int B,
-                                 int upwind, cudaStream_t st);
+                                 int upwind, cudaStream_t st, bool fp32 = false);
 
 // eta_out = M2^{-1} r_eta (+ add) for B blocks of n_eta with strides.
 cudaError_t launch_m2inv(const DeviceMesh& m, const double* r, int64_t rstride, double* out,
@@ -125,7 +126,7 @@ cudaError_t launch_m2inv(const DeviceMesh& m, const double* r, int64_t rstride, 
 // null tile t only uses k < lim[t] (the rest of its rows being zero).
 int combine_tile();
 cudaError_t launch_combine(const double* A, int Mo, int Ki, const int* lim, const double* in, int64_t in_stride,
-                           double* out, int64_t out_stride, int64_t len, cudaStream_t st);
+                           double* out, int64_t out_stride, int64_t len, cudaStream_t st, bool fp32 = false);
 
 // out = a x + b y (+ c z); any of y, z may be null.
 cudaError_t launch_lincomb(double* out, double a, const double* x, double b, const double* y,

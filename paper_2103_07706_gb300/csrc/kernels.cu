@@ -14,8 +14,14 @@
 namespace pavg {
 
 __constant__ ConstTables c_tab;
+__constant__ TablesT<float> c_tabf;
 
-cudaError_t upload_tables(const ConstTables& t) { return cudaMemcpyToSymbol(c_tab, &t, sizeof(t)); }
+cudaError_t upload_tables(const ConstTables& t) {
+  cudaError_t e = cudaMemcpyToSymbol(c_tab, &t, sizeof(t));
+  if (e != cudaSuccess) return e;
+  const TablesT<float> f = tables_to_float(t);
+  return cudaMemcpyToSymbol(c_tabf, &f, sizeof(f));
+}
 
 namespace {
 
@@ -253,72 +259,125 @@ __global__ void __launch_bounds__(128) k_apply_K(DeviceMesh m, const double* __r
 }
 
 // ------------------------------------------------------------------ nonlinear operator
-struct Side {
-  double c[12];   // signed local coefficients
-  double h[3];    // eta - b at the local vertices
-  double det, G00, G01, G11;
+// Arithmetic type R: double (FP64 path) or float (mixed precision, where each
+// quadrature point's contribution is formed in FP32 and the sums over the
+// quadrature points are accumulated in FP64).
+template <typename R>
+__device__ __forceinline__ const TablesT<R>& tab();
+template <>
+__device__ __forceinline__ const TablesT<double>& tab<double>() { return c_tab; }
+template <>
+__device__ __forceinline__ const TablesT<float>& tab<float>() { return c_tabf; }
+
+// Explicitly rounded operations (never contracted or reordered by the compiler).
+template <typename R>
+struct Rn;
+template <>
+struct Rn<double> {
+  static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+};
+template <>
+struct Rn<float> {
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
 };
 
+template <typename R>
+struct Side {
+  R c[12];   // signed local coefficients
+  R h[3];    // eta - b at the local vertices
+  R det, G00, G01, G11;
+  R dv[3];   // div_hat u_hat at the local vertices, formed in FP64 (FP32 strong form only)
+};
+
+template <typename R>
 __device__ __forceinline__ void load_side(const DeviceMesh& m, const double* __restrict__ U, int64_t cell,
-                                          Side& S) {
+                                          Side<R>& S) {
   int dof[12];
   double sg[12];
   cell_dofs(m, cell, dof, sg);
+  double cd[12];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) S.c[k] = sg[k] * __ldg(&U[dof[k]]);
+  for (int k = 0; k < 12; ++k) {
+    cd[k] = sg[k] * __ldg(&U[dof[k]]);
+    S.c[k] = (R)cd[k];
+  }
+  if (sizeof(R) == 4) {
+    // the divergence of a nearly divergence-free field is a cancelling sum of
+    // edge fluxes: form it from the FP64 coefficients
 #pragma unroll
-  for (int k = 0; k < 3; ++k) S.h[k] = __ldg(&U[m.n_u + 3 * cell + k]) - __ldg(&m.topo[3 * cell + k]);
-  S.det = __ldg(&m.det[cell]);
-  S.G00 = __ldg(&m.G[cell]);
-  S.G01 = __ldg(&m.G[m.F + cell]);
-  S.G11 = __ldg(&m.G[2 * m.F + cell]);
+    for (int v = 0; v < 3; ++v) {
+      double d = 0.0;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) d = fma(cd[k], c_tab.div_vert[k][v], d);
+      S.dv[v] = (R)d;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) S.h[k] = (R)(__ldg(&U[m.n_u + 3 * cell + k]) - __ldg(&m.topo[3 * cell + k]));
+  S.det = (R)__ldg(&m.det[cell]);
+  S.G00 = (R)__ldg(&m.G[cell]);
+  S.G01 = (R)__ldg(&m.G[m.F + cell]);
+  S.G11 = (R)__ldg(&m.G[2 * m.F + cell]);
 }
 
+template <typename R>
 struct FacetValues {
-  double flux;     // u+ . n+ ds / dtau
-  double tan;      // |e| (t . u~)
-  double hup;      // (eta - b)~
-  double up0, up1, um0, um1;
+  R flux;     // u+ . n+ ds / dtau
+  R tan;      // |e| (t . u~)
+  R hup;      // (eta - b)~
+  R hp, hm;   // eta - b on each side
+  R up0, up1, um0, um1;
 };
 
 // Values shared by the two cells of a facet at point p, evaluated with
 // explicitly rounded operations so that both cells obtain identical bits.
 // Upwind: the side the flow leaves (flux > 0: plus); the printed rule of
 // Sec. 2.5 (u~ = u+ when u . n+ < 0) is the alternative for the velocity.
-__device__ __forceinline__ FacetValues facet_point(const Side& P, int lp, const Side& Mn, int lm, int p,
-                                                   int upwind) {
-  FacetValues f;
-  double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0, hp = 0.0, hm = 0.0;
+template <typename R>
+__device__ __forceinline__ FacetValues<R> facet_point(const Side<R>& P, int lp, const Side<R>& Mn, int lm, int p,
+                                                      int upwind) {
+  const TablesT<R>& T = tab<R>();
+  using O = Rn<R>;
+  FacetValues<R> f;
+  R a0 = 0, a1 = 0, b0 = 0, b1 = 0, hp = 0, hm = 0;
 #pragma unroll
   for (int j = 0; j < 12; ++j) {
-    a0 = __fma_rn(P.c[j], c_tab.fq_psi[0][lp][p][j][0], a0);
-    a1 = __fma_rn(P.c[j], c_tab.fq_psi[0][lp][p][j][1], a1);
-    b0 = __fma_rn(Mn.c[j], c_tab.fq_psi[1][lm][p][j][0], b0);
-    b1 = __fma_rn(Mn.c[j], c_tab.fq_psi[1][lm][p][j][1], b1);
+    a0 = O::fma(P.c[j], T.fq_psi[0][lp][p][j][0], a0);
+    a1 = O::fma(P.c[j], T.fq_psi[0][lp][p][j][1], a1);
+    b0 = O::fma(Mn.c[j], T.fq_psi[1][lm][p][j][0], b0);
+    b1 = O::fma(Mn.c[j], T.fq_psi[1][lm][p][j][1], b1);
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    hp = __fma_rn(P.h[k], c_tab.fq_phi[0][lp][p][k], hp);
-    hm = __fma_rn(Mn.h[k], c_tab.fq_phi[1][lm][p][k], hm);
+    hp = O::fma(P.h[k], T.fq_phi[0][lp][p][k], hp);
+    hm = O::fma(Mn.h[k], T.fq_phi[1][lm][p][k], hm);
   }
-  const double dp0 = c_tab.edge_dir[lp][0], dp1 = c_tab.edge_dir[lp][1];
-  const double dm0 = c_tab.edge_dir[lm][0], dm1 = c_tab.edge_dir[lm][1];
-  const double flux = __dsub_rn(__dmul_rn(a0, dp1), __dmul_rn(a1, dp0));
-  const bool plus_up = flux > 0.0;
-  const bool plus_up_vel = upwind == PAVG_UPWIND_STANDARD ? plus_up : (flux < 0.0);
-  double tan;
+  const R dp0 = T.edge_dir[lp][0], dp1 = T.edge_dir[lp][1];
+  const R dm0 = T.edge_dir[lm][0], dm1 = T.edge_dir[lm][1];
+  const R flux = O::sub(O::mul(a0, dp1), O::mul(a1, dp0));
+  const bool plus_up = flux > R(0);
+  const bool plus_up_vel = upwind == PAVG_UPWIND_STANDARD ? plus_up : (flux < R(0));
+  R tan;
   if (plus_up_vel) {
-    double g0 = __fma_rn(P.G00, a0, __dmul_rn(P.G01, a1));
-    double g1 = __fma_rn(P.G01, a0, __dmul_rn(P.G11, a1));
-    tan = __ddiv_rn(__fma_rn(dp0, g0, __dmul_rn(dp1, g1)), P.det);
+    R g0 = O::fma(P.G00, a0, O::mul(P.G01, a1));
+    R g1 = O::fma(P.G01, a0, O::mul(P.G11, a1));
+    tan = O::div(O::fma(dp0, g0, O::mul(dp1, g1)), P.det);
   } else {
-    double g0 = __fma_rn(Mn.G00, b0, __dmul_rn(Mn.G01, b1));
-    double g1 = __fma_rn(Mn.G01, b0, __dmul_rn(Mn.G11, b1));
-    tan = -__ddiv_rn(__fma_rn(dm0, g0, __dmul_rn(dm1, g1)), Mn.det);
+    R g0 = O::fma(Mn.G00, b0, O::mul(Mn.G01, b1));
+    R g1 = O::fma(Mn.G01, b0, O::mul(Mn.G11, b1));
+    tan = -O::div(O::fma(dm0, g0, O::mul(dm1, g1)), Mn.det);
   }
   f.flux = flux;
   f.tan = tan;
   f.hup = plus_up ? hp : hm;
+  f.hp = hp;
+  f.hm = hm;
   f.up0 = a0; f.up1 = a1; f.um0 = b0; f.um1 = b1;
   return f;
 }
@@ -330,14 +389,24 @@ __device__ __forceinline__ FacetValues facet_point(const Side& P, int lp, const 
 // The cell integrand in reference form is, with v = G u_hat and the
 // derivative d_tau = v1 d/dx - v0 d/dy:
 //   [d_tau cross2(u_hat, psi_i) + div psi_i (u_hat . v) / 2] / det^2.
-__global__ void __launch_bounds__(128) k_nonlinear(DeviceMesh m, const double* __restrict__ Uall,
-                                                   double* Rall, int upwind) {
+// Sums over quadrature points are accumulated in FP64.
+// In FP32 (R = float) the elevation terms use the equivalent strong form
+//   re_k = -int_K phi_k div(u (eta - b)) + int_dK phi_k (u . n) ((eta - b)_own - (eta - b)~),
+// identical under exact integration (the divergence theorem on each cell;
+// the integrands are polynomials integrated exactly), which avoids the
+// cancellation between the cell and facet terms of the weak form (both grow
+// like 1 / h while their sum does not).
+template <typename R>
+__global__ void __launch_bounds__(128) k_nonlinear(DeviceMesh m, const double* __restrict__ Uall, double* Rall,
+                                                   int upwind) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= m.F) return;
+  const TablesT<R>& T = tab<R>();
+  constexpr bool kStrongDG = sizeof(R) == 4;
   const int64_t n = m.n;
   const double* U = Uall + (int64_t)blockIdx.y * n;
-  double* R = Rall + (int64_t)blockIdx.y * n;
-  Side own;
+  double* Rout = Rall + (int64_t)blockIdx.y * n;
+  Side<R> own;
   load_side(m, U, c, own);
   double r[12], re[3] = {0.0, 0.0, 0.0};
 #pragma unroll
@@ -345,44 +414,53 @@ __global__ void __launch_bounds__(128) k_nonlinear(DeviceMesh m, const double* _
   // ---- cell terms
 #pragma unroll 1
   for (int q = 0; q < kCellQ; ++q) {
-    double u0 = 0, u1 = 0, d00 = 0, d01 = 0, d10 = 0, d11 = 0;  // d_ca = d u_c / d x_a
+    R u0 = 0, u1 = 0, d00 = 0, d01 = 0, d10 = 0, d11 = 0;  // d_ca = d u_c / d x_a
 #pragma unroll
     for (int j = 0; j < 12; ++j) {
-      const double cj = own.c[j];
-      u0 = fma(cj, c_tab.cq_psi[q][j][0], u0);
-      u1 = fma(cj, c_tab.cq_psi[q][j][1], u1);
-      d00 = fma(cj, c_tab.cq_dpsi[q][j][0][0], d00);
-      d01 = fma(cj, c_tab.cq_dpsi[q][j][0][1], d01);
-      d10 = fma(cj, c_tab.cq_dpsi[q][j][1][0], d10);
-      d11 = fma(cj, c_tab.cq_dpsi[q][j][1][1], d11);
+      const R cj = own.c[j];
+      u0 = fma(cj, T.cq_psi[q][j][0], u0);
+      u1 = fma(cj, T.cq_psi[q][j][1], u1);
+      d00 = fma(cj, T.cq_dpsi[q][j][0][0], d00);
+      d01 = fma(cj, T.cq_dpsi[q][j][0][1], d01);
+      d10 = fma(cj, T.cq_dpsi[q][j][1][0], d10);
+      d11 = fma(cj, T.cq_dpsi[q][j][1][1], d11);
     }
-    const double h = own.h[0] * c_tab.cq_phi[q][0] + own.h[1] * c_tab.cq_phi[q][1] + own.h[2] * c_tab.cq_phi[q][2];
-    const double v0 = own.G00 * u0 + own.G01 * u1;
-    const double v1 = own.G01 * u0 + own.G11 * u1;
-    const double wq = c_tab.cq_w[q];
-    const double half_ke = 0.5 * (u0 * v0 + u1 * v1);
-    const double t0 = v1 * d00 - v0 * d01;  // d_tau u_hat
-    const double t1 = v1 * d10 - v0 * d11;
+    const R h = own.h[0] * T.cq_phi[q][0] + own.h[1] * T.cq_phi[q][1] + own.h[2] * T.cq_phi[q][2];
+    const R v0 = own.G00 * u0 + own.G01 * u1;
+    const R v1 = own.G01 * u0 + own.G11 * u1;
+    const R wq = T.cq_w[q];
+    const R half_ke = R(0.5) * (u0 * v0 + u1 * v1);
+    const R t0 = v1 * d00 - v0 * d01;  // d_tau u_hat
+    const R t1 = v1 * d10 - v0 * d11;
     // coefficients of psi_i0, psi_i1, d0 psi_i0, d1 psi_i0, d0 psi_i1, d1 psi_i1
-    const double k0 = -t1 * wq, k1 = t0 * wq;
-    const double k2 = (-u1 * v1 + half_ke) * wq, k3 = (u1 * v0) * wq;
-    const double k4 = (u0 * v1) * wq, k5 = (-u0 * v0 + half_ke) * wq;
+    const R k0 = -t1 * wq, k1 = t0 * wq;
+    const R k2 = (-u1 * v1 + half_ke) * wq, k3 = (u1 * v0) * wq;
+    const R k4 = (u0 * v1) * wq, k5 = (-u0 * v0 + half_ke) * wq;
 #pragma unroll
     for (int i = 0; i < 12; ++i) {
-      double t = k0 * c_tab.cq_psi[q][i][0];
-      t = fma(k1, c_tab.cq_psi[q][i][1], t);
-      t = fma(k2, c_tab.cq_dpsi[q][i][0][0], t);
-      t = fma(k3, c_tab.cq_dpsi[q][i][0][1], t);
-      t = fma(k4, c_tab.cq_dpsi[q][i][1][0], t);
-      t = fma(k5, c_tab.cq_dpsi[q][i][1][1], t);
-      r[i] += t;
+      R t = k0 * T.cq_psi[q][i][0];
+      t = fma(k1, T.cq_psi[q][i][1], t);
+      t = fma(k2, T.cq_dpsi[q][i][0][0], t);
+      t = fma(k3, T.cq_dpsi[q][i][0][1], t);
+      t = fma(k4, T.cq_dpsi[q][i][1][0], t);
+      t = fma(k5, T.cq_dpsi[q][i][1][1], t);
+      r[i] += (double)t;
     }
-    const double hw = h * wq;
-    re[0] -= (u0 + u1) * hw;
-    re[1] += u0 * hw;
-    re[2] += u1 * hw;
+    if (kStrongDG) {
+      // div_hat(u_hat h_hat) = h_hat (d00 + d11) + u_hat . grad_hat h_hat (DG1: constant gradient)
+      const R divu = own.dv[0] * T.cq_phi[q][0] + own.dv[1] * T.cq_phi[q][1] + own.dv[2] * T.cq_phi[q][2];
+      const R g = h * divu + u0 * (own.h[1] - own.h[0]) + u1 * (own.h[2] - own.h[0]);
+      const R gw = g * wq;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) re[k] -= (double)(gw * T.cq_phi[q][k]);
+    } else {
+      const R hw = h * wq;
+      re[0] -= (double)((u0 + u1) * hw);
+      re[1] += (double)(u0 * hw);
+      re[2] += (double)(u1 * hw);
+    }
   }
-  const double idet2 = 1.0 / (own.det * own.det);
+  const double idet2 = 1.0 / ((double)own.det * (double)own.det);
 #pragma unroll
   for (int i = 0; i < 12; ++i) r[i] *= idet2;
   // ---- facet terms
@@ -394,33 +472,33 @@ __global__ void __launch_bounds__(128) k_nonlinear(DeviceMesh m, const double* _
     const unsigned lpos = m.edge_lpos[e];
     const int64_t nbr = plus ? m.edge_minus[e] : m.edge_plus[e];
     const int nloc = plus ? (int)(lpos >> 2) : (int)(lpos & 3u);
-    Side nb;
+    Side<R> nb;
     load_side(m, U, nbr, nb);
 #pragma unroll 1
     for (int p = 0; p < kFacetQ; ++p) {
-      const double wp = c_tab.fq_w[p];
+      const R wp = T.fq_w[p];
       if (plus) {
-        FacetValues f = facet_point(own, i, nb, nloc, p, upwind);
-        const double sc = -wp * f.tan / own.det;
+        FacetValues<R> f = facet_point(own, i, nb, nloc, p, upwind);
+        const R sc = -wp * f.tan / own.det;
 #pragma unroll
         for (int j = 0; j < 12; ++j) {
-          double q = f.up0 * c_tab.fq_psi[0][i][p][j][1] - f.up1 * c_tab.fq_psi[0][i][p][j][0];
-          r[j] = fma(sc, q, r[j]);
+          R qv = f.up0 * T.fq_psi[0][i][p][j][1] - f.up1 * T.fq_psi[0][i][p][j][0];
+          r[j] += (double)(sc * qv);
         }
-        const double fh = -wp * f.flux * f.hup;
+        const R fh = kStrongDG ? wp * f.flux * (f.hp - f.hup) : -wp * f.flux * f.hup;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) re[k] = fma(fh, c_tab.fq_phi[0][i][p][k], re[k]);
+        for (int k = 0; k < 3; ++k) re[k] += (double)(fh * T.fq_phi[0][i][p][k]);
       } else {
-        FacetValues f = facet_point(nb, nloc, own, i, p, upwind);
-        const double sc = wp * f.tan / own.det;
+        FacetValues<R> f = facet_point(nb, nloc, own, i, p, upwind);
+        const R sc = wp * f.tan / own.det;
 #pragma unroll
         for (int j = 0; j < 12; ++j) {
-          double q = f.um0 * c_tab.fq_psi[1][i][p][j][1] - f.um1 * c_tab.fq_psi[1][i][p][j][0];
-          r[j] = fma(sc, q, r[j]);
+          R qv = f.um0 * T.fq_psi[1][i][p][j][1] - f.um1 * T.fq_psi[1][i][p][j][0];
+          r[j] += (double)(sc * qv);
         }
-        const double fh = wp * f.flux * f.hup;
+        const R fh = kStrongDG ? wp * f.flux * (f.hup - f.hm) : wp * f.flux * f.hup;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) re[k] = fma(fh, c_tab.fq_phi[1][i][p][k], re[k]);
+        for (int k = 0; k < 3; ++k) re[k] += (double)(fh * T.fq_phi[1][i][p][k]);
       }
     }
   }
@@ -431,11 +509,11 @@ __global__ void __launch_bounds__(128) k_nonlinear(DeviceMesh m, const double* _
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     double v = sg[k] * r[k];
-    if (k < 9) atomicAdd(&R[dof[k]], v);
-    else R[dof[k]] = v;
+    if (k < 9) atomicAdd(&Rout[dof[k]], v);
+    else Rout[dof[k]] = v;
   }
 #pragma unroll
-  for (int k = 0; k < 3; ++k) R[m.n_u + 3 * c + k] = re[k];
+  for (int k = 0; k < 3; ++k) Rout[m.n_u + 3 * c + k] = re[k];
 }
 
 __global__ void k_m2inv(DeviceMesh m, const double* __restrict__ r, int64_t rstride, double* out,
@@ -458,31 +536,33 @@ __global__ void k_m2inv(DeviceMesh m, const double* __restrict__ r, int64_t rstr
 }
 
 // out[m][j] = sum_k A[m][k] in[k][j]; MT output rows per block row, whose
-// nonzero k range is k < lim[tile] when lim is given.
-template <int MT>
+// nonzero k range is k < lim[tile] when lim is given.  TA: accumulation type
+// (double on the FP64 path, float in mixed precision).
+template <int MT, typename TA>
 __global__ void __launch_bounds__(256) k_combine(const double* __restrict__ A, int Mo, int Ki,
                                                  const int* __restrict__ lim, const double* __restrict__ in,
                                                  int64_t in_stride, double* out, int64_t out_stride, int64_t len) {
-  extern __shared__ double sA[];  // [MT][Ki]
+  extern __shared__ __align__(16) unsigned char sA_raw[];
+  TA* sA = reinterpret_cast<TA*>(sA_raw);  // [MT][Ki]
   const int m0 = blockIdx.y * MT;
   const int kn = lim ? lim[blockIdx.y] : Ki;
   for (int t = threadIdx.x; t < MT * Ki; t += blockDim.x) {
     int mm = m0 + t / Ki, k = t % Ki;
-    sA[t] = mm < Mo ? A[(int64_t)mm * Ki + k] : 0.0;
+    sA[t] = mm < Mo ? (TA)A[(int64_t)mm * Ki + k] : TA(0);
   }
   __syncthreads();
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < len; j += (int64_t)gridDim.x * blockDim.x) {
-    double acc[MT];
+    TA acc[MT];
 #pragma unroll
-    for (int t = 0; t < MT; ++t) acc[t] = 0.0;
+    for (int t = 0; t < MT; ++t) acc[t] = TA(0);
     for (int k = 0; k < kn; ++k) {
-      const double v = __ldg(&in[(int64_t)k * in_stride + j]);
+      const TA v = (TA)__ldg(&in[(int64_t)k * in_stride + j]);
 #pragma unroll
       for (int t = 0; t < MT; ++t) acc[t] = fma(sA[t * Ki + k], v, acc[t]);
     }
 #pragma unroll
     for (int t = 0; t < MT; ++t)
-      if (m0 + t < Mo) out[(int64_t)(m0 + t) * out_stride + j] = acc[t];
+      if (m0 + t < Mo) out[(int64_t)(m0 + t) * out_stride + j] = (double)acc[t];
   }
 }
 
@@ -586,9 +666,10 @@ cudaError_t launch_apply_K(const DeviceMesh& m, const double* U, double s, doubl
 }
 
 cudaError_t launch_nonlinear_rhs(const DeviceMesh& m, const double* U, double* r, int B, int upwind,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, bool fp32) {
   dim3 grid((unsigned)((m.F + 127) / 128), (unsigned)B);
-  k_nonlinear<<<grid, 128, 0, st>>>(m, U, r, upwind);
+  if (fp32) k_nonlinear<float><<<grid, 128, 0, st>>>(m, U, r, upwind);
+  else k_nonlinear<double><<<grid, 128, 0, st>>>(m, U, r, upwind);
   return cudaGetLastError();
 }
 
@@ -602,17 +683,19 @@ cudaError_t launch_m2inv(const DeviceMesh& m, const double* r, int64_t rstride, 
 int combine_tile() { return 8; }
 
 cudaError_t launch_combine(const double* A, int Mo, int Ki, const int* lim, const double* in, int64_t in_stride,
-                           double* out, int64_t out_stride, int64_t len, cudaStream_t st) {
+                           double* out, int64_t out_stride, int64_t len, cudaStream_t st, bool fp32) {
   constexpr int MT = 8;
-  size_t smem = sizeof(double) * MT * Ki;
+  const size_t smem = (fp32 ? sizeof(float) : sizeof(double)) * MT * Ki;
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_combine<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_combine<MT, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_combine<MT, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
   dim3 grid((unsigned)grid_for(len, 256, 152 * 4), (unsigned)((Mo + MT - 1) / MT));
-  k_combine<MT><<<grid, 256, smem, st>>>(A, Mo, Ki, lim, in, in_stride, out, out_stride, len);
+  if (fp32) k_combine<MT, float><<<grid, 256, smem, st>>>(A, Mo, Ki, lim, in, in_stride, out, out_stride, len);
+  else k_combine<MT, double><<<grid, 256, smem, st>>>(A, Mo, Ki, lim, in, in_stride, out, out_stride, len);
   return cudaGetLastError();
 }
 

@@ -45,23 +45,37 @@ void build_reference_element(RefElement* el);
 // Gauss-Legendre on [0, 1].
 void gauss_legendre01(int n, double* x, double* w);
 
-// Tables copied to __constant__ memory for the kernels.
-struct ConstTables {
-  double D[3][12];             // int_ref phi_i div psi_j
-  double M2inv_ref[3][3];      // inverse of int_ref phi_i phi_j (M2^{-1} = M2inv_ref / det)
-  double M2_ref[3][3];         // int_ref phi_i phi_j (M2 = det * M2_ref)
+// Tables copied to __constant__ memory for the kernels (one copy in FP64 and
+// one in FP32; every member is an array of R, so the two layouts correspond
+// element by element).
+template <typename R>
+struct TablesT {
+  R D[3][12];             // int_ref phi_i div psi_j
+  R M2inv_ref[3][3];      // inverse of int_ref phi_i phi_j (M2^{-1} = M2inv_ref / det)
+  R M2_ref[3][3];         // int_ref phi_i phi_j (M2 = det * M2_ref)
   // cell rule for N: points, weights and basis data
-  double cq_w[kCellQ];
-  double cq_psi[kCellQ][12][2];
-  double cq_dpsi[kCellQ][12][2][2];
-  double cq_phi[kCellQ][3];
+  R cq_w[kCellQ];
+  R cq_psi[kCellQ][12][2];
+  R cq_dpsi[kCellQ][12][2][2];
+  R cq_phi[kCellQ][3];
   // facet rule: for each local edge (3) and each point, the reference basis at
   // tau (plus side: counter-clockwise parameter tau) and at 1 - tau (minus side)
-  double fq_w[kFacetQ];
-  double fq_psi[2][3][kFacetQ][12][2];   // [side][local edge][point]
-  double fq_phi[2][3][kFacetQ][3];
-  double edge_dir[3][2];
+  R fq_w[kFacetQ];
+  R fq_psi[2][3][kFacetQ][12][2];   // [side][local edge][point]
+  R fq_phi[2][3][kFacetQ][3];
+  R edge_dir[3][2];
+  R div_vert[12][3];      // div_hat psi_j at the reference vertices (a P1 function)
 };
+using ConstTables = TablesT<double>;
+
+inline TablesT<float> tables_to_float(const ConstTables& t) {
+  static_assert(sizeof(ConstTables) == 2 * sizeof(TablesT<float>), "tables must be plain arrays");
+  TablesT<float> f;
+  const double* src = reinterpret_cast<const double*>(&t);
+  float* dst = reinterpret_cast<float*>(&f);
+  for (size_t i = 0; i < sizeof(ConstTables) / sizeof(double); ++i) dst[i] = (float)src[i];
+  return f;
+}
 
 // Per-cell data in structure-of-arrays form.
 struct HostCellData {

@@ -495,6 +495,12 @@ void build_cell_data(const Mesh& m, const RefElement& el, double omega, HostCell
         tab->fq_phi[side][i][p][2] = y;
       }
   for (int i = 0; i < 3; ++i) { tab->edge_dir[i][0] = kEdgeDir[i][0]; tab->edge_dir[i][1] = kEdgeDir[i][1]; }
+  const double vx[3] = {0.0, 1.0, 0.0}, vy[3] = {0.0, 0.0, 1.0};
+  for (int v = 0; v < 3; ++v) {
+    double g[12][2][2];
+    el.eval_grad(vx[v], vy[v], g);
+    for (int j = 0; j < 12; ++j) tab->div_vert[j][v] = g[j][0][0] + g[j][1][1];
+  }
 
   // self-check of the degree-5 rule
   for (int p = 0; p <= 5; ++p)

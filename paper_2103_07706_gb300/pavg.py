@@ -21,6 +21,8 @@ PAVG_UPWIND_STANDARD = 0
 PAVG_UPWIND_AS_PRINTED = 1
 PAVG_SOLVER_MIXED = 0
 PAVG_SOLVER_FP64 = 1
+PAVG_PRECISION_FP64 = 0
+PAVG_PRECISION_MIXED = 1
 
 ERRORS = {
     -1: "PAVG_ERR_INVAL", -2: "PAVG_ERR_NOMEM", -3: "PAVG_ERR_CUDA", -4: "PAVG_ERR_NOCONV",
@@ -49,6 +51,7 @@ class Params(ctypes.Structure):
         ("quad_rule", ctypes.c_int),
         ("upwind_convention", ctypes.c_int),
         ("solver", ctypes.c_int),
+        ("precision", ctypes.c_int),
     ]
 
 

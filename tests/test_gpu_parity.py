@@ -12,7 +12,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 RTOL = 1e-12
-LAM = {0: 0.00036, 1: 0.00072, 2: 0.00142, 3: 0.00286, 4: 0.0057}
+LAM = {0: 0.00036, 1: 0.00072, 2: 0.00142, 3: 0.00286, 4: 0.0057}  # lambda_max per refinement (H = 5000 m)
 _GPU = {}
 
 
