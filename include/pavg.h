@@ -193,6 +193,80 @@ int pavg_kernel_time(pavg_ctx* ctx, double* total_ms, int* launches);
 /* Readable message of the last failure (static storage owned by the context). */
 const char* pavg_last_error(const pavg_ctx* ctx);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent instances evaluated together.
+ *
+ * A batch groups n contexts (any refinements and parameters, each with the
+ * mixed M1 solver, the default).  pavg_batch_averaged_rhs computes, for every
+ * instance i, out_i = N-bar(U_i) with its own window T_i and shift count M_i
+ * (Sec. 2.2, Eq. vt_discretised, evaluated as pavg_averaged_rhs does).  The
+ * single-vector Chebyshev chains of all instances (Sec. 2.4) run in ONE
+ * persistent cooperative launch, each instance on its own range of blocks
+ * that synchronise only among themselves; likewise every instance's Clenshaw
+ * sum.  The shift contractions and N run per instance between the two
+ * launches.  Everything between the input and output copies is captured once
+ * per (T_i, M_i) list in a CUDA graph and replayed.
+ *
+ * The grid of the persistent launches is chosen by an autotuner: threads per
+ * block (128 or 256, i.e. 32 or 64 cells per block-pass), co-resident blocks
+ * per SM, whether the FP32 element matrices stay in shared memory, and how
+ * blocks are shared among instances.  It times each candidate on a few steps
+ * of the real forward chains (per-instance device timers) and keeps the one
+ * with the smallest predicted launch time.  Results of different
+ * configurations differ only by rounding; a fixed configuration gives
+ * bit-identical results on every call.
+ *
+ * A context may belong to one batch at a time and must not be used by other
+ * calls while a batch call on it is in flight.  The contexts must outlive the
+ * batch.  Per-instance errors are latched in each context (pavg_sync,
+ * pavg_get_stats on the context); pavg_batch_sync reports the first.
+ * ------------------------------------------------------------------------ */
+typedef struct pavg_batch pavg_batch; /* opaque, library-owned */
+
+typedef struct {
+  int threads;        /* 128 or 256 */
+  int blocks_per_sm;  /* co-resident blocks of the persistent launch per SM */
+  int resident;       /* 1: FP32 element matrices in shared memory; 0: streamed from L2 */
+  int weighting;      /* blocks per instance proportional to 0: cells x chain steps, 1: cells */
+  double predicted_ms;/* autotuner's predicted forward-chain launch time (0 when set by hand) */
+} pavg_batch_config;
+
+/* ctxs: host array of n distinct contexts on the current device, n >= 1.
+ * Errors: INVAL (null, n < 1, a repeated context, a context with the FP64
+ * solver or on another device), NOMEM. */
+int pavg_batch_create(pavg_ctx* const* ctxs, int n, pavg_batch** out);
+int pavg_batch_destroy(pavg_batch* b);
+
+/* T, M: host arrays of n windows (seconds, >= 0) and shift counts (>= 1).
+ * U, out: host arrays of n device pointers, instance i's state and result
+ * (n_i doubles each, not aliasing).  Autotunes on the first call when no
+ * configuration is set. */
+int pavg_batch_averaged_rhs(pavg_batch* b, const double* T, const int* M, const double* const* U,
+                            double* const* out, void* stream);
+
+/* Runs the autotuner on these inputs (the work of one call's forward chains,
+ * truncated to a few steps per candidate), keeps the best configuration and
+ * returns it.  Synchronises `stream`. */
+int pavg_batch_autotune(pavg_batch* b, const double* T, const int* M, const double* const* U, void* stream,
+                        pavg_batch_config* best);
+/* Sets or reads the configuration used by later calls (captured graphs of
+ * another configuration are dropped).  Set: INVAL when the configuration
+ * cannot be launched co-resident for some (T, M) list at call time, reported
+ * then by pavg_batch_averaged_rhs. */
+int pavg_batch_set_config(pavg_batch* b, const pavg_batch_config* cfg);
+int pavg_batch_get_config(const pavg_batch* b, pavg_batch_config* cfg);
+
+/* Durations of the two persistent launches of the last pavg_batch_averaged_rhs
+ * (forward chains, Clenshaw sums), from events inside the graph; host
+ * outputs, synchronises on the last event. */
+int pavg_batch_kernel_time(pavg_batch* b, double* forward_ms, double* backward_ms);
+
+/* Wait for the batch's work on `stream`; the first latched instance error. */
+int pavg_batch_sync(pavg_batch* b, void* stream);
+
+/* Readable message of the batch's last failure. */
+const char* pavg_batch_last_error(const pavg_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,12 +16,9 @@
 
 using namespace pavg;
 
-#include "context.h"
+#include "api_internal.h"
 
-using pavg_detail::AvgPlan;
-using pavg_detail::EventPair;
-
-namespace {
+namespace pavg_api {
 
 #ifndef PAVG_MIXED_SOLVE_RTOL
 #define PAVG_MIXED_SOLVE_RTOL 1e-5
@@ -34,33 +31,7 @@ int set_err(pavg_ctx* c, int code, const std::string& msg) {
   return code;
 }
 
-#define CK(call)                                                                        \
-  do {                                                                                  \
-    cudaError_t e_ = (call);                                                            \
-    if (e_ != cudaSuccess)                                                              \
-      return set_err(ctx, PAVG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
-  } while (0)
-
-template <class T>
-cudaError_t dalloc(T** p, size_t count) {
-  return cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
-}
-
-template <class T>
-cudaError_t upload(T** p, const std::vector<T>& v) {
-  cudaError_t e = dalloc(p, v.size());
-  if (e != cudaSuccess) return e;
-  return cudaMemcpy(*p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
-}
-
 cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
-
-// Counts one of this library's kernels and checks its launch.
-#define KL(call)          \
-  do {                    \
-    ++ctx->launches;      \
-    CK(call);             \
-  } while (0)
 
 void begin_call(pavg_ctx* ctx) {
   ctx->launches = 0;
@@ -265,6 +236,21 @@ int get_plan(pavg_ctx* ctx, double T, int M, AvgPlan** out) {
   return PAVG_OK;
 }
 
+int enq_avg_shifts(pavg_ctx* ctx, const AvgPlan& pl, cudaStream_t st) {
+  const DeviceMesh& m = ctx->dm;
+  const int64_t n = m.n;
+  const int K = pl.K, M = pl.M;
+  double* Q = ctx->Q;
+  const bool fp32 = ctx->p.precision == PAVG_PRECISION_MIXED;
+  KL(launch_combine(pl.dA, M, K + 1, pl.dlimA, Q, n, ctx->Um, n, n, st, fp32));
+  CK(cudaMemset2DAsync(ctx->Rm, sizeof(double) * n, 0, sizeof(double) * 3 * m.E, M, st));
+  KL(launch_nonlinear_rhs(m, ctx->Um, ctx->Rm, M, ctx->p.upwind_convention, st, fp32));
+  // the weighted sum over shifts stays FP64 in every precision: the average
+  // cancels most of the oscillating terms, so rounding here is amplified
+  KL(launch_combine(pl.dB, K + 1, M, pl.dlimB, ctx->Rm, n, Q, n, n, st));  // y_k overwrite Q_k
+  return PAVG_OK;
+}
+
 // Shared-basis averaged nonlinearity (Sec. 2.2, Eq. vt_discretised):
 //   U_m = sum_k c_k(lam|s_m|) sgn(s_m)^k Q_k,  Q_k = Q_k(L/lam) U      (forward)
 //   r_m = weak-form N(U_m)                                             (Sec. 2.5)
@@ -277,7 +263,7 @@ int get_plan(pavg_ctx* ctx, double T, int M, AvgPlan** out) {
 int enq_avg(pavg_ctx* ctx, const AvgPlan& pl, const double* U, double* out, cudaStream_t st) {
   const DeviceMesh& m = ctx->dm;
   const int64_t n = m.n;
-  const int K = pl.K, M = pl.M;
+  const int K = pl.K;
   if (pl.T == 0.0) return enq_nonlinear(ctx, U, out, ctx->Rm, st);
   double* Q = ctx->Q;
   CK(cudaMemcpyAsync(Q, U, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
@@ -286,13 +272,8 @@ int enq_avg(pavg_ctx* ctx, const AvgPlan& pl, const double* U, double* out, cuda
                       k == 0 ? nullptr : Q + (int64_t)(k - 1) * n, Q + (int64_t)(k + 1) * n, st);
     if (rc) return rc;
   }
-  const bool fp32 = ctx->p.precision == PAVG_PRECISION_MIXED;
-  KL(launch_combine(pl.dA, M, K + 1, pl.dlimA, Q, n, ctx->Um, n, n, st, fp32));
-  CK(cudaMemset2DAsync(ctx->Rm, sizeof(double) * n, 0, sizeof(double) * 3 * m.E, M, st));
-  KL(launch_nonlinear_rhs(m, ctx->Um, ctx->Rm, M, ctx->p.upwind_convention, st, fp32));
-  // the weighted sum over shifts stays FP64 in every precision: the average
-  // cancels most of the oscillating terms, so rounding here is amplified
-  KL(launch_combine(pl.dB, K + 1, M, pl.dlimB, ctx->Rm, n, Q, n, n, st));  // y_k overwrite Q_k
+  int rc0 = enq_avg_shifts(ctx, pl, st);
+  if (rc0) return rc0;
   double* b[3] = {ctx->vec[0], ctx->vec[1], ctx->vec[2]};
   const double* b1 = nullptr;  // b_{k+1}
   const double* b2 = nullptr;  // b_{k+2}
@@ -437,7 +418,9 @@ bool valid_params(const pavg_params* p) {
          (p->precision == PAVG_PRECISION_FP64 || p->precision == PAVG_PRECISION_MIXED);
 }
 
-}  // namespace
+}  // namespace pavg_api
+
+using namespace pavg_api;
 
 extern "C" {
 
@@ -482,7 +465,10 @@ int pavg_create(const pavg_params* p, pavg_ctx** out) {
     HostCellData hc;
     ConstTables tab;
     build_cell_data(ctx->mesh, el, p->omega, &hc, &tab);
-    if (upload_tables(tab) != cudaSuccess) { rc = set_err(ctx, PAVG_ERR_CUDA, "constant upload failed"); throw 0; }
+    if (upload_tables(tab) != cudaSuccess || upload_chain_tables(tab) != cudaSuccess) {
+      rc = set_err(ctx, PAVG_ERR_CUDA, "constant upload failed");
+      throw 0;
+    }
     const Mesh& ms = ctx->mesh;
     DeviceMesh& m = ctx->dm;
     m.F = ms.F(); m.E = ms.E(); m.n_u = 3 * m.E + 3 * m.F; m.n_eta = 3 * m.F; m.n = m.n_u + m.n_eta;
@@ -513,7 +499,8 @@ int pavg_create(const pavg_params* p, pavg_ctx** out) {
     CgIrWork& wi = ctx->cgi;
     ok = ok && cg_ir_configure(m.F, &wi) == cudaSuccess;
     // FP32 element matrices: packed for the shared-memory path, row blocks when streamed
-    if (ok) ok = wi.smem > 0 ? upload(&m.M1p, hc.M1p) == cudaSuccess : upload(&m.M1f, hc.M1f) == cudaSuccess;
+    // (the batched kernel may take either path for any mesh)
+    if (ok) ok = upload(&m.M1p, hc.M1p) == cudaSuccess && upload(&m.M1f, hc.M1f) == cudaSuccess;
     ok = ok && dalloc(&wi.x[0], m.n_u) == cudaSuccess && dalloc(&wi.x[1], m.n_u) == cudaSuccess &&
          dalloc(&wi.ax, m.n_u) == cudaSuccess && dalloc(&wi.r64, m.n_u) == cudaSuccess &&
          dalloc(&wi.fbuf, 9 * 4 * (size_t)(m.E + m.F)) == cudaSuccess &&

@@ -1,0 +1,589 @@
+// C-ABI of instance batches (declared in include/pavg.h): several contexts
+// evaluate their averaged nonlinearities together, their recurrences in one
+// persistent launch per direction (k_chain, batch.cu), with an autotuned grid.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "api_internal.h"
+
+using namespace pavg_api;
+
+namespace {
+
+// Batch-level variants of the error macros (they report into the batch).
+#define BCK(call)                                                                        \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return bset_err(b, PAVG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr int kTuneSteps = 4;  // chain steps per autotuning candidate
+
+struct Config {
+  int nt = 256, bps = 3, res = 0, weighting = 0;
+  double predicted_ms = 0.0;
+};
+
+bool same(const Config& a, const Config& c) {
+  return a.nt == c.nt && a.bps == c.bps && a.res == c.res && a.weighting == c.weighting;
+}
+
+// One launch of k_chain: its problems (uploaded) and its grid.
+struct Launch {
+  std::vector<ChainProblem> probs;
+  ChainProblem* d = nullptr;
+  int blocks = 0;
+  size_t smem = 0;
+};
+
+struct BatchPlan {
+  std::vector<int> K;              // per instance (-1: T = 0, N only)
+  std::vector<AvgPlan*> pl;        // per instance (null for T = 0)
+  Launch fwd, bwd;
+  Config cfg;
+  cudaGraphExec_t exec = nullptr;
+  int launches = 0;
+  std::vector<const double*> ws;   // Q, Um, Rm of every instance when captured
+};
+
+}  // namespace
+
+struct pavg_batch {
+  std::vector<pavg_ctx*> ctx;
+  int device = 0, sms = 0;
+  // per-instance scratch of the persistent launches
+  std::vector<double*> partial;
+  std::vector<float*> partial_f;
+  std::vector<double*> scal;
+  unsigned long long* sync = nullptr;   // [2][n][8]: forward launch, backward launch
+  unsigned long long* timer = nullptr;  // [n][2]
+  Config cfg;
+  bool have_cfg = false;
+  std::map<std::vector<std::pair<double, int>>, BatchPlan> plans;
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t ev[4] = {};
+  bool ev_recorded = false;
+  std::string err;
+};
+
+namespace {
+
+int bset_err(pavg_batch* b, int code, const std::string& msg) {
+  if (b) b->err = msg;
+  return code;
+}
+
+int64_t cells_of(const pavg_batch* b, int i) { return b->ctx[i]->dm.F; }
+
+// Blocks per problem: total blocks shared in proportion to the weights, at
+// least one and at most one per NT/4 cells for each problem.  False when the
+// problems do not fit.
+bool share_blocks(const std::vector<int64_t>& F, const std::vector<int>& steps, int total, int nt, int weighting,
+                  std::vector<int>* nb) {
+  const int P = (int)F.size();
+  nb->assign(P, 1);
+  if (P > total) return false;
+  std::vector<int64_t> need(P);
+  std::vector<double> w(P);
+  double wsum = 0.0;
+  for (int p = 0; p < P; ++p) {
+    need[p] = (F[p] + nt / 4 - 1) / (nt / 4);
+    w[p] = (double)F[p] * (weighting == 0 ? std::max(steps[p], 1) : 1);
+    wsum += w[p];
+  }
+  int used = P;
+  for (int p = 0; p < P; ++p) {
+    const int64_t t = std::min<int64_t>(need[p], (int64_t)std::floor(total * w[p] / wsum));
+    if (t > 1) { used += (int)t - 1; (*nb)[p] = (int)t; }
+  }
+  while (used > total) {  // the floor of each share can still overshoot by the minimum of one block
+    int q = (int)(std::max_element(nb->begin(), nb->end()) - nb->begin());
+    --(*nb)[q];
+    --used;
+  }
+  while (used < total) {  // the rest to the problem with the most work per block
+    int q = -1;
+    double best = 0.0;
+    for (int p = 0; p < P; ++p)
+      if ((*nb)[p] < need[p] && w[p] / (*nb)[p] > best) { best = w[p] / (*nb)[p]; q = p; }
+    if (q < 0) break;
+    ++(*nb)[q];
+    ++used;
+  }
+  return true;
+}
+
+// Problems of one direction (mode 0 forward chains, 1 Clenshaw sums) for the
+// instances `idx`, grid from the configuration.  max_steps < 0: full chains.
+int build_launch(pavg_batch* b, const BatchPlan& bp, int mode, const std::vector<int>& idx, const Config& cfg,
+                 int max_steps, bool timers, Launch* L) {
+  L->probs.clear();
+  L->blocks = 0;
+  L->smem = 0;
+  if (idx.empty()) return PAVG_OK;
+  std::vector<int64_t> F;
+  std::vector<int> steps;
+  for (int i : idx) {
+    F.push_back(cells_of(b, i));
+    int s = mode == 0 ? bp.K[i] : bp.K[i] + 1;
+    if (max_steps >= 0) s = std::min(s, max_steps);
+    steps.push_back(s);
+  }
+  int per_sm = 0;
+  if (chain_occupancy(cfg.nt, false, 0, &per_sm) != cudaSuccess)
+    return bset_err(b, PAVG_ERR_CUDA, "occupancy query failed");
+  if (per_sm < cfg.bps && !cfg.res) return bset_err(b, PAVG_ERR_INVAL, "configuration does not fit an SM");
+  const int total = cfg.bps * b->sms;
+  std::vector<int> nb;
+  if (!share_blocks(F, steps, total, cfg.nt, cfg.weighting, &nb))
+    return bset_err(b, PAVG_ERR_INVAL, "more instances than co-resident blocks");
+  if (cfg.res) {
+    size_t smem = 0;
+    for (size_t p = 0; p < idx.size(); ++p) {
+      if (!b->ctx[idx[p]]->dm.M1p) return bset_err(b, PAVG_ERR_INVAL, "resident path needs packed matrices");
+      smem = std::max(smem, chain_res_smem(F[p], nb[p], cfg.nt));
+    }
+    if (smem > 200 * 1024) return bset_err(b, PAVG_ERR_INVAL, "resident matrices do not fit shared memory");
+    if (chain_occupancy(cfg.nt, true, smem, &per_sm) != cudaSuccess)
+      return bset_err(b, PAVG_ERR_CUDA, "occupancy query failed");
+    if (per_sm < cfg.bps) return bset_err(b, PAVG_ERR_INVAL, "resident configuration does not fit an SM");
+    L->smem = smem;
+  }
+  int block0 = 0;
+  for (size_t p = 0; p < idx.size(); ++p) {
+    const int i = idx[p];
+    pavg_ctx* c = b->ctx[i];
+    ChainProblem pr{};
+    pr.m = c->dm;
+    pr.w = c->cgi;
+    pr.cp = c->cgip;
+    pr.g = c->p.g;
+    pr.H = c->p.H;
+    pr.lam = c->lam;
+    pr.ru = c->ru;
+    pr.Q = c->Q;
+    pr.bufs[0] = c->vec[0];
+    pr.bufs[1] = c->vec[1];
+    pr.bufs[2] = c->vec[2];
+    pr.out = c->io_out;
+    pr.partial = b->partial[i];
+    pr.partial_f = b->partial_f[i];
+    pr.scal = b->scal[i];
+    pr.sync = b->sync + ((size_t)mode * b->ctx.size() + i) * 8;
+    pr.timer = timers ? b->timer + 2 * (size_t)i : nullptr;
+    pr.mode = mode;
+    pr.K = max_steps >= 0 ? std::min(bp.K[i], max_steps) : bp.K[i];
+    pr.block0 = block0;
+    pr.nblocks = nb[p];
+    block0 += nb[p];
+    L->probs.push_back(pr);
+  }
+  L->blocks = block0;
+  return PAVG_OK;
+}
+
+int upload_launch(pavg_batch* b, Launch* L) {
+  if (L->probs.empty()) return PAVG_OK;
+  if (!L->d) BCK(cudaMalloc((void**)&L->d, sizeof(ChainProblem) * b->ctx.size()));
+  BCK(cudaMemcpy(L->d, L->probs.data(), sizeof(ChainProblem) * L->probs.size(), cudaMemcpyHostToDevice));
+  return PAVG_OK;
+}
+
+int enq_launch(pavg_batch* b, const Launch& L, const Config& c, int mode, int max_steps, cudaStream_t st) {
+  if (L.probs.empty()) return PAVG_OK;
+  BCK(cudaMemsetAsync(b->sync + (size_t)mode * b->ctx.size() * 8, 0, sizeof(unsigned long long) * 8 * b->ctx.size(),
+                      st));
+  BCK(launch_chain(L.d, (int)L.probs.size(), L.blocks, c.nt, c.res != 0, L.smem, max_steps, st));
+  return PAVG_OK;
+}
+
+int drop_exec(BatchPlan* bp) {
+  if (bp->exec) cudaGraphExecDestroy(bp->exec);
+  bp->exec = nullptr;
+  return PAVG_OK;
+}
+
+void free_launch(Launch* L) {
+  cudaFree(L->d);
+  L->d = nullptr;
+}
+
+// Plan of a (T_i, M_i) list: per-instance plans and workspaces.  A workspace
+// that grows moves its buffers, so every captured batch graph is dropped.
+int get_batch_plan(pavg_batch* b, const double* T, const int* M, BatchPlan** out) {
+  const int n = (int)b->ctx.size();
+  std::vector<std::pair<double, int>> key(n);
+  for (int i = 0; i < n; ++i) {
+    if (!(T[i] >= 0.0) || !std::isfinite(T[i]) || M[i] < 1) return bset_err(b, PAVG_ERR_INVAL, "invalid T or M");
+    key[i] = {T[i], T[i] == 0.0 ? 1 : M[i]};
+  }
+  auto it = b->plans.find(key);
+  if (it != b->plans.end()) { *out = &it->second; return PAVG_OK; }
+  BatchPlan bp;
+  bp.K.resize(n);
+  bp.pl.resize(n, nullptr);
+  bool moved = false;
+  for (int i = 0; i < n; ++i) {
+    pavg_ctx* c = b->ctx[i];
+    const double* q0 = c->Q;
+    int K = 0, Mi = 1;
+    if (T[i] > 0.0) {
+      int rc = get_plan(c, T[i], M[i], &bp.pl[i]);
+      if (rc) return bset_err(b, rc, "instance " + std::to_string(i) + ": " + c->err);
+      K = bp.pl[i]->K;
+      Mi = M[i];
+      bp.K[i] = K;
+    } else {
+      bp.K[i] = -1;
+    }
+    int rc = ensure_avg_workspace(c, K, Mi);
+    if (rc) return bset_err(b, rc, "instance " + std::to_string(i) + ": " + c->err);
+    moved = moved || (q0 && q0 != c->Q);
+  }
+  if (moved)
+    for (auto& kv : b->plans) drop_exec(&kv.second);
+  auto res = b->plans.emplace(key, bp);
+  *out = &res.first->second;
+  return PAVG_OK;
+}
+
+// The instances' workspace buffers; a single-instance call can grow (move) them.
+std::vector<const double*> workspaces(const pavg_batch* b) {
+  std::vector<const double*> w;
+  for (auto* c : b->ctx) {
+    w.push_back(c->Q);
+    w.push_back(c->Um);
+    w.push_back(c->Rm);
+  }
+  return w;
+}
+
+void split(const BatchPlan& bp, std::vector<int>* fwd, std::vector<int>* bwd, std::vector<int>* n_only) {
+  for (int i = 0; i < (int)bp.K.size(); ++i) {
+    if (bp.K[i] < 0) { n_only->push_back(i); continue; }
+    if (bp.K[i] >= 1) fwd->push_back(i);
+    bwd->push_back(i);
+  }
+}
+
+int record(pavg_batch* b, int k, cudaStream_t st) {
+  BCK(cudaEventRecordWithFlags(b->ev[k], st, cudaEventRecordExternal));
+  return PAVG_OK;
+}
+
+// Captures the whole evaluation (inputs already in Q_0 of each instance,
+// results left in io_out) with the batch's configuration.
+int capture(pavg_batch* b, BatchPlan* bp) {
+  drop_exec(bp);
+  std::vector<int> fwd, bwd, n_only;
+  split(*bp, &fwd, &bwd, &n_only);
+  int rc = build_launch(b, *bp, 0, fwd, b->cfg, -1, false, &bp->fwd);
+  if (!rc) rc = build_launch(b, *bp, 1, bwd, b->cfg, -1, false, &bp->bwd);
+  if (!rc) rc = upload_launch(b, &bp->fwd);
+  if (!rc) rc = upload_launch(b, &bp->bwd);
+  if (rc) return rc;
+  cudaStream_t cs = b->cap_stream;
+  // per-context CG event brackets are not captured into batch graphs
+  std::vector<bool> timing;
+  for (auto* c : b->ctx) { timing.push_back(c->timing); c->timing = false; }
+  struct Restore {
+    pavg_batch* b;
+    std::vector<bool>& t;
+    ~Restore() { for (size_t i = 0; i < b->ctx.size(); ++i) b->ctx[i]->timing = t[i]; }
+  } restore{b, timing};
+  BCK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  int launches = 0;
+  auto body = [&]() -> int {
+    int r = record(b, 0, cs);
+    if (!r) r = enq_launch(b, bp->fwd, b->cfg, 0, -1, cs);
+    if (r) return r;
+    launches += bp->fwd.probs.empty() ? 0 : 1;
+    if ((r = record(b, 1, cs))) return r;
+    for (int i : bwd) {
+      pavg_ctx* c = b->ctx[i];
+      c->launches = 0;
+      r = enq_avg_shifts(c, *bp->pl[i], cs);
+      launches += c->launches;
+      if (r) return bset_err(b, r, "instance " + std::to_string(i) + ": " + c->err);
+    }
+    if ((r = record(b, 2, cs))) return r;
+    if ((r = enq_launch(b, bp->bwd, b->cfg, 1, -1, cs))) return r;
+    launches += bp->bwd.probs.empty() ? 0 : 1;
+    if ((r = record(b, 3, cs))) return r;
+    for (int i : n_only) {
+      pavg_ctx* c = b->ctx[i];
+      c->launches = 0;
+      r = enq_nonlinear(c, c->Q, c->io_out, c->Rm, cs);
+      launches += c->launches;
+      if (r) return bset_err(b, r, "instance " + std::to_string(i) + ": " + c->err);
+    }
+    return PAVG_OK;
+  };
+  rc = body();
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &graph);
+  if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+  if (e != cudaSuccess) return bset_err(b, PAVG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&bp->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    bp->exec = nullptr;
+    return bset_err(b, PAVG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  bp->cfg = b->cfg;
+  bp->launches = launches;
+  bp->ws = workspaces(b);
+  return PAVG_OK;
+}
+
+int load_inputs(pavg_batch* b, const double* const* U, cudaStream_t st) {
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    pavg_ctx* c = b->ctx[i];
+    BCK(cudaMemcpyAsync(c->Q, U[i], sizeof(double) * c->dm.n, cudaMemcpyDeviceToDevice, st));
+  }
+  return PAVG_OK;
+}
+
+// Autotuner: every candidate grid runs kTuneSteps steps of the forward chains
+// on the loaded inputs; each instance's device timer gives its time per step,
+// and the launch time of the full chains is predicted as the largest
+// (time per step x chain length) over the instances.
+int autotune(pavg_batch* b, BatchPlan* bp, cudaStream_t st, Config* best) {
+  std::vector<int> fwd, bwd, n_only;
+  split(*bp, &fwd, &bwd, &n_only);
+  Config keep;
+  keep.predicted_ms = 0.0;
+  if (fwd.empty()) { *best = keep; return PAVG_OK; }
+  BCK(cudaStreamSynchronize(st));
+  Launch L;
+  const int nts[2] = {128, 256};
+  bool found = false;
+  const std::string saved = b->err;
+  for (int nt : nts)
+    for (int bps = 1; bps <= 4; ++bps)
+      for (int res = 0; res <= 1; ++res)
+        for (int wt = 0; wt <= 1; ++wt) {
+          Config c;
+          c.nt = nt; c.bps = bps; c.res = res; c.weighting = wt;
+          if (build_launch(b, *bp, 0, fwd, c, kTuneSteps, true, &L)) continue;  // does not fit
+          // the weights use the full chain lengths
+          {
+            std::vector<int64_t> F;
+            std::vector<int> steps;
+            for (int i : fwd) { F.push_back(cells_of(b, i)); steps.push_back(bp->K[i]); }
+            std::vector<int> nb;
+            if (!share_blocks(F, steps, c.bps * b->sms, c.nt, c.weighting, &nb)) continue;
+            int block0 = 0;
+            size_t smem = 0;
+            for (size_t p = 0; p < fwd.size(); ++p) {
+              L.probs[p].block0 = block0;
+              L.probs[p].nblocks = nb[p];
+              block0 += nb[p];
+              if (c.res) smem = std::max(smem, chain_res_smem(F[p], nb[p], c.nt));
+            }
+            if (c.res) {
+              int per_sm = 0;
+              if (smem > 200 * 1024 || chain_occupancy(c.nt, true, smem, &per_sm) != cudaSuccess || per_sm < c.bps)
+                continue;
+              L.smem = smem;
+            }
+            L.blocks = block0;
+          }
+          if (upload_launch(b, &L)) { free_launch(&L); return PAVG_ERR_CUDA; }
+          BCK(cudaMemsetAsync(b->timer, 0, sizeof(unsigned long long) * 2 * b->ctx.size(), st));
+          if (enq_launch(b, L, c, 0, -1, st)) { cudaGetLastError(); continue; }
+          BCK(cudaStreamSynchronize(st));
+          std::vector<unsigned long long> t(2 * b->ctx.size());
+          BCK(cudaMemcpy(t.data(), b->timer, sizeof(unsigned long long) * t.size(), cudaMemcpyDeviceToHost));
+          double pred = 0.0;
+          for (int i : fwd) {
+            const int ran = std::min(bp->K[i], kTuneSteps);
+            const double dt = (double)(t[2 * i + 1] - t[2 * i]) * 1e-6;  // ms
+            pred = std::max(pred, dt / ran * bp->K[i]);
+          }
+          c.predicted_ms = pred;
+          if (!found || pred < best->predicted_ms) { *best = c; found = true; }
+        }
+  free_launch(&L);
+  b->err = saved;
+  for (int i : fwd) {
+    int rc = check_flags(b->ctx[i]);
+    if (rc) return bset_err(b, rc, "autotuning run, instance " + std::to_string(i) + ": " + b->ctx[i]->err);
+  }
+  if (!found) return bset_err(b, PAVG_ERR_INVAL, "no grid configuration fits these instances");
+  return PAVG_OK;
+}
+
+void free_batch(pavg_batch* b) {
+  if (!b) return;
+  for (auto& kv : b->plans) {
+    drop_exec(&kv.second);
+    free_launch(&kv.second.fwd);
+    free_launch(&kv.second.bwd);
+  }
+  for (auto* p : b->partial) cudaFree(p);
+  for (auto* p : b->partial_f) cudaFree(p);
+  for (auto* p : b->scal) cudaFree(p);
+  cudaFree(b->sync);
+  cudaFree(b->timer);
+  for (auto e : b->ev)
+    if (e) cudaEventDestroy(e);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pavg_batch_create(pavg_ctx* const* ctxs, int n, pavg_batch** out) {
+  if (!out) return PAVG_ERR_INVAL;
+  *out = nullptr;
+  if (!ctxs || n < 1) return PAVG_ERR_INVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PAVG_ERR_CUDA;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i] || ctxs[i]->device != dev || ctxs[i]->p.solver != PAVG_SOLVER_MIXED) return PAVG_ERR_INVAL;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return PAVG_ERR_INVAL;
+  }
+  pavg_batch* b = new pavg_batch();
+  b->ctx.assign(ctxs, ctxs + n);
+  b->device = dev;
+  bool ok = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;
+  b->partial.assign(n, nullptr);
+  b->partial_f.assign(n, nullptr);
+  b->scal.assign(n, nullptr);
+  for (int i = 0; i < n && ok; ++i) {
+    const size_t most = (size_t)((ctxs[i]->dm.F + 31) / 32);  // blocks of 32 cells
+    ok = dalloc(&b->partial[i], 3 * most) == cudaSuccess && dalloc(&b->partial_f[i], 3 * most) == cudaSuccess &&
+         dalloc(&b->scal[i], 8) == cudaSuccess;
+  }
+  ok = ok && dalloc(&b->sync, 16 * (size_t)n) == cudaSuccess && dalloc(&b->timer, 2 * (size_t)n) == cudaSuccess;
+  for (auto& e : b->ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+  if (!ok) {
+    free_batch(b);
+    return PAVG_ERR_NOMEM;
+  }
+  *out = b;
+  return PAVG_OK;
+}
+
+int pavg_batch_destroy(pavg_batch* b) {
+  if (!b) return PAVG_ERR_INVAL;
+  cudaDeviceSynchronize();
+  free_batch(b);
+  return PAVG_OK;
+}
+
+int pavg_batch_autotune(pavg_batch* b, const double* T, const int* M, const double* const* U, void* stream,
+                        pavg_batch_config* best) {
+  if (!b || !T || !M || !U) return PAVG_ERR_INVAL;
+  for (size_t i = 0; i < b->ctx.size(); ++i)
+    if (!U[i]) return bset_err(b, PAVG_ERR_INVAL, "null input pointer");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  BatchPlan* bp = nullptr;
+  int rc = get_batch_plan(b, T, M, &bp);
+  if (!rc) rc = load_inputs(b, U, st);
+  Config c;
+  if (!rc) rc = autotune(b, bp, st, &c);
+  if (rc) return rc;
+  if (!b->have_cfg || !same(c, b->cfg))
+    for (auto& kv : b->plans) drop_exec(&kv.second);
+  b->cfg = c;
+  b->have_cfg = true;
+  if (best) *best = {c.nt, c.bps, c.res, c.weighting, c.predicted_ms};
+  return PAVG_OK;
+}
+
+int pavg_batch_set_config(pavg_batch* b, const pavg_batch_config* cfg) {
+  if (!b || !cfg) return PAVG_ERR_INVAL;
+  if ((cfg->threads != 128 && cfg->threads != 256) || cfg->blocks_per_sm < 1 || cfg->blocks_per_sm > 8 ||
+      (cfg->resident != 0 && cfg->resident != 1) || (cfg->weighting != 0 && cfg->weighting != 1))
+    return bset_err(b, PAVG_ERR_INVAL, "invalid configuration");
+  Config c;
+  c.nt = cfg->threads; c.bps = cfg->blocks_per_sm; c.res = cfg->resident; c.weighting = cfg->weighting;
+  if (!b->have_cfg || !same(c, b->cfg))
+    for (auto& kv : b->plans) drop_exec(&kv.second);
+  b->cfg = c;
+  b->have_cfg = true;
+  return PAVG_OK;
+}
+
+int pavg_batch_get_config(const pavg_batch* b, pavg_batch_config* cfg) {
+  if (!b || !cfg) return PAVG_ERR_INVAL;
+  if (!b->have_cfg) return PAVG_ERR_INVAL;
+  *cfg = {b->cfg.nt, b->cfg.bps, b->cfg.res, b->cfg.weighting, b->cfg.predicted_ms};
+  return PAVG_OK;
+}
+
+int pavg_batch_averaged_rhs(pavg_batch* b, const double* T, const int* M, const double* const* U,
+                            double* const* out, void* stream) {
+  if (!b || !T || !M || !U || !out) return PAVG_ERR_INVAL;
+  for (size_t i = 0; i < b->ctx.size(); ++i)
+    if (!U[i] || !out[i] || U[i] == out[i]) return bset_err(b, PAVG_ERR_INVAL, "null or aliasing state pointer");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device) return bset_err(b, PAVG_ERR_INVAL, "wrong device");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  BatchPlan* bp = nullptr;
+  int rc = get_batch_plan(b, T, M, &bp);
+  if (rc) return rc;
+  // workspaces only grow, but a larger single-instance call on a context moves them
+  if (bp->exec && bp->ws != workspaces(b)) drop_exec(bp);
+  if ((rc = load_inputs(b, U, st))) return rc;
+  if (!b->have_cfg) {
+    Config c;
+    if ((rc = autotune(b, bp, st, &c))) return rc;
+    b->cfg = c;
+    b->have_cfg = true;
+  }
+  if (!bp->exec || !same(bp->cfg, b->cfg))
+    if ((rc = capture(b, bp))) return rc;
+  BCK(cudaGraphLaunch(bp->exec, st));
+  b->ev_recorded = true;
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    pavg_ctx* c = b->ctx[i];
+    BCK(cudaMemcpyAsync(out[i], c->io_out, sizeof(double) * c->dm.n, cudaMemcpyDeviceToDevice, st));
+    c->last_degree = std::max(bp->K[i], 0);
+    c->last_launches = 0;
+  }
+  if (!b->ctx.empty()) b->ctx[0]->last_launches = bp->launches;
+  return PAVG_OK;
+}
+
+int pavg_batch_kernel_time(pavg_batch* b, double* forward_ms, double* backward_ms) {
+  if (!b || !forward_ms || !backward_ms) return PAVG_ERR_INVAL;
+  if (!b->ev_recorded) { *forward_ms = *backward_ms = 0.0; return PAVG_OK; }
+  float f = 0.f, g = 0.f;
+  BCK(cudaEventSynchronize(b->ev[3]));
+  BCK(cudaEventElapsedTime(&f, b->ev[0], b->ev[1]));
+  BCK(cudaEventElapsedTime(&g, b->ev[2], b->ev[3]));
+  *forward_ms = f;
+  *backward_ms = g;
+  return PAVG_OK;
+}
+
+int pavg_batch_sync(pavg_batch* b, void* stream) {
+  if (!b) return PAVG_ERR_INVAL;
+  BCK(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    int rc = check_flags(b->ctx[i]);
+    if (rc) return bset_err(b, rc, "instance " + std::to_string(i) + ": " + b->ctx[i]->err);
+  }
+  return PAVG_OK;
+}
+
+const char* pavg_batch_last_error(const pavg_batch* b) {
+  if (!b) return "null batch";
+  return b->err.c_str();
+}
+
+}  // extern "C"

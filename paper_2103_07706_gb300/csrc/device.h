@@ -92,6 +92,45 @@ cudaError_t cg_ir_configure(int64_t F, CgIrWork* w);
 cudaError_t launch_cg_ir(const DeviceMesh& m, const CgIrWork& w, const CgIrParams& cp, const double* b,
                          double* out, double scale_x, const double* add, cudaStream_t st);
 
+// One problem of the batched persistent recurrence kernel (k_chain): one
+// instance's whole forward Chebyshev chain (mode 0, K steps)
+//   Q_{k+1} = M^{-1}(s_k Khat Q_k) + Q_{k-1},  s_0 = 1/lam, s_k = 2/lam,
+// or its Clenshaw recurrence (mode 1, K + 1 steps, k = K .. 0)
+//   b_k = M^{-1}(y_k + s_k Khat b_{k+1}) + b_{k+2}   (b_0 is the result),
+// run by the blocks block0 .. block0 + nblocks - 1 of the launch, which
+// synchronise only among themselves.
+struct ChainProblem {
+  DeviceMesh m;
+  CgIrWork w;                   // solver scratch of the instance's context
+  CgIrParams cp;
+  double g, H, lam;
+  double* ru;                   // [n_u] assembled velocity right-hand side
+  double* Q;                    // mode 0: Q_0 .. Q_K; mode 1: y_0 .. y_K  ([K+1][n])
+  double* bufs[3];              // mode 1: b_k in bufs[k % 3]
+  double* out;                  // mode 1: result b_0
+  double* partial;              // [3][nblocks] per-block sums, FP64 phases
+  float* partial_f;             // [3][nblocks] per-block sums, FP32 phases
+  double* scal;                 // [8]
+  unsigned long long* sync;     // [8]: arrival counter (word 0), tagged sums (words 1-4); zero at launch
+  unsigned long long* timer;    // [2] or null: global timer (ns) when the problem's steps start and end
+  int mode, K;
+  int block0, nblocks;
+};
+
+// Launch of k_chain over P problems and nblocks_total co-resident blocks of
+// nt threads (128 or 256).  res: FP32 element matrices resident in shared
+// memory (smem bytes per block).  max_steps >= 0 stops every problem after
+// that many steps (autotuning runs).  Cooperative launch: all blocks are
+// co-resident.
+cudaError_t launch_chain(const ChainProblem* d_probs, int P, int nblocks_total, int nt, bool res, size_t smem,
+                         int max_steps, cudaStream_t st);
+// Blocks of k_chain<nt, res> that fit on one SM with smem dynamic bytes.
+cudaError_t chain_occupancy(int nt, bool res, size_t smem, int* per_sm);
+// Dynamic shared memory of the resident path for a problem of F cells on nb blocks.
+size_t chain_res_smem(int64_t F, int nb, int nt);
+// Upload of the reference-element tables used by k_chain.
+cudaError_t upload_chain_tables(const ConstTables& t);
+
 // Upload constant tables (reference element data) to the current device.
 cudaError_t upload_tables(const ConstTables& t);
 

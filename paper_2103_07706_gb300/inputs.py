@@ -141,3 +141,26 @@ def harmonic_state(verts, cells, seed, lmax, eta_rms=100.0, g=9.80616, omega=7.2
     l_eff = max(1.0, float(np.sqrt(np.sum(coeffs ** 2 * np.arange(lmax + 1)[:, None] ** 2) / np.sum(coeffs ** 2))))
     rossby = u_rms / (f0 * math.pi * radius / l_eff)
     return np.concatenate([u, eta]), {"rossby": rossby, "u_rms": u_rms, "edges": E, "cells": F}
+
+
+# lambda_max of L per refinement (R = 6.37122e6 m, Omega = 7.292e-5 s^-1,
+# g = 9.80616 m s^-2, H = 5000 m): the refinement-6 power-iteration estimate
+# widened by 2 % (0.02335 s^-1), halved per coarser level (the fastest
+# discrete gravity wave scales with the inverse cell size).
+def lambda_max_for(refinement):
+    return 0.02335 / 2.0 ** (6 - refinement)
+
+
+def batch_workload(seed=2103, n=64, refinements=(4, 5, 6), t_hours=(0.25, 4.0), shifts=(16, 32, 64, 128)):
+    """Independent instances of the batched evaluation: a list of dicts with
+    refinement r (uniform over `refinements`), window T in seconds (uniform in
+    `t_hours`), shift count M (uniform over `shifts`) and a state seed.  The
+    state of each instance is harmonic_state(..., seed=state_seed, lmax=16)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        out.append({"refinement": int(rng.choice(refinements)),
+                    "T": float(3600.0 * rng.uniform(*t_hours)),
+                    "M": int(rng.choice(shifts)),
+                    "state_seed": seed + 1 + i})
+    return out

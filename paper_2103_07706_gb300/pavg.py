@@ -34,6 +34,9 @@ EXPORTED = [
     "pavg_set_topography", "pavg_lambda_max", "pavg_linear", "pavg_nonlinear", "pavg_expL_apply",
     "pavg_averaged_rhs", "pavg_averaged_rhs_literal", "pavg_timestep", "pavg_sync", "pavg_get_stats",
     "pavg_reset_stats", "pavg_last_error", "pavg_kernel_timing", "pavg_kernel_time", "pavg_linear_noalloc",
+    "pavg_batch_create", "pavg_batch_destroy", "pavg_batch_averaged_rhs", "pavg_batch_autotune",
+    "pavg_batch_set_config", "pavg_batch_get_config", "pavg_batch_kernel_time", "pavg_batch_sync",
+    "pavg_batch_last_error",
 ]
 
 
@@ -65,6 +68,16 @@ class Stats(ctypes.Structure):
         ("error_flags", ctypes.c_int),
         ("kernel_launches", ctypes.c_int),
         ("cg_sweeps_mean", ctypes.c_double),
+    ]
+
+
+class BatchConfig(ctypes.Structure):
+    _fields_ = [
+        ("threads", ctypes.c_int),
+        ("blocks_per_sm", ctypes.c_int),
+        ("resident", ctypes.c_int),
+        ("weighting", ctypes.c_int),
+        ("predicted_ms", ctypes.c_double),
     ]
 
 
@@ -101,6 +114,15 @@ def load(path=LIB_PATH):
         "pavg_kernel_timing": (I, [P, I]),
         "pavg_kernel_time": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I)]),
         "pavg_linear_noalloc": (I, [P, P, P, V]),
+        "pavg_batch_create": (I, [P, I, ctypes.POINTER(P)]),
+        "pavg_batch_destroy": (I, [P]),
+        "pavg_batch_averaged_rhs": (I, [P, P, P, P, P, V]),
+        "pavg_batch_autotune": (I, [P, P, P, P, V, ctypes.POINTER(BatchConfig)]),
+        "pavg_batch_set_config": (I, [P, ctypes.POINTER(BatchConfig)]),
+        "pavg_batch_get_config": (I, [P, ctypes.POINTER(BatchConfig)]),
+        "pavg_batch_kernel_time": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "pavg_batch_sync": (I, [P, V]),
+        "pavg_batch_last_error": (ctypes.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -266,3 +288,75 @@ class Model:
         self._check(self._lib.pavg_timestep(self._h, float(dt), float(T), int(M), _ptr(U, self.n), int(nsteps),
                                             _stream()))
         return U
+
+
+class Batch:
+    """Independent instances (Models) evaluated together: their Chebyshev
+    chains and Clenshaw sums each in one persistent launch (pavg.h, batches)."""
+
+    def __init__(self, models):
+        self._lib = lib()
+        self.models = list(models)
+        n = len(self.models)
+        arr = (ctypes.c_void_p * n)(*[m._h for m in self.models])
+        h = ctypes.c_void_p()
+        rc = self._lib.pavg_batch_create(arr, n, ctypes.byref(h))
+        if rc:
+            raise PavgError(rc, "pavg_batch_create failed")
+        self._h = h
+
+    def _check(self, rc):
+        if rc:
+            raise PavgError(rc, self._lib.pavg_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pavg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _arrays(self, T, M, U):
+        n = len(self.models)
+        if not (len(T) == len(M) == len(U) == n):
+            raise ValueError("one T, M and state per instance")
+        Ta = (ctypes.c_double * n)(*[float(t) for t in T])
+        Ma = (ctypes.c_int * n)(*[int(m) for m in M])
+        Ua = (ctypes.c_void_p * n)(*[_ptr(u, m.n).value for u, m in zip(U, self.models)])
+        return Ta, Ma, Ua
+
+    def averaged_rhs(self, T, M, U, out=None):
+        """out_i = N-bar_i(U_i) for every instance; returns the list of outputs."""
+        Ta, Ma, Ua = self._arrays(T, M, U)
+        out = [torch.empty_like(u) for u in U] if out is None else out
+        Oa = (ctypes.c_void_p * len(out))(*[_ptr(o, m.n).value for o, m in zip(out, self.models)])
+        self._check(self._lib.pavg_batch_averaged_rhs(self._h, Ta, Ma, Ua, Oa, _stream()))
+        return out
+
+    def autotune(self, T, M, U):
+        Ta, Ma, Ua = self._arrays(T, M, U)
+        c = BatchConfig()
+        self._check(self._lib.pavg_batch_autotune(self._h, Ta, Ma, Ua, _stream(), ctypes.byref(c)))
+        return {k: getattr(c, k) for k, _ in BatchConfig._fields_}
+
+    def set_config(self, threads, blocks_per_sm, resident=0, weighting=0):
+        c = BatchConfig(threads, blocks_per_sm, resident, weighting, 0.0)
+        self._check(self._lib.pavg_batch_set_config(self._h, ctypes.byref(c)))
+
+    def config(self):
+        c = BatchConfig()
+        self._check(self._lib.pavg_batch_get_config(self._h, ctypes.byref(c)))
+        return {k: getattr(c, k) for k, _ in BatchConfig._fields_}
+
+    def kernel_time(self):
+        """(forward ms, backward ms) of the two persistent launches of the last call."""
+        f, g = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.pavg_batch_kernel_time(self._h, ctypes.byref(f), ctypes.byref(g)))
+        return f.value, g.value
+
+    def sync(self):
+        self._check(self._lib.pavg_batch_sync(self._h, _stream()))
