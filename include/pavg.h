@@ -267,6 +267,94 @@ int pavg_batch_sync(pavg_batch* b, void* stream);
 /* Readable message of the batch's last failure. */
 const char* pavg_batch_last_error(const pavg_batch* b);
 
+/* ------------------------------------------------------------------------
+ * Learned surrogate of the large-M average.
+ *
+ * Wide windows T need many shifts M for the Riemann sum of Sec. 2.2 to
+ * resolve the fast oscillations.  The surrogate keeps a cheap average with
+ * few shifts, V = N-bar_Mc(U), and adds a learned correction towards the
+ * large-M average:
+ *   S(U) = V + scatter(sd_y * MLP((features(U, V) - mu_x) / sd_x) + mu_y).
+ * features: per cell, its 15 local values (12 velocity coefficients times the
+ * local-to-global signs of Sec. 2.5, 3 elevation values) of U and of V, the
+ * same for the 3 cells across its edges (their own frames, local edge order),
+ * and z_c / R, G00 / det, G01 / det, G11 / det of the cell: 124 FP32 inputs.
+ * MLP: 124 -> hidden -> hidden -> 15, tanh hidden units, FP32 weights, in
+ * flat order W1 [hidden][124], b1, W2 [hidden][hidden], b2, W3 [15][hidden], b3.
+ * scatter: elevation and interior velocity values to their DOFs; an edge DOF
+ * takes the mean of its two cells' values (times their signs).
+ * Training: targets are the cell's 15 local values of N-bar_Mf(U) - V;
+ * standardised mean squared error; Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+ * Every step (features, GEMMs, activations, loss, gradients, Adam, scatter)
+ * runs in the library's kernels.  The Riemann sum with Mf shifts judges the
+ * surrogate's error and replaces it above a threshold.
+ *
+ * A surrogate is independent of any mesh: its weights are trained on pairs
+ * from one context and applied on any other (another refinement).  Scratch
+ * for each context it is used with is allocated on first use.
+ * ------------------------------------------------------------------------ */
+typedef struct pavg_surrogate pavg_surrogate; /* opaque, library-owned */
+
+/* hidden >= 1 units per layer; weights Glorot-uniform from `seed` (host
+ * 64-bit Mersenne twister), biases zero, standardisation identity. */
+int pavg_surrogate_create(int hidden, uint64_t seed, pavg_surrogate** out);
+int pavg_surrogate_destroy(pavg_surrogate* s);
+int pavg_surrogate_nparams(const pavg_surrogate* s, int64_t* n);
+/* Host copies of the flat FP32 parameter vector (nparams floats). */
+int pavg_surrogate_get_params(const pavg_surrogate* s, float* host);
+int pavg_surrogate_set_params(pavg_surrogate* s, const float* host);
+/* Host copies of the standardisation: mu_x, sd_x (124 each), mu_y, sd_y (15 each). */
+int pavg_surrogate_get_scaling(const pavg_surrogate* s, float* mu_x, float* sd_x, float* mu_y, float* sd_y);
+int pavg_surrogate_set_scaling(pavg_surrogate* s, const float* mu_x, const float* sd_x, const float* mu_y,
+                               const float* sd_y);
+
+/* Appends the F raw feature rows and raw target rows of n training pairs:
+ * states U[i], cheap averages Vc[i], large-M averages Vf[i] (host arrays of
+ * device pointers to n_ctx doubles each). */
+int pavg_surrogate_add_pairs(pavg_surrogate* s, pavg_ctx* ctx, int n, const double* const* U,
+                             const double* const* Vc, const double* const* Vf, void* stream);
+/* Rows stored so far. */
+int pavg_surrogate_rows(const pavg_surrogate* s, int64_t* rows);
+/* Column means / standard deviations over the stored rows become the
+ * standardisation; the stored rows are standardised in place.  Once. */
+int pavg_surrogate_fit_scaling(pavg_surrogate* s, void* stream);
+/* epochs passes of Adam over the stored rows in minibatches of `batch` rows
+ * (a fresh permutation per epoch from `seed`), learning rate lr.
+ * loss_per_epoch: host array of epochs doubles (mean standardised squared
+ * error over each epoch's minibatches) or NULL.  Synchronises `stream`. */
+int pavg_surrogate_train(pavg_surrogate* s, int epochs, int batch, double lr, uint64_t seed,
+                         double* loss_per_epoch, void* stream);
+/* Loss and gradient of the current parameters on rows X [B][124]
+ * (standardised) against Z [B][15] (device FP32); grad: device, nparams
+ * floats; *loss: host.  Synchronises `stream`. */
+int pavg_surrogate_gradient(pavg_surrogate* s, const float* X, const float* Z, int B, float* grad, double* loss,
+                            void* stream);
+/* One Adam update of the parameters with the given gradient (device). */
+int pavg_surrogate_adam_step(pavg_surrogate* s, const float* grad, double lr, void* stream);
+
+/* Feature rows X [F][124] (device FP32) of state U and cheap average V on
+ * the context's mesh; standardised with the surrogate's scaling when
+ * `standardised` is set, raw otherwise. */
+int pavg_surrogate_features(pavg_surrogate* s, pavg_ctx* ctx, const double* U, const double* V, float* X,
+                            int standardised, void* stream);
+
+/* out = V + correction for state U and its cheap average V (device, n doubles
+ * each; out may not alias them).  bf16: the MLP's operands rounded to BF16
+ * (FP32 sums). */
+int pavg_surrogate_apply(pavg_surrogate* s, pavg_ctx* ctx, const double* U, const double* V, double* out, int bf16,
+                         void* stream);
+/* The surrogate form of N-bar(U) with its fallback: V = N-bar_Mc(U), out =
+ * V + correction.  When check is set, also computes N-bar_Mf(U); if the
+ * relative error of the surrogate in the energy norm (H u^T M1 u + g eta^T M2 eta)
+ * exceeds threshold, out is replaced by N-bar_Mf(U) and *used_fallback = 1.
+ * *rel_err: the measured error (-1 when check is 0).  Synchronises `stream`
+ * when check is set. */
+int pavg_surrogate_averaged_rhs(pavg_surrogate* s, pavg_ctx* ctx, double T, int Mc, int Mf, double threshold,
+                                int check, int bf16, const double* U, double* out, int* used_fallback,
+                                double* rel_err, void* stream);
+
+const char* pavg_surrogate_last_error(const pavg_surrogate* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -131,6 +131,39 @@ size_t chain_res_smem(int64_t F, int nb, int nt);
 // Upload of the reference-element tables used by k_chain.
 cudaError_t upload_chain_tables(const ConstTables& t);
 
+// ---- learned surrogate (surrogate.cu)
+constexpr int kSurInputs = 124;   // 8 x 15 local values + 4 geometric values
+constexpr int kSurOutputs = 15;
+
+enum class SurGemm {
+  kForwardTanh,    // C [M][N] = tanh(A [M][K] W^T + bias), W stored [N][K]
+  kForwardLinear,  // C = A W^T + bias
+  kBackwardData,   // C [M][N] = (A [M][K] W [K][N]) (1 - aux^2)
+  kWeightGrad,     // C [M][N] = A^T B, A stored [K][M], B [K][N]; split over K into `splits` partials
+};
+cudaError_t sur_gemm(SurGemm kind, int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C,
+                     int ldc, const float* bias, const float* aux, int ldaux, int splits, bool bf16,
+                     cudaStream_t st);
+cudaError_t sur_reduce_splits(const float* part, int splits, int64_t count, float* out, cudaStream_t st);
+cudaError_t sur_colsum(const float* A, int rows, int cols, int ld, float* out, cudaStream_t st);
+// dY = scale (Y - Z); *acc += sum (Y - Z)^2 / denom (part: nblocks doubles of scratch).
+cudaError_t sur_mse(const float* Y, const float* Z, int64_t count, float scale, float* dY, double* part, int nblocks,
+                    double denom, double* acc, cudaStream_t st);
+cudaError_t sur_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2, float eps,
+                     float c1, float c2, cudaStream_t st);
+// Feature rows [F][124] of (U, V); geo [F][4]; standardised when mu is not null.
+cudaError_t sur_features(const DeviceMesh& m, const double* U, const double* V, const float* geo, const float* mu,
+                         const float* sd, float* X, cudaStream_t st);
+// Target rows [F][15] = local values of Vf - Vc; standardised when mu is not null.
+cudaError_t sur_targets(const DeviceMesh& m, const double* Vf, const double* Vc, const float* mu, const float* sd,
+                        float* Z, cudaStream_t st);
+// corr (n) = scatter of Y [F][15] * sd + mu (edge DOFs: mean of the two cells).
+cudaError_t sur_scatter(const DeviceMesh& m, const float* Y, const float* mu, const float* sd, double* corr,
+                        cudaStream_t st);
+cudaError_t sur_colstats(const float* X, int64_t rows, int cols, float* mu, float* sd, cudaStream_t st);
+cudaError_t sur_standardize(float* X, int64_t rows, int cols, const float* mu, const float* sd, cudaStream_t st);
+cudaError_t sur_gather_rows(const float* src, const int* idx, int rows, int cols, float* dst, cudaStream_t st);
+
 // Upload constant tables (reference element data) to the current device.
 cudaError_t upload_tables(const ConstTables& t);
 

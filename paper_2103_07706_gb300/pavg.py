@@ -37,6 +37,11 @@ EXPORTED = [
     "pavg_batch_create", "pavg_batch_destroy", "pavg_batch_averaged_rhs", "pavg_batch_autotune",
     "pavg_batch_set_config", "pavg_batch_get_config", "pavg_batch_kernel_time", "pavg_batch_sync",
     "pavg_batch_last_error",
+    "pavg_surrogate_create", "pavg_surrogate_destroy", "pavg_surrogate_nparams", "pavg_surrogate_get_params",
+    "pavg_surrogate_set_params", "pavg_surrogate_get_scaling", "pavg_surrogate_set_scaling",
+    "pavg_surrogate_add_pairs", "pavg_surrogate_rows", "pavg_surrogate_fit_scaling", "pavg_surrogate_train",
+    "pavg_surrogate_gradient", "pavg_surrogate_adam_step", "pavg_surrogate_features", "pavg_surrogate_apply",
+    "pavg_surrogate_averaged_rhs", "pavg_surrogate_last_error",
 ]
 
 
@@ -123,6 +128,23 @@ def load(path=LIB_PATH):
         "pavg_batch_kernel_time": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "pavg_batch_sync": (I, [P, V]),
         "pavg_batch_last_error": (ctypes.c_char_p, [P]),
+        "pavg_surrogate_create": (I, [I, ctypes.c_uint64, ctypes.POINTER(P)]),
+        "pavg_surrogate_destroy": (I, [P]),
+        "pavg_surrogate_nparams": (I, [P, ctypes.POINTER(I64)]),
+        "pavg_surrogate_get_params": (I, [P, P]),
+        "pavg_surrogate_set_params": (I, [P, P]),
+        "pavg_surrogate_get_scaling": (I, [P, P, P, P, P]),
+        "pavg_surrogate_set_scaling": (I, [P, P, P, P, P]),
+        "pavg_surrogate_add_pairs": (I, [P, P, I, P, P, P, V]),
+        "pavg_surrogate_rows": (I, [P, ctypes.POINTER(I64)]),
+        "pavg_surrogate_fit_scaling": (I, [P, V]),
+        "pavg_surrogate_train": (I, [P, I, I, D, ctypes.c_uint64, P, V]),
+        "pavg_surrogate_gradient": (I, [P, P, P, I, P, ctypes.POINTER(D), V]),
+        "pavg_surrogate_adam_step": (I, [P, P, D, V]),
+        "pavg_surrogate_features": (I, [P, P, P, P, P, I, V]),
+        "pavg_surrogate_apply": (I, [P, P, P, P, P, I, V]),
+        "pavg_surrogate_averaged_rhs": (I, [P, P, D, I, I, D, I, I, P, P, ctypes.POINTER(I), ctypes.POINTER(D), V]),
+        "pavg_surrogate_last_error": (ctypes.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -360,3 +382,126 @@ class Batch:
 
     def sync(self):
         self._check(self._lib.pavg_batch_sync(self._h, _stream()))
+
+
+N_SUR_IN = 124
+N_SUR_OUT = 15
+
+
+def _fptr(t, n=None):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float32 CUDA tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"expected {n} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Surrogate:
+    """Learned mesh-local correction of a cheap few-shift average towards the
+    large-M average (pavg.h, learned surrogate)."""
+
+    def __init__(self, hidden=128, seed=2103):
+        import numpy as np
+        self._lib = lib()
+        h = ctypes.c_void_p()
+        rc = self._lib.pavg_surrogate_create(int(hidden), ctypes.c_uint64(seed), ctypes.byref(h))
+        if rc:
+            raise PavgError(rc, "pavg_surrogate_create failed")
+        self._h = h
+        self.hidden = hidden
+        n = ctypes.c_int64()
+        self._check(self._lib.pavg_surrogate_nparams(h, ctypes.byref(n)))
+        self.nparams = n.value
+        self._np = np
+
+    def _check(self, rc):
+        if rc:
+            raise PavgError(rc, self._lib.pavg_surrogate_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pavg_surrogate_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        out = self._np.zeros(self.nparams, dtype=self._np.float32)
+        self._check(self._lib.pavg_surrogate_get_params(self._h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def set_params(self, p):
+        p = self._np.ascontiguousarray(p, dtype=self._np.float32)
+        if p.size != self.nparams:
+            raise ValueError("wrong parameter count")
+        self._check(self._lib.pavg_surrogate_set_params(self._h, p.ctypes.data_as(ctypes.c_void_p)))
+
+    def scaling(self):
+        np = self._np
+        mx, sx = np.zeros(N_SUR_IN, np.float32), np.zeros(N_SUR_IN, np.float32)
+        my, sy = np.zeros(N_SUR_OUT, np.float32), np.zeros(N_SUR_OUT, np.float32)
+        self._check(self._lib.pavg_surrogate_get_scaling(self._h, *[a.ctypes.data_as(ctypes.c_void_p)
+                                                                    for a in (mx, sx, my, sy)]))
+        return mx, sx, my, sy
+
+    def set_scaling(self, mx, sx, my, sy):
+        np = self._np
+        arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (mx, sx, my, sy)]
+        self._check(self._lib.pavg_surrogate_set_scaling(self._h, *[a.ctypes.data_as(ctypes.c_void_p)
+                                                                    for a in arrs]))
+
+    def add_pairs(self, model, U, Vc, Vf):
+        n = len(U)
+        arr = lambda L: (ctypes.c_void_p * n)(*[_ptr(x, model.n).value for x in L])
+        self._check(self._lib.pavg_surrogate_add_pairs(self._h, model._h, n, arr(U), arr(Vc), arr(Vf), _stream()))
+
+    def rows(self):
+        r = ctypes.c_int64()
+        self._check(self._lib.pavg_surrogate_rows(self._h, ctypes.byref(r)))
+        return r.value
+
+    def fit_scaling(self):
+        self._check(self._lib.pavg_surrogate_fit_scaling(self._h, _stream()))
+
+    def train(self, epochs, batch=8192, lr=1e-3, seed=7706):
+        loss = (ctypes.c_double * max(epochs, 1))()
+        self._check(self._lib.pavg_surrogate_train(self._h, int(epochs), int(batch), float(lr), ctypes.c_uint64(seed),
+                                                   loss, _stream()))
+        return list(loss)[:epochs]
+
+    def gradient(self, X, Z):
+        B = X.shape[0]
+        g = torch.empty(self.nparams, dtype=torch.float32, device=X.device)
+        loss = ctypes.c_double()
+        self._check(self._lib.pavg_surrogate_gradient(self._h, _fptr(X, B * N_SUR_IN), _fptr(Z, B * N_SUR_OUT), int(B),
+                                                      _fptr(g), ctypes.byref(loss), _stream()))
+        return loss.value, g
+
+    def adam_step(self, grad, lr):
+        self._check(self._lib.pavg_surrogate_adam_step(self._h, _fptr(grad, self.nparams), float(lr), _stream()))
+
+    def features(self, model, U, V, standardised=False):
+        X = torch.empty((model.n_cells, N_SUR_IN), dtype=torch.float32, device=U.device)
+        self._check(self._lib.pavg_surrogate_features(self._h, model._h, _ptr(U, model.n), _ptr(V, model.n), _fptr(X),
+                                                      1 if standardised else 0, _stream()))
+        return X
+
+    def apply(self, model, U, V, out=None, bf16=False):
+        out = torch.empty_like(U) if out is None else out
+        self._check(self._lib.pavg_surrogate_apply(self._h, model._h, _ptr(U, model.n), _ptr(V, model.n),
+                                                   _ptr(out, model.n), 1 if bf16 else 0, _stream()))
+        return out
+
+    def averaged_rhs(self, model, T, Mc, Mf, U, out=None, threshold=1e-3, check=True, bf16=False):
+        """(out, used_fallback, rel_err): the surrogate form of N-bar(U) judged by the Mf-shift sum."""
+        out = torch.empty_like(U) if out is None else out
+        fb, err = ctypes.c_int(), ctypes.c_double()
+        self._check(self._lib.pavg_surrogate_averaged_rhs(self._h, model._h, float(T), int(Mc), int(Mf),
+                                                          float(threshold), 1 if check else 0, 1 if bf16 else 0,
+                                                          _ptr(U, model.n), _ptr(out, model.n), ctypes.byref(fb),
+                                                          ctypes.byref(err), _stream()))
+        return out, bool(fb.value), err.value
