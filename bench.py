@@ -8,6 +8,9 @@ balanced state, through the library's C-ABI (graph-replayed).
 
 Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank evaluates its
 own independent state (weak scaling, no collective on the data path).
+Single-GPU runs add three legs to the line: the mixed-precision mode on the
+same state, the batched evaluation of 64 independent instances, and the
+learned surrogate (trained at refinement 5, applied at refinement 6).
 --impl reference times the FP64 CPU oracle (the plain literal per-shift form)
 on a bounded sample of the same workload and prints its own line.
 """
@@ -85,6 +88,159 @@ def _mixed_mode(pavg, cfg, Ud, ref, args, stream):
            "stated_bound": {"u": 1e-5, "eta": 5e-4}, "cg_sweeps_mean": st["cg_sweeps_mean"],
            "cg_iters_mean": st["cg_iters_mean"], "error_flags": st["error_flags"]}
     m.close()
+    return res
+
+
+# ----------------------------------------------------------------------------- batched instances
+SURROGATE = {"train_refinement": 5, "test_refinement": 6, "T_s": 4 * 3600.0, "Mc": 8, "Mf": 128, "pairs": 24,
+             "hidden": 128, "epochs": 30, "batch": 8192, "lr": 2e-3, "tests": 2}
+
+
+def _state_job(job):
+    """One seeded state (runs in a spawned pool worker; no CUDA)."""
+    r, seed = job
+    from oracle.mesh import build_mesh
+    from paper_2103_07706_gb300.inputs import harmonic_state
+    m = build_mesh(r, CONFIG["R"])
+    return harmonic_state(m.verts, m.cells, seed, 16)[0]
+
+
+def _make_states(jobs):
+    """States of the batched and surrogate legs, built on the host cores in a
+    spawned pool before the first CUDA call."""
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        return pool.map(_state_job, jobs)
+
+
+def _batch_jobs():
+    from paper_2103_07706_gb300.inputs import batch_workload
+    return [(w["refinement"], w["state_seed"]) for w in batch_workload()]
+
+
+def _surrogate_jobs():
+    S = SURROGATE
+    return ([(S["train_refinement"], 5000 + i) for i in range(S["pairs"])] +
+            [(S["test_refinement"], 6000 + i) for i in range(S["tests"])])
+
+
+def _batch_leg(pavg, states):
+    """64 independent instances (refinements 4-6, T in [0.25, 4] h, M in
+    {16, 32, 64, 128}): one batched evaluation (persistent recurrences,
+    autotuned grid) against the same instances one after another."""
+    import torch
+    from paper_2103_07706_gb300.inputs import batch_workload, lambda_max_for
+    work = batch_workload()
+    ms = [pavg.Model(w["refinement"], lambda_max=lambda_max_for(w["refinement"])) for w in work]
+    U = [torch.from_numpy(x).cuda() for x in states]
+    T = [w["T"] for w in work]
+    M = [w["M"] for w in work]
+    b = pavg.Batch(ms)
+    t0 = time.time()
+    out = b.averaged_rhs(T, M, U)  # autotune + capture
+    b.sync()
+    first_s = time.time() - t0
+    for m in ms:
+        m.reset_stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    b.averaged_rhs(T, M, U, out)
+    e1.record()
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1)
+    fwd, bwd = b.kernel_time()
+    b.sync()
+    f32 = f64 = 0.0
+    for m in ms:
+        st = m.stats()
+        a, c = _cg_flops(m.n_cells, m.n_u, st["cg_iters_mean"], st["cg_sweeps_mean"])
+        f32 += st["cg_solves"] * a
+        f64 += st["cg_solves"] * c
+    seq = [torch.empty_like(u) for u in U]
+    for i, m in enumerate(ms):  # capture each instance's graph
+        m.averaged_rhs(T[i], M[i], U[i], seq[i])
+    torch.cuda.synchronize()
+    e0.record()
+    for i, m in enumerate(ms):
+        m.averaged_rhs(T[i], M[i], U[i], seq[i])
+    e1.record()
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1)
+    diff = max(float(((o - q).norm() / q.norm()).item()) for o, q in zip(out, seq))
+    chain_s = (fwd + bwd) / 1e3
+    res = {"workload": "64 instances, refinements 4-6, T ~ U[0.25, 4] h, M in {16, 32, 64, 128}, harmonic l<=16",
+           "value": len(ms) / (t_batch / 1e3), "unit": "instance-evals/s", "ms_per_batch": t_batch,
+           "sequential_ms": t_seq, "speedup_vs_sequential": t_seq / t_batch,
+           "max_rel_l2_vs_single_instance": diff, "first_call_s": first_s, "config": b.config(),
+           "forward_chain_ms": fwd, "clenshaw_ms": bwd,
+           "roofline": {"bound": "alu", "kernel": "k_chain (persistent recurrences, all instances)",
+                        "achieved": f32 / chain_s / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": f32 / chain_s / 1e12 / FP32_PEAK_TFLOPS, "fp64_achieved": f64 / chain_s / 1e12,
+                        "note": "FP32 CG flops of every solve in both launches over their summed duration"},
+           "K_max": max(m.stats()["last_degree"] for m in ms)}
+    b.close()
+    for m in ms:
+        m.close()
+    return res
+
+
+def _surrogate_leg(pavg, states):
+    """Trains the surrogate on pairs generated by the method at refinement 5
+    (T = 4 h, M = 8 corrected towards M = 128) and applies it at refinement 6."""
+    import numpy as np
+    import torch
+    from paper_2103_07706_gb300.inputs import lambda_max_for
+    S = SURROGATE
+    T, Mc, Mf = S["T_s"], S["Mc"], S["Mf"]
+    mt = pavg.Model(S["train_refinement"], lambda_max=lambda_max_for(S["train_refinement"]))
+    t0 = time.time()
+    U = [torch.from_numpy(x).cuda() for x in states[:S["pairs"]]]
+    Vc = [mt.averaged_rhs(T, Mc, u) for u in U]
+    Vf = [mt.averaged_rhs(T, Mf, u) for u in U]
+    mt.sync()
+    gen_s = time.time() - t0
+    sur = pavg.Surrogate(hidden=S["hidden"], seed=2103)
+    t0 = time.time()
+    sur.add_pairs(mt, U, Vc, Vf)
+    sur.fit_scaling()
+    loss = sur.train(S["epochs"], S["batch"], S["lr"])
+    train_s = time.time() - t0
+    rows = sur.rows()
+    del U, Vc, Vf
+    mt.close()
+    m6 = pavg.Model(S["test_refinement"], lambda_max=lambda_max_for(S["test_refinement"]))
+    zero = pavg.Surrogate(hidden=8)
+    zero.set_params(np.zeros(zero.nparams, dtype=np.float32))
+    tests = [torch.from_numpy(x).cuda() for x in states[S["pairs"]:]]
+    e_cheap, e_sur, e_bf = [], [], []
+    for u in tests:
+        e_cheap.append(zero.averaged_rhs(m6, T, Mc, Mf, u, threshold=1.0)[2])
+        e_sur.append(sur.averaged_rhs(m6, T, Mc, Mf, u, threshold=1.0)[2])
+        e_bf.append(sur.averaged_rhs(m6, T, Mc, Mf, u, threshold=1.0, bf16=True)[2])
+    out = torch.empty_like(tests[0])
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    sur.averaged_rhs(m6, T, Mc, Mf, tests[0], out, check=False)
+    m6.averaged_rhs(T, Mf, tests[0], out)
+    torch.cuda.synchronize()
+    ev[0].record()
+    sur.averaged_rhs(m6, T, Mc, Mf, tests[0], out, check=False)
+    ev[1].record()
+    m6.averaged_rhs(T, Mf, tests[0], out)
+    ev[2].record()
+    torch.cuda.synchronize()
+    t_sur, t_full = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    res = {"workload": f"train r{S['train_refinement']} ({S['pairs']} pairs, {rows} cell rows), T = 4 h, "
+                       f"M = {Mc} corrected towards M = {Mf}; applied at r{S['test_refinement']} on "
+                       f"{len(tests)} unseen states",
+           "pair_generation_s": gen_s, "train_s": train_s, "loss_first_epoch": loss[0], "loss_last_epoch": loss[-1],
+           "rel_err_energy_cheap_M8": float(np.mean(e_cheap)), "rel_err_energy_surrogate": float(np.mean(e_sur)),
+           "rel_err_energy_surrogate_bf16": float(np.mean(e_bf)),
+           "gain": float(np.mean(e_cheap) / np.mean(e_sur)),
+           "surrogate_ms": t_sur, "full_M128_ms": t_full, "speedup_vs_full": t_full / t_sur,
+           "fallback_threshold": 1e-3, "would_fall_back": bool(np.mean(e_sur) > 1e-3)}
+    sur.close()
+    zero.close()
+    m6.close()
     return res
 
 
@@ -251,6 +407,13 @@ def run_pavg(args):
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    legs = set(args.legs.split(",")) if world == 1 else {"fp64"}
+    batch_states = sur_states = None
+    if legs & {"batch", "surrogate"}:  # host work in a spawned pool, before any CUDA call
+        jobs = (_batch_jobs() if "batch" in legs else []) + (_surrogate_jobs() if "surrogate" in legs else [])
+        states = _make_states(jobs)
+        nb = len(_batch_jobs()) if "batch" in legs else 0
+        batch_states, sur_states = states[:nb], states[nb:]
     q = proc = None
     if want_cpu:  # spawned before any CUDA call
         ctxmp = mp.get_context("spawn")
@@ -329,7 +492,9 @@ def run_pavg(args):
     model.sync()
 
     # mixed-precision mode on the same state: throughput and error against the FP64 result above
-    mixed = _mixed_mode(pavg, cfg, Ud, out, args, stream)
+    mixed = _mixed_mode(pavg, cfg, Ud, out, args, stream) if "mixed" in legs else None
+    batch = _batch_leg(pavg, batch_states) if "batch" in legs else None
+    surrogate = _surrogate_leg(pavg, sur_states) if "surrogate" in legs else None
 
     # parity of the small configuration against the oracle (computed by the spawned leg)
     cpu = None
@@ -384,7 +549,8 @@ def run_pavg(args):
             "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": 8 * model.n,
                     "d2h_bytes_per_step": 8 * model.n},
             "gpu_launches": st["kernel_launches"] * args.steps,
-            "roofline": roof, "cpu_baseline": cpu, "parity": parity, "precision_mixed": mixed, "clocks": clk,
+            "roofline": roof, "cpu_baseline": cpu, "parity": parity, "precision_mixed": mixed, "batch": batch, "surrogate": surrogate,
+            "clocks": clk,
             "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
             "error_flags": st["error_flags"]}
     if rank == 0:
@@ -401,6 +567,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pavg", choices=["pavg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--legs", default="fp64,mixed,batch,surrogate",
+                    help="comma list: fp64 (always), mixed, batch, surrogate (single GPU only)")
     ap.add_argument("--refinement", type=int, default=None, help="smaller case (profiling only)")
     ap.add_argument("--M", type=int, default=None, help="number of shifts (profiling only)")
     args = ap.parse_args()
@@ -409,6 +577,7 @@ def main():
         CONFIG.update({"refinement": r, "cells": 20 * 4 ** r, "M": args.M or CONFIG["M"],
                        "lambda_max": LAMBDA_R6 / 2 ** (6 - r)})
         args.no_cpu_baseline = True
+        args.legs = "fp64"
     if args.impl == "reference":
         return run_reference(args)
     return run_pavg(args)

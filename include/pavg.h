@@ -278,7 +278,10 @@ const char* pavg_batch_last_error(const pavg_batch* b);
  * features: per cell, its 15 local values (12 velocity coefficients times the
  * local-to-global signs of Sec. 2.5, 3 elevation values) of U and of V, the
  * same for the 3 cells across its edges (their own frames, local edge order),
- * and z_c / R, G00 / det, G01 / det, G11 / det of the cell: 124 FP32 inputs.
+ * and z_c / R, G00 / det, G01 / det, G11 / det of the cell: 124 FP32 inputs;
+ * velocity values (moments of a flux) are divided by the row cell's length
+ * scale sqrt(det), so that meshes of different refinement give rows of the
+ * same size (targets likewise; outputs are multiplied back).
  * MLP: 124 -> hidden -> hidden -> 15, tanh hidden units, FP32 weights, in
  * flat order W1 [hidden][124], b1, W2 [hidden][hidden], b2, W3 [15][hidden], b3.
  * scatter: elevation and interior velocity values to their DOFs; an edge DOF

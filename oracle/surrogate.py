@@ -16,11 +16,16 @@ cell's local frame, i.e. times the local-to-global signs of Sec. 2.5, and 3
 elevation values) of U and of V, the same for the three cells across its
 edges (in their own local frames, in local edge order), and 4 geometric
 values: z_c / R at the centroid (f / 2 Omega) and G / det (the cell's metric
-over its area).  124 inputs.
+over its area).  124 inputs.  The velocity coefficients are moments of a
+flux (velocity times length, Sec. 2.5), so every velocity value of a row is
+divided by the row cell's length scale l_c = sqrt(det_c): rows of meshes of
+different refinement then carry values of the same size.
 MLP: two hidden layers of tanh units, linear output of 15 values per cell.
-targets: the cell's 15 local values of N-bar_Mf(U) - V.
-scatter: elevation and interior velocity values go to their DOFs; an edge
-DOF takes the mean of the two cells' values (times their signs).
+targets: the cell's 15 local values of N-bar_Mf(U) - V, velocity values
+divided by l_c.
+scatter: velocity values times l_c; elevation and interior velocity values
+go to their DOFs; an edge DOF takes the mean of the two cells' values (times
+their signs).
 Loss: mean squared error over cells and outputs of the standardised
 targets.  Training: Adam (Kingma & Ba 2015), beta1 0.9, beta2 0.999,
 eps 1e-8.
@@ -59,29 +64,43 @@ def geometry(asm):
                      asm.G[:, 1, 1] / asm.det], axis=1)
 
 
+def length_scale(asm):
+    """(F,): l_c = sqrt(det_c), det_c = |J0 x J1| (twice the flat cell's area)."""
+    return np.sqrt(asm.det)
+
+
+def _velocity_scaled(block, ell):
+    """A (F, 15) block with its 12 velocity columns divided by ell (F,)."""
+    out = block.copy()
+    out[:, :12] /= ell[:, None]
+    return out
+
+
 def features(asm, U, V):
     """(F, 124) raw (unstandardised) inputs of every cell."""
     nb = neighbours(asm.mesh)
+    ell = length_scale(asm)
     lu, lv = local_values(asm, U), local_values(asm, V)
-    parts = [lu, lv]
+    parts = [_velocity_scaled(lu, ell), _velocity_scaled(lv, ell)]
     for i in range(3):
-        parts += [lu[nb[:, i]], lv[nb[:, i]]]
+        parts += [_velocity_scaled(lu[nb[:, i]], ell), _velocity_scaled(lv[nb[:, i]], ell)]
     parts.append(geometry(asm))
     return np.concatenate(parts, axis=1)
 
 
 def targets(asm, D):
-    """(F, 15) local values of a correction vector D."""
-    return local_values(asm, D)
+    """(F, 15) local values of a correction vector D, velocity values over l_c."""
+    return _velocity_scaled(local_values(asm, D), length_scale(asm))
 
 
 def scatter(asm, Y):
-    """Vector of n values from per-cell local values Y (F, 15)."""
+    """Vector of n values from per-cell local values Y (F, 15), velocity values times l_c."""
     out = np.zeros(asm.n_u + asm.n_eta)
+    ell = length_scale(asm)
     for c in range(asm.mesh.n_cells):
         for k in range(12):
             d = asm.udofs[c, k]
-            v = asm.sign[c, k] * Y[c, k]
+            v = asm.sign[c, k] * Y[c, k] * ell[c]
             out[d] += 0.5 * v if k < 9 else v  # local DOFs 0-8 sit on edges, 9-11 inside
         out[asm.n_u + asm.etadofs[c]] = Y[c, 12:15]
     return out

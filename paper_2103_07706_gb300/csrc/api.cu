@@ -8,6 +8,8 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
+#include <tuple>
 #include <random>
 #include <string>
 #include <vector>
@@ -377,6 +379,81 @@ int check_flags(pavg_ctx* ctx) {
   return PAVG_OK;
 }
 
+// Meshes and their operator data are shared by every context with the same
+// refinement, radius and rotation rate on one device: they are read-only after
+// set-up, and instances that share them also share their L2 footprint.
+std::mutex g_mesh_mu;
+std::map<std::tuple<int, double, double, int>, SharedMesh*> g_meshes;
+
+void free_device_mesh(DeviceMesh& m) {
+  cudaFree(m.cell_edges); cudaFree(m.cell_aligned); cudaFree(m.edge_plus); cudaFree(m.edge_minus);
+  cudaFree(m.edge_lpos); cudaFree(m.M1); cudaFree(m.C); cudaFree(m.det); cudaFree(m.G); cudaFree(m.dinv);
+  cudaFree(m.M1f); cudaFree(m.Pinv); cudaFree(m.M1p); cudaFree(m.tri);
+  m = DeviceMesh();
+}
+
+int build_shared_mesh(const pavg_params* p, SharedMesh* sh, std::string* why) {
+  build_mesh(p->refinement, p->radius, &sh->mesh);
+  RefElement el;
+  build_reference_element(&el);
+  HostCellData hc;
+  ConstTables tab;
+  build_cell_data(sh->mesh, el, p->omega, &hc, &tab);
+  if (upload_tables(tab) != cudaSuccess || upload_chain_tables(tab) != cudaSuccess) {
+    *why = "constant upload failed";
+    return PAVG_ERR_CUDA;
+  }
+  const Mesh& ms = sh->mesh;
+  DeviceMesh& m = sh->dm;
+  m.F = ms.F(); m.E = ms.E(); m.n_u = 3 * m.E + 3 * m.F; m.n_eta = 3 * m.F; m.n = m.n_u + m.n_eta;
+  std::vector<int32_t> ce(3 * m.F);
+  for (int64_t c = 0; c < m.F; ++c)
+    for (int i = 0; i < 3; ++i) ce[i * m.F + c] = ms.cell_edges[3 * c + i];
+  // FP32 element matrices both packed (shared-memory residency) and in row
+  // blocks (streamed): either solver path may run on any mesh
+  const bool ok = upload(&m.cell_edges, ce) == cudaSuccess && upload(&m.cell_aligned, ms.cell_aligned) == cudaSuccess &&
+                  upload(&m.edge_plus, ms.edge_plus) == cudaSuccess && upload(&m.edge_minus, ms.edge_minus) == cudaSuccess &&
+                  upload(&m.edge_lpos, ms.edge_lpos) == cudaSuccess && upload(&m.M1, hc.M1) == cudaSuccess &&
+                  upload(&m.C, hc.C) == cudaSuccess && upload(&m.det, hc.det) == cudaSuccess &&
+                  upload(&m.G, hc.G) == cudaSuccess && upload(&m.dinv, hc.dinv) == cudaSuccess &&
+                  upload(&m.Pinv, hc.Pinv) == cudaSuccess && upload(&m.tri, hc.tri) == cudaSuccess &&
+                  upload(&m.M1p, hc.M1p) == cudaSuccess && upload(&m.M1f, hc.M1f) == cudaSuccess;
+  if (!ok) {
+    free_device_mesh(m);
+    *why = "device upload failed";
+    return PAVG_ERR_NOMEM;
+  }
+  return PAVG_OK;
+}
+
+int acquire_mesh(const pavg_params* p, int device, SharedMesh** out, std::string* why) {
+  std::lock_guard<std::mutex> lock(g_mesh_mu);
+  const auto key = std::make_tuple(p->refinement, p->radius, p->omega, device);
+  auto it = g_meshes.find(key);
+  if (it != g_meshes.end()) {
+    ++it->second->refs;
+    *out = it->second;
+    return PAVG_OK;
+  }
+  std::unique_ptr<SharedMesh> sh(new SharedMesh());
+  int rc = build_shared_mesh(p, sh.get(), why);
+  if (rc) return rc;
+  sh->refs = 1;
+  sh->key = key;
+  g_meshes.emplace(key, sh.get());
+  *out = sh.release();
+  return PAVG_OK;
+}
+
+void release_mesh(SharedMesh* sh) {
+  if (!sh) return;
+  std::lock_guard<std::mutex> lock(g_mesh_mu);
+  if (--sh->refs > 0) return;
+  g_meshes.erase(sh->key);
+  free_device_mesh(sh->dm);
+  delete sh;
+}
+
 void free_ctx(pavg_ctx* c) {
   if (!c) return;
   for (auto& kv : c->plans) {
@@ -387,9 +464,8 @@ void free_ctx(pavg_ctx* c) {
     cudaFree(kv.second.dB);
   }
   DeviceMesh& m = c->dm;
-  cudaFree(m.cell_edges); cudaFree(m.cell_aligned); cudaFree(m.edge_plus); cudaFree(m.edge_minus);
-  cudaFree(m.edge_lpos); cudaFree(m.M1); cudaFree(m.C); cudaFree(m.det); cudaFree(m.G); cudaFree(m.dinv);
   cudaFree(m.topo);
+  release_mesh(c->shared);
   CgWork& w = c->cg;
   cudaFree(w.x); cudaFree(w.r[0]); cudaFree(w.r[1]); cudaFree(w.s[0]); cudaFree(w.s[1]);
   cudaFree(w.w[0]); cudaFree(w.w[1]); cudaFree(w.w[2]); cudaFree(w.p); cudaFree(w.partial);
@@ -398,7 +474,6 @@ void free_ctx(pavg_ctx* c) {
   cudaFree(wi.x[0]); cudaFree(wi.x[1]); cudaFree(wi.ax); cudaFree(wi.r64); cudaFree(wi.fbuf);
   cudaFree(wi.partial); cudaFree(wi.partial_f);
   cudaFree(wi.bar); cudaFree(wi.scal); cudaFree(wi.tag);
-  cudaFree(m.M1f); cudaFree(m.Pinv); cudaFree(m.M1p); cudaFree(m.tri);
   cudaFree(c->ru);
   for (auto* v : c->vec) cudaFree(v);
   cudaFree(c->io_in); cudaFree(c->io_out); cudaFree(c->Q); cudaFree(c->Um); cudaFree(c->Rm);
@@ -459,29 +534,14 @@ int pavg_create(const pavg_params* p, pavg_ctx** out) {
   int rc = PAVG_OK;
   try {
     cudaGetDevice(&ctx->device);
-    build_mesh(p->refinement, p->radius, &ctx->mesh);
-    RefElement el;
-    build_reference_element(&el);
-    HostCellData hc;
-    ConstTables tab;
-    build_cell_data(ctx->mesh, el, p->omega, &hc, &tab);
-    if (upload_tables(tab) != cudaSuccess || upload_chain_tables(tab) != cudaSuccess) {
-      rc = set_err(ctx, PAVG_ERR_CUDA, "constant upload failed");
-      throw 0;
-    }
-    const Mesh& ms = ctx->mesh;
+    SharedMesh* sh = nullptr;
+    std::string why;
+    if ((rc = acquire_mesh(p, ctx->device, &sh, &why))) { set_err(ctx, rc, why); throw 0; }
+    ctx->shared = sh;
+    ctx->mesh = sh->mesh;
+    ctx->dm = sh->dm;
     DeviceMesh& m = ctx->dm;
-    m.F = ms.F(); m.E = ms.E(); m.n_u = 3 * m.E + 3 * m.F; m.n_eta = 3 * m.F; m.n = m.n_u + m.n_eta;
-    std::vector<int32_t> ce(3 * m.F);
-    for (int64_t c = 0; c < m.F; ++c)
-      for (int i = 0; i < 3; ++i) ce[i * m.F + c] = ms.cell_edges[3 * c + i];
-    bool ok = upload(&m.cell_edges, ce) == cudaSuccess && upload(&m.cell_aligned, ms.cell_aligned) == cudaSuccess &&
-              upload(&m.edge_plus, ms.edge_plus) == cudaSuccess && upload(&m.edge_minus, ms.edge_minus) == cudaSuccess &&
-              upload(&m.edge_lpos, ms.edge_lpos) == cudaSuccess && upload(&m.M1, hc.M1) == cudaSuccess &&
-              upload(&m.C, hc.C) == cudaSuccess && upload(&m.det, hc.det) == cudaSuccess &&
-              upload(&m.G, hc.G) == cudaSuccess && upload(&m.dinv, hc.dinv) == cudaSuccess &&
-              upload(&m.Pinv, hc.Pinv) == cudaSuccess && upload(&m.tri, hc.tri) == cudaSuccess &&
-              dalloc(&m.topo, m.n_eta) == cudaSuccess;
+    bool ok = dalloc(&m.topo, m.n_eta) == cudaSuccess;
     if (!ok) { rc = set_err(ctx, PAVG_ERR_NOMEM, "device upload failed"); throw 0; }
     cudaMemset(m.topo, 0, sizeof(double) * m.n_eta);
     CgWork& w = ctx->cg;
@@ -498,9 +558,6 @@ int pavg_create(const pavg_params* p, pavg_ctx** out) {
     for (auto*& v : ctx->vec) ok = ok && dalloc(&v, m.n) == cudaSuccess;
     CgIrWork& wi = ctx->cgi;
     ok = ok && cg_ir_configure(m.F, &wi) == cudaSuccess;
-    // FP32 element matrices: packed for the shared-memory path, row blocks when streamed
-    // (the batched kernel may take either path for any mesh)
-    if (ok) ok = upload(&m.M1p, hc.M1p) == cudaSuccess && upload(&m.M1f, hc.M1f) == cudaSuccess;
     ok = ok && dalloc(&wi.x[0], m.n_u) == cudaSuccess && dalloc(&wi.x[1], m.n_u) == cudaSuccess &&
          dalloc(&wi.ax, m.n_u) == cudaSuccess && dalloc(&wi.r64, m.n_u) == cudaSuccess &&
          dalloc(&wi.fbuf, 9 * 4 * (size_t)(m.E + m.F)) == cudaSuccess &&

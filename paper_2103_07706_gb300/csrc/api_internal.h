@@ -14,6 +14,7 @@
 using namespace pavg;
 using pavg_detail::AvgPlan;
 using pavg_detail::EventPair;
+using pavg_detail::SharedMesh;
 
 #define CK(call)                                                                        \
   do {                                                                                  \

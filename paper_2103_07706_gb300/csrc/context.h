@@ -5,6 +5,7 @@
 
 #include <map>
 #include <string>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -28,12 +29,23 @@ struct AvgPlan {
   std::vector<EventPair> pairs;   // CG event brackets inside the graph (owned)
 };
 
+// Mesh and operator data shared by the contexts with the same refinement,
+// radius, rotation rate and device (reference counted, read-only after set-up).
+struct SharedMesh {
+  int refs = 0;
+  std::tuple<int, double, double, int> key;
+  pavg_detail::SharedMesh* shared = nullptr;
+  pavg::Mesh mesh;
+  pavg::DeviceMesh dm;  // topo stays per context
+};
+
 }  // namespace pavg_detail
 
 struct pavg_ctx {
   using AvgPlan = pavg_detail::AvgPlan;
   using EventPair = pavg_detail::EventPair;
   pavg_params p{};
+  pavg_detail::SharedMesh* shared = nullptr;
   pavg::Mesh mesh;
   pavg::DeviceMesh dm;
   pavg::CgWork cg;

@@ -182,18 +182,20 @@ __device__ __forceinline__ int64_t across(const DeviceMesh& m, int64_t c, int i)
 }
 
 // Row c of the feature matrix: own U, own V, then (U, V) of the cells across
-// local edges 0, 1, 2, then the 4 geometric values; (x - mu) / sd when mu is given.
+// local edges 0, 1, 2, then the 4 geometric values; velocity values over the
+// row cell's length scale sqrt(det_c); (x - mu) / sd when mu is given.
 __global__ void k_sur_features(DeviceMesh m, const double* __restrict__ U, const double* __restrict__ V,
                                const float* __restrict__ geo, const float* __restrict__ mu,
                                const float* __restrict__ sd, float* X) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= m.F) return;
   float* row = X + (size_t)c * kSurInputs;
+  const double inv_ell = 1.0 / sqrt(m.det[c]);
   double v[15];
   auto put = [&](int base) {
 #pragma unroll
     for (int k = 0; k < 15; ++k) {
-      float x = (float)v[k];
+      float x = (float)(k < 12 ? v[k] * inv_ell : v[k]);
       if (mu) x = (x - mu[base + k]) / sd[base + k];
       row[base + k] = x;
     }
@@ -217,7 +219,8 @@ __global__ void k_sur_features(DeviceMesh m, const double* __restrict__ U, const
   }
 }
 
-// Row c of the targets: local values of Vf - Vc, (z - mu) / sd when mu is given.
+// Row c of the targets: local values of Vf - Vc, velocity values over
+// sqrt(det_c), (z - mu) / sd when mu is given.
 __global__ void k_sur_targets(DeviceMesh m, const double* __restrict__ Vf, const double* __restrict__ Vc,
                               const float* __restrict__ mu, const float* __restrict__ sd, float* Z) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -225,15 +228,17 @@ __global__ void k_sur_targets(DeviceMesh m, const double* __restrict__ Vf, const
   double a[15], b[15];
   cell_local(m, c, Vf, a);
   cell_local(m, c, Vc, b);
+  const double inv_ell = 1.0 / sqrt(m.det[c]);
 #pragma unroll
   for (int k = 0; k < 15; ++k) {
-    float z = (float)(a[k] - b[k]);
+    float z = (float)(k < 12 ? (a[k] - b[k]) * inv_ell : a[k] - b[k]);
     if (mu) z = (z - mu[k]) / sd[k];
     Z[(size_t)c * kSurOutputs + k] = z;
   }
 }
 
-// corr += scatter of the de-standardised outputs: interior velocity and
+// corr += scatter of the de-standardised outputs (velocity values times
+// sqrt(det_c)): interior velocity and
 // elevation values stored, edge values half from each of the two cells
 // (corr's edge DOFs zero on entry; two additions into zero are exact in
 // either order).
@@ -245,8 +250,12 @@ __global__ void k_sur_scatter(DeviceMesh m, const float* __restrict__ Y, const f
   double sg[12];
   cell_dofs(m, c, dof, sg);
   double y[15];
+  const double ell = sqrt(m.det[c]);
 #pragma unroll
-  for (int k = 0; k < 15; ++k) y[k] = (double)Y[(size_t)c * kSurOutputs + k] * (double)sd[k] + (double)mu[k];
+  for (int k = 0; k < 15; ++k) {
+    y[k] = (double)Y[(size_t)c * kSurOutputs + k] * (double)sd[k] + (double)mu[k];
+    if (k < 12) y[k] *= ell;
+  }
 #pragma unroll
   for (int k = 0; k < 9; ++k) atomicAdd(&corr[dof[k]], 0.5 * sg[k] * y[k]);
 #pragma unroll

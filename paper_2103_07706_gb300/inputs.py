@@ -35,17 +35,27 @@ def _gl01(n):
 
 
 def real_sph_harm_sum(points, coeffs, lmax):
-    """sum_lm coeffs[l, m + lmax] Y_lm(points/|points|), normalised recurrence."""
+    """sum_lm coeffs[l, m + lmax] Y_lm(points/|points|), normalised recurrence.
+
+    For each order m the associated Legendre values are summed over l first;
+    cos(m phi) and sin(m phi) come from the angle-addition recurrence."""
     p = np.asarray(points, dtype=np.float64)
     r = np.linalg.norm(p, axis=-1)
     ct = np.clip(p[..., 2] / r, -1.0, 1.0)
     st = np.sqrt(np.maximum(0.0, 1.0 - ct * ct))
-    ph = np.arctan2(p[..., 1], p[..., 0])
+    rho = np.hypot(p[..., 0], p[..., 1])
+    safe = np.where(rho > 0.0, rho, 1.0)
+    c1 = np.where(rho > 0.0, p[..., 0] / safe, 1.0)  # cos(phi), sin(phi)
+    s1 = np.where(rho > 0.0, p[..., 1] / safe, 0.0)
     out = np.zeros_like(ct)
     pmm = np.full_like(ct, math.sqrt(1.0 / (4.0 * math.pi)))
+    cm, sm = np.ones_like(ct), np.zeros_like(ct)  # cos(m phi), sin(m phi)
     for m in range(0, lmax + 1):
         if m > 0:
             pmm = math.sqrt((2.0 * m + 1.0) / (2.0 * m)) * st * pmm
+            cm, sm = cm * c1 - sm * s1, sm * c1 + cm * s1
+        acc_c = np.zeros_like(ct)
+        acc_s = np.zeros_like(ct)
         plm2 = None
         plm1 = pmm
         for l in range(m, lmax + 1):
@@ -61,11 +71,13 @@ def real_sph_harm_sum(points, coeffs, lmax):
                 plm2, plm1 = plm1, plm
             if l == 0:
                 continue
-            if m == 0:
-                out += coeffs[l, lmax] * plm
-            else:
-                out += coeffs[l, lmax + m] * math.sqrt(2.0) * plm * np.cos(m * ph)
-                out += coeffs[l, lmax - m] * math.sqrt(2.0) * plm * np.sin(m * ph)
+            acc_c += coeffs[l, lmax + m] * plm
+            if m > 0:
+                acc_s += coeffs[l, lmax - m] * plm
+        if m == 0:
+            out += acc_c
+        else:
+            out += math.sqrt(2.0) * (acc_c * cm + acc_s * sm)
     return out
 
 

@@ -166,3 +166,23 @@ def test_batch_full_size_workload():
     b.close()
     for m in ms:
         m.close()
+
+
+def test_contexts_share_the_mesh_but_not_topography():
+    """Contexts of one refinement share mesh and operator data; each keeps its
+    own topography and workspace, and destroying one leaves the other intact."""
+    import torch
+    from paper_2103_07706_gb300 import pavg
+    a = pavg.Model(2, lambda_max=LAM[2])
+    b = pavg.Model(2, lambda_max=LAM[2])
+    o = orc(2)
+    U = dev(state(o))
+    ref = a.nonlinear(U).cpu().numpy()
+    b.set_topography(dev(300.0 * np.random.default_rng(1).random(o.n_eta)))
+    assert np.array_equal(a.nonlinear(U).cpu().numpy(), ref)
+    assert not np.array_equal(b.nonlinear(U).cpu().numpy(), ref)
+    b.close()
+    assert np.array_equal(a.averaged_rhs(1800.0, 4, U).cpu().numpy(),
+                          pavg.Model(2, lambda_max=LAM[2]).averaged_rhs(1800.0, 4, U).cpu().numpy())
+    torch.cuda.synchronize()
+    a.close()

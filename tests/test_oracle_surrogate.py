@@ -83,9 +83,10 @@ def test_neighbours_from_vertex_sets(asm1):
 
 
 def test_features_place_a_single_dof(asm1):
-    """A state with one nonzero edge DOF shows up, with the cell's sign, in the
-    own slot of its two cells and in the neighbour slot of every cell next to
-    either of them (2 + 2 x 3 entries), and nowhere else."""
+    """A state with one nonzero edge DOF shows up, with the cell's sign and over
+    the row cell's length scale sqrt(det), in the own slot of its two cells and
+    in the neighbour slot of every cell next to either of them (2 + 2 x 3
+    entries), and nowhere else."""
     mesh = asm1.mesh
     n = asm1.n_u + asm1.n_eta
     nb = S.neighbours(mesh)
@@ -94,15 +95,16 @@ def test_features_place_a_single_dof(asm1):
     U[3 * e + j] = 1.0
     X = S.features(asm1, U, np.zeros(n))
     want = np.zeros_like(X[:, :120])
+    ell = np.sqrt(asm1.det)  # each row's velocity values are in units of its cell's length
     for side in range(2):
         c, i = mesh.edge_cells[e, side], mesh.edge_local[e, side]
         s = asm1.sign[c, 3 * i + j]
-        want[c, 3 * i + j] = s
+        want[c, 3 * i + j] = s / ell[c]
         for other in range(mesh.n_cells):
             for k in range(3):
                 if nb[other, k] == c:
-                    want[other, 30 + 30 * k + 3 * i + j] = s
-    assert np.array_equal(X[:, :120], want)
+                    want[other, 30 + 30 * k + 3 * i + j] = s / ell[other]
+    assert np.allclose(X[:, :120], want, rtol=1e-15, atol=0)
     assert np.count_nonzero(want) == 8
 
 
