@@ -57,6 +57,19 @@ def _cg_flops(F, n_u, iters, sweeps):
     return iters * 530.0 * F, sweeps * (288.0 * F + 6.0 * n_u)
 
 
+def job_throughput(ms_local, steps, dist=None, device="cpu"):
+    """(slowest rank's ms, whole-job evaluations per second): every rank times
+    `steps` evaluations of its own state; the job is as fast as its slowest
+    rank, and all ranks' evaluations count."""
+    import torch
+    world = dist.get_world_size() if dist is not None else 1
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * steps / (ms_max / 1e3)
+
+
 def _mixed_mode(pavg, cfg, Ud, ref, args, stream):
     """Times the PAVG_PRECISION_MIXED path on the bench state and states its
     relative L2 error per field against the FP64 GPU result `ref`."""
@@ -466,11 +479,7 @@ def run_pavg(args):
     model.sync()
     st = model.stats()
     cg_ms, cg_n = model.kernel_time()
-    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * args.steps / (ms_max / 1e3)
+    ms_max, value = job_throughput(ms, args.steps, dist, "cuda")
 
     # end to end through the C-ABI: pinned host input -> device, evaluate, result -> host
     Uh = torch.from_numpy(U).pin_memory()
@@ -485,10 +494,7 @@ def run_pavg(args):
     e3.record(stream)
     barrier()
     ms_e2e = e2.elapsed_time(e3)
-    t = torch.tensor([ms_e2e], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * args.steps / (float(t.item()) / 1e3)
+    _, e2e_value = job_throughput(ms_e2e, args.steps, dist, "cuda")
     model.sync()
 
     # mixed-precision mode on the same state: throughput and error against the FP64 result above

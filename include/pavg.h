@@ -244,6 +244,16 @@ int pavg_batch_destroy(pavg_batch* b);
 int pavg_batch_averaged_rhs(pavg_batch* b, const double* T, const int* M, const double* const* U,
                             double* const* out, void* stream);
 
+/* nsteps averaged Lawson RK4 steps (Sec. 2.3, Eqs. stage1_c to stage4) of
+ * every instance, in place on U[i] (host array of device pointers), with its
+ * own dt[i], T[i], M[i] (host arrays).  The four averaged right-hand sides of
+ * a step run as batched evaluations; the six exponentials of a step run as
+ * one persistent launch of all instances' Chebyshev chains each, followed by
+ * a one-row contraction per instance.  Results equal pavg_timestep on each
+ * context up to rounding. */
+int pavg_batch_timestep(pavg_batch* b, const double* dt, const double* T, const int* M, double* const* U,
+                        int nsteps, void* stream);
+
 /* Runs the autotuner on these inputs (the work of one call's forward chains,
  * truncated to a few steps per candidate), keeps the best configuration and
  * returns it.  Synchronises `stream`. */

@@ -70,6 +70,16 @@ struct pavg_batch {
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t ev[4] = {};
   bool ev_recorded = false;
+  // batched exponentials: per (t_i) list, the coefficient rows and the chain launch
+  struct ExpPlan {
+    std::vector<int> K;
+    std::vector<double*> coef;  // per instance [K_i + 1]: c_k(lambda |t|) sgn(t)^k
+    Launch fwd;
+    Config cfg;
+    std::vector<const double*> ws;
+  };
+  std::map<std::vector<double>, ExpPlan> exps;
+  std::vector<std::vector<double*>> stage;  // per instance: k1, k2, k3, k4, EhU, tmp, tmp2
   std::string err;
 };
 
@@ -423,6 +433,12 @@ int autotune(pavg_batch* b, BatchPlan* bp, cudaStream_t st, Config* best) {
 
 void free_batch(pavg_batch* b) {
   if (!b) return;
+  for (auto& kv : b->exps) {
+    for (auto* c : kv.second.coef) cudaFree(c);
+    free_launch(&kv.second.fwd);
+  }
+  for (auto& v : b->stage)
+    for (auto* x : v) cudaFree(x);
   for (auto& kv : b->plans) {
     drop_exec(&kv.second);
     free_launch(&kv.second.fwd);
@@ -437,6 +453,61 @@ void free_batch(pavg_batch* b) {
     if (e) cudaEventDestroy(e);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   delete b;
+}
+
+// out_i = e^{t_i L} in_i for every instance (Sec. 2.4): the Chebyshev chains
+// of all instances in one persistent launch (the forward mode of k_chain),
+// then per instance the one-row contraction out = sum_k c_k sgn(t)^k Q_k.
+int batch_expL(pavg_batch* b, const std::vector<double>& t, const std::vector<const double*>& in,
+               const std::vector<double*>& out, cudaStream_t st) {
+  const int n = (int)b->ctx.size();
+  auto it = b->exps.find(t);
+  if (it == b->exps.end()) {
+    pavg_batch::ExpPlan ep;
+    ep.K.resize(n);
+    ep.coef.assign(n, nullptr);
+    for (int i = 0; i < n; ++i) {
+      pavg_ctx* c = b->ctx[i];
+      std::vector<double> cf = cheb_coefficients(c->lam * std::fabs(t[i]), c->p.cheb_tol);
+      ep.K[i] = (int)cf.size() - 1;
+      const double sg = t[i] >= 0 ? 1.0 : -1.0;
+      double f = 1.0;
+      for (auto& x : cf) { x *= f; f *= sg; }
+      if (upload(&ep.coef[i], cf) != cudaSuccess) return bset_err(b, PAVG_ERR_NOMEM, "coefficient upload");
+    }
+    it = b->exps.emplace(t, std::move(ep)).first;
+  }
+  pavg_batch::ExpPlan& ep = it->second;
+  for (int i = 0; i < n; ++i) {
+    pavg_ctx* c = b->ctx[i];
+    int rc = ensure_avg_workspace(c, ep.K[i], std::max(c->Mcap, 1));
+    if (rc) return bset_err(b, rc, "instance " + std::to_string(i) + ": " + c->err);
+  }
+  if (!b->have_cfg) { b->cfg = Config(); b->have_cfg = true; }
+  if (ep.fwd.probs.empty() || !same(ep.cfg, b->cfg) || ep.ws != workspaces(b)) {
+    BatchPlan bp;
+    bp.K = ep.K;
+    std::vector<int> idx;
+    for (int i = 0; i < n; ++i)
+      if (ep.K[i] >= 1) idx.push_back(i);
+    int rc = build_launch(b, bp, 0, idx, b->cfg, -1, false, &ep.fwd);
+    if (!rc) rc = upload_launch(b, &ep.fwd);
+    if (rc) return rc;
+    ep.cfg = b->cfg;
+    ep.ws = workspaces(b);
+  }
+  for (int i = 0; i < n; ++i) {
+    pavg_ctx* c = b->ctx[i];
+    BCK(cudaMemcpyAsync(c->Q, in[i], sizeof(double) * c->dm.n, cudaMemcpyDeviceToDevice, st));
+  }
+  int rc = enq_launch(b, ep.fwd, b->cfg, 0, -1, st);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) {
+    pavg_ctx* c = b->ctx[i];
+    const int64_t nn = c->dm.n;
+    BCK(launch_combine(ep.coef[i], 1, ep.K[i] + 1, nullptr, c->Q, nn, out[i], nn, nn, st));
+  }
+  return PAVG_OK;
 }
 
 }  // namespace
@@ -556,6 +627,67 @@ int pavg_batch_averaged_rhs(pavg_batch* b, const double* T, const int* M, const 
     c->last_launches = 0;
   }
   if (!b->ctx.empty()) b->ctx[0]->last_launches = bp->launches;
+  return PAVG_OK;
+}
+
+int pavg_batch_timestep(pavg_batch* b, const double* dt, const double* T, const int* M, double* const* U, int nsteps,
+                        void* stream) {
+  if (!b || !dt || !T || !M || !U || nsteps < 0) return PAVG_ERR_INVAL;
+  const int n = (int)b->ctx.size();
+  for (int i = 0; i < n; ++i)
+    if (!U[i] || !std::isfinite(dt[i])) return bset_err(b, PAVG_ERR_INVAL, "null state or non-finite dt");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (b->stage.empty()) {
+    b->stage.assign(n, std::vector<double*>(7, nullptr));
+    for (int i = 0; i < n; ++i)
+      for (auto*& x : b->stage[i])
+        if (dalloc(&x, b->ctx[i]->dm.n) != cudaSuccess) return bset_err(b, PAVG_ERR_NOMEM, "timestep buffers");
+  }
+  auto col = [&](int j) {
+    std::vector<double*> v(n);
+    for (int i = 0; i < n; ++i) v[i] = b->stage[i][j];
+    return v;
+  };
+  const std::vector<double*> k1 = col(0), k2 = col(1), k3 = col(2), k4 = col(3), EhU = col(4), tmp = col(5),
+                             tmp2 = col(6);
+  std::vector<double*> u(U, U + n);
+  std::vector<double> half(n), full(dt, dt + n);
+  for (int i = 0; i < n; ++i) half[i] = 0.5 * dt[i];  // E(dt/2) of Sec. 2.3
+  auto cptr = [](const std::vector<double*>& v) { return std::vector<const double*>(v.begin(), v.end()); };
+  auto avg = [&](const std::vector<double*>& in, const std::vector<double*>& out) {
+    return pavg_batch_averaged_rhs(b, T, M, cptr(in).data(), out.data(), stream);
+  };
+  // out_i = ax x_i + by_i y_i (+ cz_i z_i), per instance
+  auto lin = [&](const std::vector<double*>& out, const std::vector<double*>& x, double ax,
+                 const std::vector<double*>& y, const std::vector<double>& by, const std::vector<double*>* z,
+                 const std::vector<double>* cz) -> int {
+    for (int i = 0; i < n; ++i)
+      BCK(launch_lincomb(out[i], ax, x[i], by[i], y[i], z ? (*cz)[i] : 0.0, z ? (*z)[i] : nullptr,
+                         b->ctx[i]->dm.n, st));
+    return PAVG_OK;
+  };
+  std::vector<double> dt2(n), dt3(n), dt6(n), ones(n, 1.0);
+  for (int i = 0; i < n; ++i) { dt2[i] = 0.5 * dt[i]; dt3[i] = dt[i] / 3.0; dt6[i] = dt[i] / 6.0; }
+  int rc = PAVG_OK;
+  for (int step = 0; step < nsteps; ++step) {
+    // Lawson RK4 (Sec. 2.3), in the form of pavg_timestep
+    if ((rc = avg(u, k1))) return rc;
+    if ((rc = batch_expL(b, half, cptr(u), EhU, st))) return rc;
+    if ((rc = lin(tmp, u, 1.0, k1, dt2, nullptr, nullptr))) return rc;
+    if ((rc = batch_expL(b, half, cptr(tmp), tmp2, st))) return rc;
+    if ((rc = avg(tmp2, k2))) return rc;
+    if ((rc = lin(tmp, EhU, 1.0, k2, dt2, nullptr, nullptr))) return rc;
+    if ((rc = avg(tmp, k3))) return rc;
+    if ((rc = lin(tmp, EhU, 1.0, k3, full, nullptr, nullptr))) return rc;
+    if ((rc = batch_expL(b, half, cptr(tmp), tmp2, st))) return rc;
+    if ((rc = avg(tmp2, k4))) return rc;
+    // U+ = E(dt)(U + dt/6 k1) + dt/6 [2 E(dt/2)(k2 + k3) + k4]
+    if ((rc = lin(tmp, k2, 1.0, k3, ones, nullptr, nullptr))) return rc;
+    if ((rc = batch_expL(b, half, cptr(tmp), tmp2, st))) return rc;
+    if ((rc = lin(tmp, u, 1.0, k1, dt6, nullptr, nullptr))) return rc;
+    if ((rc = batch_expL(b, full, cptr(tmp), EhU, st))) return rc;
+    if ((rc = lin(u, EhU, 1.0, tmp2, dt3, &k4, &dt6))) return rc;
+  }
   return PAVG_OK;
 }
 

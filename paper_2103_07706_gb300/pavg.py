@@ -36,7 +36,7 @@ EXPORTED = [
     "pavg_reset_stats", "pavg_last_error", "pavg_kernel_timing", "pavg_kernel_time", "pavg_linear_noalloc",
     "pavg_batch_create", "pavg_batch_destroy", "pavg_batch_averaged_rhs", "pavg_batch_autotune",
     "pavg_batch_set_config", "pavg_batch_get_config", "pavg_batch_kernel_time", "pavg_batch_sync",
-    "pavg_batch_last_error",
+    "pavg_batch_last_error", "pavg_batch_timestep",
     "pavg_surrogate_create", "pavg_surrogate_destroy", "pavg_surrogate_nparams", "pavg_surrogate_get_params",
     "pavg_surrogate_set_params", "pavg_surrogate_get_scaling", "pavg_surrogate_set_scaling",
     "pavg_surrogate_add_pairs", "pavg_surrogate_rows", "pavg_surrogate_fit_scaling", "pavg_surrogate_train",
@@ -128,6 +128,7 @@ def load(path=LIB_PATH):
         "pavg_batch_kernel_time": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "pavg_batch_sync": (I, [P, V]),
         "pavg_batch_last_error": (ctypes.c_char_p, [P]),
+        "pavg_batch_timestep": (I, [P, P, P, P, P, I, V]),
         "pavg_surrogate_create": (I, [I, ctypes.c_uint64, ctypes.POINTER(P)]),
         "pavg_surrogate_destroy": (I, [P]),
         "pavg_surrogate_nparams": (I, [P, ctypes.POINTER(I64)]),
@@ -358,6 +359,13 @@ class Batch:
         Oa = (ctypes.c_void_p * len(out))(*[_ptr(o, m.n).value for o, m in zip(out, self.models)])
         self._check(self._lib.pavg_batch_averaged_rhs(self._h, Ta, Ma, Ua, Oa, _stream()))
         return out
+
+    def timestep(self, dt, T, M, U, nsteps=1):
+        """nsteps averaged Lawson RK4 steps of every instance, in place on U."""
+        Ta, Ma, Ua = self._arrays(T, M, U)
+        Da = (ctypes.c_double * len(U))(*[float(x) for x in dt])
+        self._check(self._lib.pavg_batch_timestep(self._h, Da, Ta, Ma, Ua, int(nsteps), _stream()))
+        return U
 
     def autotune(self, T, M, U):
         Ta, Ma, Ua = self._arrays(T, M, U)

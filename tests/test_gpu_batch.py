@@ -186,3 +186,24 @@ def test_contexts_share_the_mesh_but_not_topography():
                           pavg.Model(2, lambda_max=LAM[2]).averaged_rhs(1800.0, 4, U).cpu().numpy())
     torch.cuda.synchronize()
     a.close()
+
+
+def test_batch_timestep_matches_single_instance_and_oracle():
+    """Two averaged Lawson RK4 steps of instances with their own dt, T, M."""
+    from paper_2103_07706_gb300 import pavg
+    spec = [(2, 900.0, 3600.0, 8), (3, 900.0, 3600.0, 8), (3, 600.0, 1800.0, 5), (2, 1200.0, 0.0, 1)]
+    ms = [pavg.Model(r, lambda_max=LAM[r]) for r, _, _, _ in spec]
+    U0 = [state(orc(r), seed=70 + i) for i, (r, _, _, _) in enumerate(spec)]
+    Ub = [dev(u) for u in U0]
+    b = pavg.Batch(ms)
+    b.timestep([d for _, d, _, _ in spec], [t for _, _, t, _ in spec], [m for _, _, _, m in spec], Ub, 2)
+    b.sync()
+    for i, (r, d, t, m) in enumerate(spec):
+        Us = dev(U0[i])
+        ms[i].timestep(d, t, m, Us, 2)
+        assert_close(orc(r), Ub[i].cpu().numpy(), Us.cpu().numpy())
+    o = orc(3)
+    assert_close(o, Ub[1].cpu().numpy(), o.timestep(900.0, 3600.0, 8, U0[1], 2))
+    b.close()
+    for m_ in ms:
+        m_.close()
