@@ -105,8 +105,8 @@ def _mixed_mode(pavg, cfg, Ud, ref, args, stream):
 
 
 # ----------------------------------------------------------------------------- batched instances
-SURROGATE = {"train_refinement": 5, "test_refinement": 6, "T_s": 4 * 3600.0, "Mc": 8, "Mf": 128, "pairs": 24,
-             "hidden": 128, "epochs": 30, "batch": 8192, "lr": 2e-3, "tests": 2}
+SURROGATE = {"train_refinement": 5, "tests": {6: 2, 7: 1}, "T_s": 4 * 3600.0, "Mc": 8, "Mf": 128, "pairs": 24,
+             "hidden": 128, "epochs": 30, "batch": 8192, "lr": 2e-3}
 
 
 def _state_job(job):
@@ -133,7 +133,7 @@ def _batch_jobs():
 def _surrogate_jobs():
     S = SURROGATE
     return ([(S["train_refinement"], 5000 + i) for i in range(S["pairs"])] +
-            [(S["test_refinement"], 6000 + i) for i in range(S["tests"])])
+            [(r, 6000 + 100 * r + i) for r, k in S["tests"].items() for i in range(k)])
 
 
 def _batch_leg(pavg, states):
@@ -221,39 +221,45 @@ def _surrogate_leg(pavg, states):
     rows = sur.rows()
     del U, Vc, Vf
     mt.close()
-    m6 = pavg.Model(S["test_refinement"], lambda_max=lambda_max_for(S["test_refinement"]))
     zero = pavg.Surrogate(hidden=8)
     zero.set_params(np.zeros(zero.nparams, dtype=np.float32))
-    tests = [torch.from_numpy(x).cuda() for x in states[S["pairs"]:]]
-    e_cheap, e_sur, e_bf = [], [], []
-    for u in tests:
-        e_cheap.append(zero.averaged_rhs(m6, T, Mc, Mf, u, threshold=1.0)[2])
-        e_sur.append(sur.averaged_rhs(m6, T, Mc, Mf, u, threshold=1.0)[2])
-        e_bf.append(sur.averaged_rhs(m6, T, Mc, Mf, u, threshold=1.0, bf16=True)[2])
-    out = torch.empty_like(tests[0])
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    sur.averaged_rhs(m6, T, Mc, Mf, tests[0], out, check=False)
-    m6.averaged_rhs(T, Mf, tests[0], out)
-    torch.cuda.synchronize()
-    ev[0].record()
-    sur.averaged_rhs(m6, T, Mc, Mf, tests[0], out, check=False)
-    ev[1].record()
-    m6.averaged_rhs(T, Mf, tests[0], out)
-    ev[2].record()
-    torch.cuda.synchronize()
-    t_sur, t_full = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
     res = {"workload": f"train r{S['train_refinement']} ({S['pairs']} pairs, {rows} cell rows), T = 4 h, "
-                       f"M = {Mc} corrected towards M = {Mf}; applied at r{S['test_refinement']} on "
-                       f"{len(tests)} unseen states",
+                       f"M = {Mc} corrected towards M = {Mf}; applied on unseen states at refinements "
+                       + ", ".join(f"{r} ({k})" for r, k in S["tests"].items()),
            "pair_generation_s": gen_s, "train_s": train_s, "loss_first_epoch": loss[0], "loss_last_epoch": loss[-1],
-           "rel_err_energy_cheap_M8": float(np.mean(e_cheap)), "rel_err_energy_surrogate": float(np.mean(e_sur)),
-           "rel_err_energy_surrogate_bf16": float(np.mean(e_bf)),
-           "gain": float(np.mean(e_cheap) / np.mean(e_sur)),
-           "surrogate_ms": t_sur, "full_M128_ms": t_full, "speedup_vs_full": t_full / t_sur,
-           "fallback_threshold": 1e-3, "would_fall_back": bool(np.mean(e_sur) > 1e-3)}
+           "fallback_threshold": 1e-3}
+    k0 = S["pairs"]
+    for r, k in S["tests"].items():
+        mr = pavg.Model(r, lambda_max=lambda_max_for(r))
+        tests = [torch.from_numpy(x).cuda() for x in states[k0:k0 + k]]
+        k0 += k
+        e_cheap, e_sur, e_bf = [], [], []
+        for u in tests:
+            e_cheap.append(zero.averaged_rhs(mr, T, Mc, Mf, u, threshold=1.0)[2])
+            e_sur.append(sur.averaged_rhs(mr, T, Mc, Mf, u, threshold=1.0)[2])
+            e_bf.append(sur.averaged_rhs(mr, T, Mc, Mf, u, threshold=1.0, bf16=True)[2])
+        out = torch.empty_like(tests[0])
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        sur.averaged_rhs(mr, T, Mc, Mf, tests[0], out, check=False)
+        mr.averaged_rhs(T, Mf, tests[0], out)
+        torch.cuda.synchronize()
+        ev[0].record()
+        sur.averaged_rhs(mr, T, Mc, Mf, tests[0], out, check=False)
+        ev[1].record()
+        mr.averaged_rhs(T, Mf, tests[0], out)
+        ev[2].record()
+        torch.cuda.synchronize()
+        t_sur, t_full = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        res[f"r{r}"] = {"cells": mr.n_cells, "rel_err_energy_cheap_M8": float(np.mean(e_cheap)),
+                        "rel_err_energy_surrogate": float(np.mean(e_sur)),
+                        "rel_err_energy_surrogate_bf16": float(np.mean(e_bf)),
+                        "gain": float(np.mean(e_cheap) / np.mean(e_sur)),
+                        "surrogate_ms": t_sur, "full_M128_ms": t_full, "speedup_vs_full": t_full / t_sur,
+                        "would_fall_back": bool(np.mean(e_sur) > 1e-3)}
+        del tests, out
+        mr.close()
     sur.close()
     zero.close()
-    m6.close()
     return res
 
 

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -522,6 +523,8 @@ int pavg_create(const pavg_params* p, pavg_ctx** out) {
   *out = nullptr;
   if (!valid_params(p)) return PAVG_ERR_INVAL;
   pavg_ctx* ctx = new pavg_ctx();
+  static std::atomic<uint64_t> next_uid{1};
+  ctx->uid = next_uid++;
   ctx->p = *p;
   ctx->cgp.rtol = p->cg_rtol;
   ctx->cgp.maxit = p->cg_maxit;

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <map>
 #include <string>
 #include <tuple>
@@ -42,6 +43,7 @@ struct SharedMesh {
 }  // namespace pavg_detail
 
 struct pavg_ctx {
+  uint64_t uid = 0;  // unique per context in this process (a freed context's address can be reused)
   using AvgPlan = pavg_detail::AvgPlan;
   using EventPair = pavg_detail::EventPair;
   pavg_params p{};

@@ -31,6 +31,7 @@ constexpr int kMseBlocks = 64;
 
 // Device scratch for one context the surrogate runs on.
 struct CtxData {
+  uint64_t uid = 0;        // the context these buffers were made for
   float* geo = nullptr;    // [F][4]
   float* X = nullptr;      // [F][124]
   float* H1 = nullptr;     // [F][hidden]
@@ -120,8 +121,13 @@ std::vector<float> cell_geometry(const pavg_ctx* ctx) {
 
 int ctx_data(pavg_surrogate* s, pavg_ctx* ctx, CtxData** out) {
   auto it = s->ctx.find(ctx);
-  if (it != s->ctx.end()) { *out = &it->second; return PAVG_OK; }
+  if (it != s->ctx.end()) {
+    if (it->second.uid == ctx->uid) { *out = &it->second; return PAVG_OK; }
+    free_ctxdata(it->second);  // a new context at a destroyed one's address
+    s->ctx.erase(it);
+  }
   CtxData d;
+  d.uid = ctx->uid;
   const int64_t F = ctx->dm.F, n = ctx->dm.n;
   bool ok = upload(&d.geo, cell_geometry(ctx)) == cudaSuccess && dalloc(&d.X, (size_t)F * kIn) == cudaSuccess &&
             dalloc(&d.H1, (size_t)F * s->hidden) == cudaSuccess && dalloc(&d.H2, (size_t)F * s->hidden) == cudaSuccess &&

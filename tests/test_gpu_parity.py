@@ -233,3 +233,25 @@ def test_full_size_properties():
     assert g.stats()["error_flags"] == 0
     del torch
     g.close()
+
+
+def test_refinement7_streamed_solver_matches_fp64_solver():
+    """Refinement 7 (327680 cells) does not fit the shared-memory-resident
+    path, so the mixed solver streams its FP32 element matrices; its L U must
+    agree with the independent FP64 Jacobi CG to the solve tolerance."""
+    from paper_2103_07706_gb300 import pavg
+    from paper_2103_07706_gb300.inputs import lambda_max_for
+    a = pavg.Model(7, lambda_max=lambda_max_for(7))
+    b = pavg.Model(7, lambda_max=lambda_max_for(7), solver=pavg.PAVG_SOLVER_FP64)
+    U = np.random.default_rng(77).standard_normal(a.n) * 1e6
+    U[a.n_u:] *= 1e-4
+    Ud = dev(U)
+    x = a.linear(Ud).cpu().numpy()
+    y = b.linear(Ud).cpu().numpy()
+    a.sync()
+    b.sync()
+    nu = a.n_u
+    assert np.linalg.norm(x[:nu] - y[:nu]) <= 1e-12 * np.linalg.norm(y[:nu])
+    assert np.array_equal(x[nu:], y[nu:])  # the elevation part has no M1 solve
+    a.close()
+    b.close()

@@ -178,3 +178,47 @@ def test_surrogate_argument_errors():
         sur.set_scaling(np.zeros(124), np.zeros(124), np.zeros(15), np.ones(15))
     sur.close()
     del torch
+
+
+def test_features_and_apply_at_refinement6():
+    """The benchmark's inference size: GPU features of every cell and the
+    applied correction on every DOF against the oracle at refinement 6."""
+    from oracle.assembly import Assembly
+    from oracle.mesh import build_mesh
+    from paper_2103_07706_gb300 import pavg
+    from paper_2103_07706_gb300.inputs import harmonic_state, lambda_max_for
+    m = pavg.Model(6, lambda_max=lambda_max_for(6))
+    mesh = build_mesh(6, 6.37122e6)
+    asm = Assembly(mesh, 7.292e-5, 6.37122e6)
+    U, _ = harmonic_state(mesh.verts, mesh.cells, 11, 16)
+    V, _ = harmonic_state(mesh.verts, mesh.cells, 12, 16)
+    sur = pavg.Surrogate(hidden=32, seed=6)
+    X = sur.features(m, dev(U), dev(V)).cpu().numpy()
+    want = S.features(asm, U, V)
+    assert np.allclose(X, want, rtol=1e-6, atol=1e-6 * np.abs(want).max(axis=0))
+    rng = np.random.default_rng(6)
+    mx, sx = want.mean(axis=0).astype(np.float32), (want.std(axis=0) + 1e-3).astype(np.float32)
+    my, sy = rng.standard_normal(S.N_OUT).astype(np.float32), (0.5 + rng.random(S.N_OUT)).astype(np.float32)
+    sur.set_scaling(mx, sx, my, sy)
+    p = _blocks(sur.params(), 32)
+    got = sur.apply(m, dev(U), dev(V)).cpu().numpy() - V
+    corr = S.apply(asm, p, tuple(a.astype(np.float64) for a in (mx, sx, my, sy)), U, V) - V
+    assert np.abs(got - corr).max() <= 1e-5 * np.abs(corr).max()
+    sur.close()
+    m.close()
+
+
+def test_scratch_follows_the_context_not_its_address():
+    """A context created after another was destroyed may reuse its address;
+    the surrogate's per-context scratch must follow the new context's mesh."""
+    from paper_2103_07706_gb300 import pavg
+    sur = pavg.Surrogate(hidden=8)
+    o2, o3 = orc(2), orc(3)
+    for r, o in ((2, o2), (3, o3), (2, o2)):
+        m = pavg.Model(r, lambda_max=LAM[r])
+        U = state(o, seed=5)
+        X = sur.features(m, dev(U), dev(U)).cpu().numpy()
+        assert X.shape == (m.n_cells, S.N_IN)
+        assert np.allclose(X, S.features(o.ops.asm, U, U), rtol=1e-6, atol=1e-6)
+        m.close()
+    sur.close()
