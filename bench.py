@@ -120,14 +120,23 @@ def _state_job(job):
 
 def _make_states(jobs):
     """States of the batched and surrogate legs, built on the host cores in a
-    spawned pool before the first CUDA call."""
+    spawned pool before the first CUDA call (in this process when few)."""
+    if len(jobs) <= 8:
+        return [_state_job(j) for j in jobs]
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
         return pool.map(_state_job, jobs)
 
 
-def _batch_jobs():
+BATCH = {"n": 64, "max_refinement": 6}  # the workload; smaller only for profiling
+
+
+def _batch_work():
     from paper_2103_07706_gb300.inputs import batch_workload
-    return [(w["refinement"], w["state_seed"]) for w in batch_workload()]
+    return [w for w in batch_workload() if w["refinement"] <= BATCH["max_refinement"]][:BATCH["n"]]
+
+
+def _batch_jobs():
+    return [(w["refinement"], w["state_seed"]) for w in _batch_work()]
 
 
 def _surrogate_jobs():
@@ -141,8 +150,8 @@ def _batch_leg(pavg, states):
     {16, 32, 64, 128}): one batched evaluation (persistent recurrences,
     autotuned grid) against the same instances one after another."""
     import torch
-    from paper_2103_07706_gb300.inputs import batch_workload, lambda_max_for
-    work = batch_workload()
+    from paper_2103_07706_gb300.inputs import lambda_max_for
+    work = _batch_work()
     ms = [pavg.Model(w["refinement"], lambda_max=lambda_max_for(w["refinement"])) for w in work]
     U = [torch.from_numpy(x).cuda() for x in states]
     T = [w["T"] for w in work]
@@ -181,7 +190,8 @@ def _batch_leg(pavg, states):
     t_seq = e0.elapsed_time(e1)
     diff = max(float(((o - q).norm() / q.norm()).item()) for o, q in zip(out, seq))
     chain_s = (fwd + bwd) / 1e3
-    res = {"workload": "64 instances, refinements 4-6, T ~ U[0.25, 4] h, M in {16, 32, 64, 128}, harmonic l<=16",
+    res = {"workload": f"{len(ms)} instances, refinements 4-{BATCH['max_refinement']}, T ~ U[0.25, 4] h, "
+                       "M in {16, 32, 64, 128}, harmonic l<=16",
            "value": len(ms) / (t_batch / 1e3), "unit": "instance-evals/s", "ms_per_batch": t_batch,
            "sequential_ms": t_seq, "speedup_vs_sequential": t_seq / t_batch,
            "max_rel_l2_vs_single_instance": diff, "first_call_s": first_s, "config": b.config(),
@@ -579,6 +589,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pavg", choices=["pavg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-n", type=int, default=None, help="instances of the batched leg (profiling only)")
+    ap.add_argument("--batch-max-r", type=int, default=None, help="largest refinement of the batched leg (profiling only)")
     ap.add_argument("--legs", default="fp64,mixed,batch,surrogate",
                     help="comma list: fp64 (always), mixed, batch, surrogate (single GPU only)")
     ap.add_argument("--refinement", type=int, default=None, help="smaller case (profiling only)")
@@ -590,6 +602,9 @@ def main():
                        "lambda_max": LAMBDA_R6 / 2 ** (6 - r)})
         args.no_cpu_baseline = True
         args.legs = "fp64"
+    if args.batch_n is not None or args.batch_max_r is not None:
+        BATCH.update({"n": args.batch_n or BATCH["n"], "max_refinement": args.batch_max_r or BATCH["max_refinement"]})
+        args.no_cpu_baseline = True
     if args.impl == "reference":
         return run_reference(args)
     return run_pavg(args)
