@@ -58,6 +58,7 @@ struct pavg_ctx {
   int device = 0;
   // scratch
   double* ru = nullptr;         // [n_u] assembled velocity rhs
+  double* facets = nullptr;     // [kFacetChunk][F][3][15] facet terms of N per (cell, local edge)
   double* vec[6] = {};          // [n] general vectors
   double* io_in = nullptr;      // [n] graph input
   double* io_out = nullptr;     // [n] graph output

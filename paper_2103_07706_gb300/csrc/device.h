@@ -184,10 +184,13 @@ cudaError_t launch_apply_K(const DeviceMesh& m, const double* U, double s, doubl
                            double* ru, double* eta_out, cudaStream_t st);
 
 // Weak-form right-hand side of N for B states [B][n] -> r [B][n]
-// (r's velocity edge DOFs must be zeroed first).
+// (r's velocity edge DOFs must be zeroed first), in chunks of `chunk` states:
+// per chunk one launch over the edges (facet terms of both cells, into
+// `facets`, chunk x F x 3 x 15 doubles of scratch) and one over the cells.
 // fp32: FP32 arithmetic per quadrature point, FP64 sums over the points.
+constexpr int kFacetChunk = 16;
 cudaError_t launch_nonlinear_rhs(const DeviceMesh& m, const double* U, double* r, int B,
-                                 int upwind, cudaStream_t st, bool fp32 = false);
+                                 int upwind, cudaStream_t st, bool fp32, double* facets, int chunk);
 
 // eta_out = M2^{-1} r_eta (+ add) for B blocks of n_eta with strides.
 cudaError_t launch_m2inv(const DeviceMesh& m, const double* r, int64_t rstride, double* out,

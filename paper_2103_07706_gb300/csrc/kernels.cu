@@ -382,6 +382,57 @@ __device__ __forceinline__ FacetValues<R> facet_point(const Side<R>& P, int lp, 
   return f;
 }
 
+// Facet terms of N (Sec. 2.5) for one edge and one state, for both of its
+// cells at once: at each of the edge's quadrature points the upwinded values
+// are formed once (facet_point), and each side's contributions
+//   r_j  -= / += w (u_perp . w_j) (t . u~)      (velocity tests of that side)
+//   re_k -/+ w phi_k (u . n+) (eta - b)~         (elevation tests; FP32: strong form)
+// are summed over the points in FP64 and stored in the side's slot
+// FR[cell][local edge][15] (each slot written by exactly one edge).
+template <typename R>
+__global__ void __launch_bounds__(128) k_facets(DeviceMesh m, const double* __restrict__ Uall, double* FRall,
+                                                int upwind) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m.E) return;
+  const TablesT<R>& T = tab<R>();
+  constexpr bool kStrongDG = sizeof(R) == 4;
+  const double* U = Uall + (int64_t)blockIdx.y * m.n;
+  double* FR = FRall + (int64_t)blockIdx.y * m.F * 45;
+  const int64_t cp = m.edge_plus[e], cm = m.edge_minus[e];
+  const unsigned lpos = m.edge_lpos[e];
+  const int lp = (int)(lpos & 3u), lm = (int)(lpos >> 2);
+  Side<R> P, Mn;
+  load_side(m, U, cp, P);
+  load_side(m, U, cm, Mn);
+  double rp[12], rm[12], ep[3] = {0.0, 0.0, 0.0}, em[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int j = 0; j < 12; ++j) rp[j] = rm[j] = 0.0;
+#pragma unroll 1
+  for (int p = 0; p < kFacetQ; ++p) {
+    const R wp = T.fq_w[p];
+    const FacetValues<R> f = facet_point(P, lp, Mn, lm, p, upwind);
+    const R scp = -wp * f.tan / P.det, scm = wp * f.tan / Mn.det;
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+      rp[j] += (double)(scp * (f.up0 * T.fq_psi[0][lp][p][j][1] - f.up1 * T.fq_psi[0][lp][p][j][0]));
+      rm[j] += (double)(scm * (f.um0 * T.fq_psi[1][lm][p][j][1] - f.um1 * T.fq_psi[1][lm][p][j][0]));
+    }
+    const R fhp = kStrongDG ? wp * f.flux * (f.hp - f.hup) : -wp * f.flux * f.hup;
+    const R fhm = kStrongDG ? wp * f.flux * (f.hup - f.hm) : wp * f.flux * f.hup;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      ep[k] += (double)(fhp * T.fq_phi[0][lp][p][k]);
+      em[k] += (double)(fhm * T.fq_phi[1][lm][p][k]);
+    }
+  }
+  double* sp = FR + (cp * 3 + lp) * 15;
+  double* sm = FR + (cm * 3 + lm) * 15;
+#pragma unroll
+  for (int j = 0; j < 12; ++j) { sp[j] = rp[j]; sm[j] = rm[j]; }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) { sp[12 + k] = ep[k]; sm[12 + k] = em[k]; }
+}
+
 // Weak-form right-hand side of N (Sec. 2.5) for one cell and one state:
 //   r_i  = int_K [u . grad_perp(u_perp . w_i) + div w_i |u|^2/2]
 //          - int_dK (+/-) (u_perp . w_i) (t . u~)          (velocity test w_i)
@@ -398,7 +449,7 @@ __device__ __forceinline__ FacetValues<R> facet_point(const Side<R>& P, int lp, 
 // like 1 / h while their sum does not).
 template <typename R>
 __global__ void __launch_bounds__(128) k_nonlinear(DeviceMesh m, const double* __restrict__ Uall, double* Rall,
-                                                   int upwind) {
+                                                   const double* __restrict__ FRall) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= m.F) return;
   const TablesT<R>& T = tab<R>();
@@ -463,44 +514,14 @@ __global__ void __launch_bounds__(128) k_nonlinear(DeviceMesh m, const double* _
   const double idet2 = 1.0 / ((double)own.det * (double)own.det);
 #pragma unroll
   for (int i = 0; i < 12; ++i) r[i] *= idet2;
-  // ---- facet terms
-  const unsigned al = m.cell_aligned[c];
-#pragma unroll 1
+  // ---- facet terms, evaluated once per edge by k_facets (slots [c][local edge][15])
+  const double* FR = FRall + ((int64_t)blockIdx.y * m.F + c) * 45;
+#pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const int e = m.cell_edges[i * m.F + c];
-    const bool plus = (al >> i) & 1u;
-    const unsigned lpos = m.edge_lpos[e];
-    const int64_t nbr = plus ? m.edge_minus[e] : m.edge_plus[e];
-    const int nloc = plus ? (int)(lpos >> 2) : (int)(lpos & 3u);
-    Side<R> nb;
-    load_side(m, U, nbr, nb);
-#pragma unroll 1
-    for (int p = 0; p < kFacetQ; ++p) {
-      const R wp = T.fq_w[p];
-      if (plus) {
-        FacetValues<R> f = facet_point(own, i, nb, nloc, p, upwind);
-        const R sc = -wp * f.tan / own.det;
 #pragma unroll
-        for (int j = 0; j < 12; ++j) {
-          R qv = f.up0 * T.fq_psi[0][i][p][j][1] - f.up1 * T.fq_psi[0][i][p][j][0];
-          r[j] += (double)(sc * qv);
-        }
-        const R fh = kStrongDG ? wp * f.flux * (f.hp - f.hup) : -wp * f.flux * f.hup;
+    for (int j = 0; j < 12; ++j) r[j] += __ldcg(&FR[15 * i + j]);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) re[k] += (double)(fh * T.fq_phi[0][i][p][k]);
-      } else {
-        FacetValues<R> f = facet_point(nb, nloc, own, i, p, upwind);
-        const R sc = wp * f.tan / own.det;
-#pragma unroll
-        for (int j = 0; j < 12; ++j) {
-          R qv = f.um0 * T.fq_psi[1][i][p][j][1] - f.um1 * T.fq_psi[1][i][p][j][0];
-          r[j] += (double)(sc * qv);
-        }
-        const R fh = kStrongDG ? wp * f.flux * (f.hup - f.hm) : wp * f.flux * f.hup;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) re[k] += (double)(fh * T.fq_phi[1][i][p][k]);
-      }
-    }
+    for (int k = 0; k < 3; ++k) re[k] += __ldcg(&FR[15 * i + 12 + k]);
   }
   // ---- to global numbering
   int dof[12];
@@ -666,11 +687,24 @@ cudaError_t launch_apply_K(const DeviceMesh& m, const double* U, double s, doubl
 }
 
 cudaError_t launch_nonlinear_rhs(const DeviceMesh& m, const double* U, double* r, int B, int upwind,
-                                 cudaStream_t st, bool fp32) {
-  dim3 grid((unsigned)((m.F + 127) / 128), (unsigned)B);
-  if (fp32) k_nonlinear<float><<<grid, 128, 0, st>>>(m, U, r, upwind);
-  else k_nonlinear<double><<<grid, 128, 0, st>>>(m, U, r, upwind);
-  return cudaGetLastError();
+                                 cudaStream_t st, bool fp32, double* facets, int chunk) {
+  if (!facets || chunk < 1) return cudaErrorInvalidValue;
+  for (int b0 = 0; b0 < B; b0 += chunk) {
+    const int nb = B - b0 < chunk ? B - b0 : chunk;
+    const double* Ub = U + (int64_t)b0 * m.n;
+    double* rb = r + (int64_t)b0 * m.n;
+    dim3 ge((unsigned)((m.E + 127) / 128), (unsigned)nb), gc((unsigned)((m.F + 127) / 128), (unsigned)nb);
+    if (fp32) {
+      k_facets<float><<<ge, 128, 0, st>>>(m, Ub, facets, upwind);
+      k_nonlinear<float><<<gc, 128, 0, st>>>(m, Ub, rb, facets);
+    } else {
+      k_facets<double><<<ge, 128, 0, st>>>(m, Ub, facets, upwind);
+      k_nonlinear<double><<<gc, 128, 0, st>>>(m, Ub, rb, facets);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_m2inv(const DeviceMesh& m, const double* r, int64_t rstride, double* out,
