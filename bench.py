@@ -104,6 +104,35 @@ def _mixed_mode(pavg, cfg, Ud, ref, args, stream):
     return res
 
 
+def _precision_days(pavg, cfg, U, days):
+    """The precision configuration over simulated days: averaged Lawson RK4
+    steps of dt = 900 s (T = 1 h, M = 64) at refinement 6 from the same state
+    in FP64 and in the mixed-precision mode; relative L2 error of the mixed
+    state per field after every step."""
+    import torch
+    mk = lambda prec: pavg.Model(cfg["refinement"], lambda_max=cfg["lambda_max"], g=cfg["g"], H=cfg["H"],
+                                 omega=cfg["Omega"], radius=cfg["R"], cheb_tol=cfg["cheb_tol"],
+                                 cg_rtol=cfg["cg_rtol"], precision=prec)
+    a, b = mk(pavg.PAVG_PRECISION_FP64), mk(pavg.PAVG_PRECISION_MIXED)
+    Ua, Ub = torch.from_numpy(U).cuda(), torch.from_numpy(U).cuda()
+    nu, steps, dt = a.n_u, int(round(days * 96)), 900.0
+    err_u, err_eta = [], []
+    t0 = time.time()
+    for _ in range(steps):
+        a.timestep(dt, cfg["T_s"], cfg["M"], Ua, 1)
+        b.timestep(dt, cfg["T_s"], cfg["M"], Ub, 1)
+        err_u.append(float(((Ub[:nu] - Ua[:nu]).norm() / Ua[:nu].norm()).item()))
+        err_eta.append(float(((Ub[nu:] - Ua[nu:]).norm() / Ua[nu:].norm()).item()))
+    a.sync()
+    b.sync()
+    res = {"workload": f"refinement 6, dt 900 s, T 1 h, M 64, {steps} steps ({days} days)",
+           "wall_s": time.time() - t0, "rel_l2_u_per_step": err_u, "rel_l2_eta_per_step": err_eta,
+           "final_rel_l2_u": err_u[-1] if err_u else None, "final_rel_l2_eta": err_eta[-1] if err_eta else None}
+    a.close()
+    b.close()
+    return res
+
+
 # ----------------------------------------------------------------------------- batched instances
 SURROGATE = {"train_refinement": 5, "tests": {6: 2, 7: 1}, "T_s": 4 * 3600.0, "Mc": 8, "Mf": 128, "pairs": 24,
              "hidden": 128, "epochs": 30, "batch": 8192, "lr": 2e-3}
@@ -516,6 +545,7 @@ def run_pavg(args):
     # mixed-precision mode on the same state: throughput and error against the FP64 result above
     mixed = _mixed_mode(pavg, cfg, Ud, out, args, stream) if "mixed" in legs else None
     batch = _batch_leg(pavg, batch_states) if "batch" in legs else None
+    days = _precision_days(pavg, cfg, U, args.days) if "precision_days" in legs else None
     surrogate = _surrogate_leg(pavg, sur_states) if "surrogate" in legs else None
 
     # parity of the small configuration against the oracle (computed by the spawned leg)
@@ -571,7 +601,7 @@ def run_pavg(args):
             "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": 8 * model.n,
                     "d2h_bytes_per_step": 8 * model.n},
             "gpu_launches": st["kernel_launches"] * args.steps,
-            "roofline": roof, "cpu_baseline": cpu, "parity": parity, "precision_mixed": mixed, "batch": batch, "surrogate": surrogate,
+            "roofline": roof, "cpu_baseline": cpu, "parity": parity, "precision_mixed": mixed, "precision_days": days, "batch": batch, "surrogate": surrogate,
             "clocks": clk,
             "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
             "error_flags": st["error_flags"]}
@@ -592,7 +622,8 @@ def main():
     ap.add_argument("--batch-n", type=int, default=None, help="instances of the batched leg (profiling only)")
     ap.add_argument("--batch-max-r", type=int, default=None, help="largest refinement of the batched leg (profiling only)")
     ap.add_argument("--legs", default="fp64,mixed,batch,surrogate",
-                    help="comma list: fp64 (always), mixed, batch, surrogate (single GPU only)")
+                    help="comma list: fp64 (always), mixed, batch, surrogate, precision_days (single GPU only)")
+    ap.add_argument("--days", type=float, default=1.0, help="simulated days of the precision_days leg")
     ap.add_argument("--refinement", type=int, default=None, help="smaller case (profiling only)")
     ap.add_argument("--M", type=int, default=None, help="number of shifts (profiling only)")
     args = ap.parse_args()
