@@ -129,7 +129,7 @@ int enq_nonlinear(pavg_ctx* ctx, const double* U, double* out, double* scratch, 
   const DeviceMesh& m = ctx->dm;
   CK(cudaMemsetAsync(scratch, 0, sizeof(double) * 3 * m.E, st));
   KL(launch_nonlinear_rhs(m, U, scratch, 1, ctx->p.upwind_convention, st,
-                          ctx->p.precision == PAVG_PRECISION_MIXED, ctx->facets, kFacetChunk));
+                          ctx->p.precision == PAVG_PRECISION_MIXED, ctx->facets, ctx->facet_chunk));
   return enq_mass_solve(ctx, scratch, out, st);
 }
 
@@ -247,7 +247,7 @@ int enq_avg_shifts(pavg_ctx* ctx, const AvgPlan& pl, cudaStream_t st) {
   const bool fp32 = ctx->p.precision == PAVG_PRECISION_MIXED;
   KL(launch_combine(pl.dA, M, K + 1, pl.dlimA, Q, n, ctx->Um, n, n, st, fp32));
   CK(cudaMemset2DAsync(ctx->Rm, sizeof(double) * n, 0, sizeof(double) * 3 * m.E, M, st));
-  KL(launch_nonlinear_rhs(m, ctx->Um, ctx->Rm, M, ctx->p.upwind_convention, st, fp32, ctx->facets, kFacetChunk));
+  KL(launch_nonlinear_rhs(m, ctx->Um, ctx->Rm, M, ctx->p.upwind_convention, st, fp32, ctx->facets, ctx->facet_chunk));
   // the weighted sum over shifts stays FP64 in every precision: the average
   // cancels most of the oscillating terms, so rounding here is amplified
   KL(launch_combine(pl.dB, K + 1, M, pl.dlimB, ctx->Rm, n, Q, n, n, st));  // y_k overwrite Q_k
@@ -548,6 +548,9 @@ int pavg_create(const pavg_params* p, pavg_ctx** out) {
     bool ok = dalloc(&m.topo, m.n_eta) == cudaSuccess;
     if (!ok) { rc = set_err(ctx, PAVG_ERR_NOMEM, "device upload failed"); throw 0; }
     cudaMemset(m.topo, 0, sizeof(double) * m.n_eta);
+    // facet scratch of N: up to kFacetChunk states per launch, at most ~512 MB
+    ctx->facet_chunk = (int)std::max<int64_t>(
+        1, std::min<int64_t>(kFacetChunk, ((int64_t)512 << 20) / ((int64_t)45 * sizeof(double) * m.F)));
     CgWork& w = ctx->cg;
     if (cg_configure(m.F, &w) != cudaSuccess) { rc = set_err(ctx, PAVG_ERR_CUDA, "CG configuration failed"); throw 0; }
     ok = dalloc(&w.x, m.n_u) == cudaSuccess && dalloc(&w.r[0], m.n_u) == cudaSuccess &&
@@ -557,7 +560,7 @@ int pavg_create(const pavg_params* p, pavg_ctx** out) {
          dalloc(&w.p, m.n_u) == cudaSuccess && dalloc(&w.partial, 6 * (size_t)w.nblocks) == cudaSuccess &&
          dalloc(&w.bar, 2) == cudaSuccess && dalloc(&w.flags, 1) == cudaSuccess && dalloc(&w.stats, 4) == cudaSuccess &&
          dalloc(&ctx->ru, m.n_u) == cudaSuccess && dalloc(&ctx->io_in, m.n) == cudaSuccess &&
-         dalloc(&ctx->facets, (size_t)kFacetChunk * 45 * m.F) == cudaSuccess &&
+         dalloc(&ctx->facets, (size_t)ctx->facet_chunk * 45 * m.F) == cudaSuccess &&
          dalloc(&ctx->io_out, m.n) == cudaSuccess && dalloc(&ctx->dpart, 4096) == cudaSuccess &&
          cudaMallocHost((void**)&ctx->host_part, sizeof(double) * 4096) == cudaSuccess;
     for (auto*& v : ctx->vec) ok = ok && dalloc(&v, m.n) == cudaSuccess;

@@ -58,7 +58,8 @@ struct pavg_ctx {
   int device = 0;
   // scratch
   double* ru = nullptr;         // [n_u] assembled velocity rhs
-  double* facets = nullptr;     // [kFacetChunk][F][3][15] facet terms of N per (cell, local edge)
+  double* facets = nullptr;     // [facet_chunk][F][3][15] facet terms of N per (cell, local edge)
+  int facet_chunk = 1;          // states per N launch pair: kFacetChunk, fewer on large meshes
   double* vec[6] = {};          // [n] general vectors
   double* io_in = nullptr;      // [n] graph input
   double* io_out = nullptr;     // [n] graph output

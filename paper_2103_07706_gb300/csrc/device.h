@@ -187,6 +187,7 @@ cudaError_t launch_apply_K(const DeviceMesh& m, const double* U, double s, doubl
 // (r's velocity edge DOFs must be zeroed first), in chunks of `chunk` states:
 // per chunk one launch over the edges (facet terms of both cells, into
 // `facets`, chunk x F x 3 x 15 doubles of scratch) and one over the cells.
+// kFacetChunk is the largest chunk (contexts use fewer on large meshes).
 // fp32: FP32 arithmetic per quadrature point, FP64 sums over the points.
 constexpr int kFacetChunk = 16;
 cudaError_t launch_nonlinear_rhs(const DeviceMesh& m, const double* U, double* r, int B,
