@@ -350,7 +350,8 @@ int estimate_lambda(pavg_ctx* ctx) {
   if (cudaMemcpy(v, h.data(), sizeof(double) * n, cudaMemcpyHostToDevice) != cudaSuccess)
     return set_err(ctx, PAVG_ERR_CUDA, "lambda_max: upload failed");
   double nv = std::sqrt(host_winner(ctx, v, v));
-  launch_lincomb(v, 1.0 / nv, v, 0, nullptr, 0, nullptr, n, 0);
+  if (!(nv > 0) || launch_lincomb(v, 1.0 / nv, v, 0, nullptr, 0, nullptr, n, 0) != cudaSuccess)
+    return set_err(ctx, PAVG_ERR_CUDA, "lambda_max: normalisation failed");
   double est = 0;
   for (int it = 0; it < 400; ++it) {
     int rc = enq_linear(ctx, v, Lv, 0);
@@ -360,7 +361,8 @@ int estimate_lambda(pavg_ctx* ctx) {
     if (rc) return rc;
     double nw = std::sqrt(host_winner(ctx, w, w));
     if (!(nw > 0) || !std::isfinite(rq)) return set_err(ctx, PAVG_ERR_NONFINITE, "lambda_max: iteration failed");
-    launch_lincomb(v, -1.0 / nw, w, 0, nullptr, 0, nullptr, n, 0);
+    if (launch_lincomb(v, -1.0 / nw, w, 0, nullptr, 0, nullptr, n, 0) != cudaSuccess)
+      return set_err(ctx, PAVG_ERR_CUDA, "lambda_max: update failed");
     double nest = std::sqrt(rq);
     if (est > 0 && std::fabs(nest - est) <= 1e-9 * nest) { est = nest; break; }
     est = nest;
@@ -547,7 +549,10 @@ int pavg_create(const pavg_params* p, pavg_ctx** out) {
     DeviceMesh& m = ctx->dm;
     bool ok = dalloc(&m.topo, m.n_eta) == cudaSuccess;
     if (!ok) { rc = set_err(ctx, PAVG_ERR_NOMEM, "device upload failed"); throw 0; }
-    cudaMemset(m.topo, 0, sizeof(double) * m.n_eta);
+    if (cudaMemset(m.topo, 0, sizeof(double) * m.n_eta) != cudaSuccess) {
+      rc = set_err(ctx, PAVG_ERR_CUDA, "topography initialisation failed");
+      throw 0;
+    }
     // facet scratch of N: up to kFacetChunk states per launch, at most ~512 MB
     ctx->facet_chunk = (int)std::max<int64_t>(
         1, std::min<int64_t>(kFacetChunk, ((int64_t)512 << 20) / ((int64_t)45 * sizeof(double) * m.F)));
@@ -585,10 +590,12 @@ int pavg_create(const pavg_params* p, pavg_ctx** out) {
       wi.pf = fb + 8 * s4;
     }
     if (!ok) { rc = set_err(ctx, PAVG_ERR_NOMEM, "workspace allocation failed"); throw 0; }
-    cudaMemset(w.bar, 0, 2 * sizeof(unsigned));
-    cudaMemset(w.flags, 0, sizeof(int));
-    cudaMemset(w.stats, 0, 4 * sizeof(unsigned long long));
-    cudaMemset(ctx->cgi.bar, 0, 2 * sizeof(unsigned));
+    if (cudaMemset(w.bar, 0, 2 * sizeof(unsigned)) != cudaSuccess || cudaMemset(w.flags, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemset(w.stats, 0, 4 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(ctx->cgi.bar, 0, 2 * sizeof(unsigned)) != cudaSuccess) {
+      rc = set_err(ctx, PAVG_ERR_CUDA, "solver state initialisation failed");
+      throw 0;
+    }
     if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
       rc = set_err(ctx, PAVG_ERR_CUDA, "stream creation failed");
       throw 0;
