@@ -22,7 +22,8 @@
  * against (1,0), (0,1), (-y,x) on the reference triangle.  Elevation DOF
  * 3c + i is the value at local vertex i of cell c.  Cells, vertices and edges
  * are numbered by the canonical icosahedral construction exported by
- * pavg_mesh_export.  A batch of B states is laid out [B][n].
+ * pavg_mesh_export.  A batch of B states is laid out [B][n]; B = 0 is a
+ * valid empty batch (no work; its state pointers may then be NULL).
  *
  * Pointers marked "device" are caller-owned CUDA device memory (e.g. a torch
  * tensor's data_ptr()); the library never frees them.  Calls that take a

@@ -660,7 +660,7 @@ int pavg_lambda_max(const pavg_ctx* ctx, double* out) {
 }
 
 int pavg_linear(pavg_ctx* ctx, const double* U, double* LU, int B, void* stream) {
-  if (!ctx || !U || !LU || B < 0) return PAVG_ERR_INVAL;
+  if (!ctx || B < 0 || (B > 0 && (!U || !LU))) return PAVG_ERR_INVAL;
   CallScope scope_(ctx);
   const int64_t n = ctx->dm.n;
   for (int b = 0; b < B; ++b) {
@@ -671,7 +671,7 @@ int pavg_linear(pavg_ctx* ctx, const double* U, double* LU, int B, void* stream)
 }
 
 int pavg_nonlinear(pavg_ctx* ctx, const double* U, double* NU, int B, void* stream) {
-  if (!ctx || !U || !NU || B < 0) return PAVG_ERR_INVAL;
+  if (!ctx || B < 0 || (B > 0 && (!U || !NU))) return PAVG_ERR_INVAL;
   CallScope scope_(ctx);
   const int64_t n = ctx->dm.n;
   for (int b = 0; b < B; ++b) {
@@ -682,7 +682,7 @@ int pavg_nonlinear(pavg_ctx* ctx, const double* U, double* NU, int B, void* stre
 }
 
 int pavg_expL_apply(pavg_ctx* ctx, double t, const double* U, double* out, int B, void* stream) {
-  if (!ctx || !U || !out || B < 0 || !std::isfinite(t)) return PAVG_ERR_INVAL;
+  if (!ctx || B < 0 || (B > 0 && (!U || !out)) || !std::isfinite(t)) return PAVG_ERR_INVAL;
   CallScope scope_(ctx);
   const int64_t n = ctx->dm.n;
   for (int b = 0; b < B; ++b) {

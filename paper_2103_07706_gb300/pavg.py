@@ -182,7 +182,7 @@ def _ptr(t, n, B=None):
     want = n if B is None else B * n
     if t.numel() != want:
         raise ValueError(f"expected {want} elements, got {t.numel()}")
-    return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(t.data_ptr() or None)
 
 
 def _stream():

@@ -207,3 +207,25 @@ def test_batch_timestep_matches_single_instance_and_oracle():
     b.close()
     for m_ in ms:
         m_.close()
+
+
+def test_batch_instance_with_topography():
+    """Each instance keeps its own topography inside a batch."""
+    from paper_2103_07706_gb300 import pavg
+    o = orc(2)
+    b0 = 300.0 * np.random.default_rng(8).random(o.n_eta)
+    ms = [pavg.Model(2, lambda_max=LAM[2]) for _ in range(2)]
+    ms[1].set_topography(dev(b0))
+    U = [dev(state(o, seed=31)), dev(state(o, seed=32))]
+    b = pavg.Batch(ms)
+    out = b.averaged_rhs([3600.0, 3600.0], [6, 6], U)
+    b.sync()
+    assert_close(o, out[0].cpu().numpy(), o.averaged_rhs(3600.0, 6, U[0].cpu().numpy()))
+    o.ops.set_topography(b0)
+    try:
+        assert_close(o, out[1].cpu().numpy(), o.averaged_rhs(3600.0, 6, U[1].cpu().numpy()))
+    finally:
+        o.ops.set_topography(np.zeros(o.n_eta))
+    b.close()
+    for m in ms:
+        m.close()

@@ -255,3 +255,29 @@ def test_refinement7_streamed_solver_matches_fp64_solver():
     assert np.array_equal(x[nu:], y[nu:])  # the elevation part has no M1 solve
     a.close()
     b.close()
+
+
+def test_averaged_rhs_with_topography_and_printed_upwind():
+    """The average with a nonzero topography b, and with the velocity upwind
+    rule as printed in Sec. 2.5, against the oracle's literal sum."""
+    for upwind in (0, 1):
+        g, o = gpu(2, upwind_convention=upwind), orc(2, upwind=upwind)
+        b = 250.0 * np.random.default_rng(21).random(o.n_eta)
+        U = state(o, eta_noise=5.0)
+        g.set_topography(dev(b))
+        o.ops.set_topography(b)
+        try:
+            assert_close(o, g.averaged_rhs(5400.0, 6, dev(U)).cpu().numpy(), o.averaged_rhs(5400.0, 6, U))
+        finally:
+            g.set_topography(dev(np.zeros(o.n_eta)))
+            o.ops.set_topography(np.zeros(o.n_eta))
+
+
+def test_empty_batches_are_no_ops():
+    import torch
+    g = gpu(2)
+    empty = torch.empty(0, dtype=torch.float64, device="cuda")
+    for f in (g.linear, g.nonlinear):
+        assert f(empty).numel() == 0
+    assert g.expL(600.0, empty).numel() == 0
+    g.sync()
