@@ -353,8 +353,8 @@ int pavg_surrogate_features(pavg_surrogate* s, pavg_ctx* ctx, const double* U, c
                             int standardised, void* stream);
 
 /* out = V + correction for state U and its cheap average V (device, n doubles
- * each; out may not alias them).  bf16: the MLP's operands rounded to BF16
- * (FP32 sums). */
+ * each; out may not alias them).  bf16: the MLP's GEMMs on the tensor cores
+ * with BF16 operands and FP32 accumulation. */
 int pavg_surrogate_apply(pavg_surrogate* s, pavg_ctx* ctx, const double* U, const double* V, double* out, int bf16,
                          void* stream);
 /* The surrogate form of N-bar(U) with its fallback: V = N-bar_Mc(U), out =

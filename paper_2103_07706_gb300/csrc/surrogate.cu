@@ -7,8 +7,8 @@
 // 327680 cells of refinement 7 about 22 GFLOP.  Both are far from any
 // roofline of their own next to the averages they replace, so the GEMMs are
 // plain shared-memory tiled FP32 kernels (64 x 64 output tile, 16-deep k
-// slices, 4 x 4 outputs per thread); the BF16 mode rounds both operands to
-// BF16 as they enter shared memory (BF16 inputs, exact products, FP32 sums).
+// slices, 4 x 4 outputs per thread).  BF16 inference runs on the tensor
+// cores (mma.sync, BF16 operands, FP32 accumulation).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -99,6 +99,97 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(int M, int N, int K, cons
       Cz[(size_t)m * ldc + n] = v;
     }
   }
+}
+
+// BF16 inference on the tensor cores: C [M][N] = A [M][K] W^T + bias (tanh
+// when EPI = 1), W stored [N][K], both rounded to BF16, FP32 accumulation,
+// by mma.sync m16n8k16 (row.col, bf16 x bf16 -> f32).  Block tile 64 x 64,
+// four warps of 32 x 32 (2 x 4 tiles of 16 x 8), K in slices of 16 staged in
+// shared memory as BF16.
+constexpr int kTcBM = 64, kTcBN = 64, kTcBK = 16;
+
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x (low half) = lo
+  return *reinterpret_cast<const unsigned*>(&v);
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(128) k_gemm_bf16_tc(int M, int N, int K, const float* __restrict__ A, int lda,
+                                                     const float* __restrict__ W, int ldw, float* C, int ldc,
+                                                     const float* __restrict__ bias) {
+  // BF16 pairs along k: As[m][k/2], Ws[n][k/2] (one 32-bit word = two k values)
+  __shared__ unsigned As[kTcBM][kTcBK / 2 + 1];
+  __shared__ unsigned Ws[kTcBN][kTcBK / 2 + 1];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * kTcBN;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;  // warp tile origin in the block tile
+  const int g = lane >> 2, tg = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += kTcBK) {
+    // stage: 64 rows x 8 pairs for A and for W, 128 threads x 4 pairs each
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int idx = tid + 128 * r, row = idx >> 3, kp = idx & 7, k = k0 + 2 * kp;
+      const int gm = m0 + row, gn = n0 + row;
+      float a0 = 0.f, a1 = 0.f, w0 = 0.f, w1 = 0.f;
+      if (gm < M) {
+        if (k < K) a0 = A[(size_t)gm * lda + k];
+        if (k + 1 < K) a1 = A[(size_t)gm * lda + k + 1];
+      }
+      if (gn < N) {
+        if (k < K) w0 = W[(size_t)gn * ldw + k];
+        if (k + 1 < K) w1 = W[(size_t)gn * ldw + k + 1];
+      }
+      As[row][kp] = pack_bf16(a0, a1);
+      Ws[row][kp] = pack_bf16(w0, w1);
+    }
+    __syncthreads();
+    unsigned af[2][4], bf[4][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int r0 = wm + 16 * i + g;
+      af[i][0] = As[r0][tg];          // rows g,   k 2tg..2tg+1
+      af[i][1] = As[r0 + 8][tg];      // rows g+8, k 2tg..2tg+1
+      af[i][2] = As[r0][tg + 4];      // rows g,   k 2tg+8..
+      af[i][3] = As[r0 + 8][tg + 4];  // rows g+8, k 2tg+8..
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = wn + 8 * j + g;
+      bf[j][0] = Ws[n][tg];      // k 2tg..2tg+1, column n
+      bf[j][1] = Ws[n][tg + 4];  // k 2tg+8..,    column n
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+            "{%0, %1, %2, %3};"
+            : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
+            : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bf[j][0]), "r"(bf[j][1]));
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int m = m0 + wm + 16 * i + g + (r >= 2 ? 8 : 0);
+        const int n = n0 + wn + 8 * j + 2 * tg + (r & 1);
+        if (m < M && n < N) {
+          float v = acc[i][j][r] + bias[n];
+          if (EPI == 1) v = tanhf(v);
+          C[(size_t)m * ldc + n] = v;
+        }
+      }
 }
 
 // out[i] = sum over z of part[z count + i], in z order.
@@ -323,6 +414,14 @@ cudaError_t gemm_t(int M, int N, int K, const float* A, int lda, const float* B,
   return cudaGetLastError();
 }
 
+template <int EPI>
+cudaError_t gemm_bf16_tc(int M, int N, int K, const float* A, int lda, const float* W, int ldw, float* C, int ldc,
+                         const float* bias, cudaStream_t st) {
+  dim3 grid((N + kTcBN - 1) / kTcBN, (M + kTcBM - 1) / kTcBM);
+  k_gemm_bf16_tc<EPI><<<grid, 128, 0, st>>>(M, N, K, A, lda, W, ldw, C, ldc, bias);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t sur_gemm(SurGemm kind, int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C,
@@ -330,11 +429,11 @@ cudaError_t sur_gemm(SurGemm kind, int M, int N, int K, const float* A, int lda,
                      cudaStream_t st) {
   switch (kind) {
     case SurGemm::kForwardTanh:  // A [M][K], B = W [N][K]
-      return bf16 ? gemm_t<false, true, 1, true>(M, N, K, A, lda, B, ldb, C, ldc, bias, aux, ldaux, 1, st)
-                  : gemm_t<false, true, 1, false>(M, N, K, A, lda, B, ldb, C, ldc, bias, aux, ldaux, 1, st);
+      if (bf16) return gemm_bf16_tc<1>(M, N, K, A, lda, B, ldb, C, ldc, bias, st);
+      return gemm_t<false, true, 1, false>(M, N, K, A, lda, B, ldb, C, ldc, bias, aux, ldaux, 1, st);
     case SurGemm::kForwardLinear:
-      return bf16 ? gemm_t<false, true, 2, true>(M, N, K, A, lda, B, ldb, C, ldc, bias, aux, ldaux, 1, st)
-                  : gemm_t<false, true, 2, false>(M, N, K, A, lda, B, ldb, C, ldc, bias, aux, ldaux, 1, st);
+      if (bf16) return gemm_bf16_tc<2>(M, N, K, A, lda, B, ldb, C, ldc, bias, st);
+      return gemm_t<false, true, 2, false>(M, N, K, A, lda, B, ldb, C, ldc, bias, aux, ldaux, 1, st);
     case SurGemm::kBackwardData:  // dA = (dY [M][K] W [K][N]) (1 - H^2)
       return gemm_t<false, false, 3, false>(M, N, K, A, lda, B, ldb, C, ldc, bias, aux, ldaux, 1, st);
     case SurGemm::kWeightGrad:  // dW [M][N] = dY^T (dY stored [K][M]) X [K][N], split over K

@@ -222,3 +222,38 @@ def test_scratch_follows_the_context_not_its_address():
         assert np.allclose(X, S.features(o.ops.asm, U, U), rtol=1e-6, atol=1e-6)
         m.close()
     sur.close()
+
+
+def _bf16(x):
+    """Round float32 values to bfloat16 (nearest, ties to even), kept as float32."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32)
+
+
+def test_bf16_tensor_core_inference_matches_bf16_arithmetic():
+    """BF16 inference (tensor cores, FP32 accumulation) against the same
+    network evaluated in numpy with every GEMM operand rounded to BF16."""
+    from paper_2103_07706_gb300 import pavg
+    m, o = _model(2), orc(2)
+    U = state(o, seed=13, eta_noise=5.0)
+    V = state(o, seed=14, eta_noise=2.0)
+    sur = pavg.Surrogate(hidden=64, seed=15)
+    X = S.features(o.ops.asm, U, V)
+    mx, sx = X.mean(axis=0).astype(np.float32), (X.std(axis=0) + 1e-3).astype(np.float32)
+    my, sy = np.zeros(S.N_OUT, np.float32), np.ones(S.N_OUT, np.float32)
+    sur.set_scaling(mx, sx, my, sy)
+    p = {k: v.astype(np.float32) for k, v in _blocks(sur.params(), 64).items()}
+    Xs = sur.features(m, dev(U), dev(V), standardised=True).cpu().numpy()
+    H1 = np.tanh(_bf16(Xs) @ _bf16(p["W1"]).T + p["b1"]).astype(np.float32)
+    H2 = np.tanh(_bf16(H1) @ _bf16(p["W2"]).T + p["b2"]).astype(np.float32)
+    Y = (_bf16(H2) @ _bf16(p["W3"]).T + p["b3"]).astype(np.float64)
+    want = S.scatter(o.ops.asm, Y)
+    got = sur.apply(m, dev(U), dev(V), bf16=True).cpu().numpy() - V
+    # the hidden activations are rounded to BF16 too, so FP32 summation-order
+    # differences occasionally flip a rounding by one BF16 step (2^-8); a
+    # wrong fragment layout would give O(1) errors
+    assert np.linalg.norm(got - want) <= 1e-3 * np.linalg.norm(want)
+    assert np.abs(got - want).max() <= 1e-2 * np.abs(want).max()
+    sur.close()
+    m.close()
