@@ -8,9 +8,10 @@ balanced state, through the library's C-ABI (graph-replayed).
 
 Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank evaluates its
 own independent state (weak scaling, no collective on the data path).
-Single-GPU runs add three legs to the line: the mixed-precision mode on the
-same state, the batched evaluation of 64 independent instances, and the
-learned surrogate (trained at refinement 5, applied at refinement 6).
+Single-GPU runs add legs to the line: the mixed-precision mode and the
+literal per-shift form on the same state, the batched evaluation of 64
+independent instances, and the learned surrogate (trained at refinement 5,
+applied at refinements 6 and 7).
 --impl reference times the FP64 CPU oracle (the plain literal per-shift form)
 on a bounded sample of the same workload and prints its own line.
 """
@@ -102,6 +103,59 @@ def _mixed_mode(pavg, cfg, Ud, ref, args, stream):
            "cg_iters_mean": st["cg_iters_mean"], "error_flags": st["error_flags"]}
     m.close()
     return res
+
+
+def _literal_leg(model, cfg, Ud, ref):
+    """The literal per-shift form (each shift its own forward and backward
+    exponential, N with its mass solves) on the benchmark state: throughput
+    and relative L2 error per field against the shared-basis FP64 result."""
+    import torch
+    T, M = cfg["T_s"], cfg["M"]
+    o = torch.empty_like(Ud)
+    model.averaged_rhs_literal(T, M, Ud, o)  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    model.averaged_rhs_literal(T, M, Ud, o)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    nu = model.n_u
+    err = lambda sl: float((o[sl] - ref[sl]).norm() / ref[sl].norm())
+    return {"value": 1e3 / ms, "unit": "evals/s", "ms_per_step": ms,
+            "rel_l2_u_vs_shared": err(slice(0, nu)), "rel_l2_eta_vs_shared": err(slice(nu, None)),
+            "note": "sum over shifts of 2 K_m L applications each, against 2 K_max + 1 mass solves shared"}
+
+
+def _day_r5(pavg):
+    """Refinement 5, M = 32, T in {0.5, 1, 2} h: one simulated day of averaged
+    Lawson RK4 steps of 900 s from seeded states 2104-2106 (FP64), with the
+    relative drift of the total mass (sum over cells of det/6 times the sum
+    of the three DG1 values: the exact integral of eta on the flat cells)."""
+    import numpy as np
+    import torch
+    from paper_2103_07706_gb300.inputs import harmonic_state, lambda_max_for
+    m = pavg.Model(5, lambda_max=lambda_max_for(5))
+    verts, cells = m.mesh()
+    P = verts[cells]
+    det = np.linalg.norm(np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]), axis=1)
+    w = torch.from_numpy(np.repeat(det / 6.0, 3)).cuda()
+    mass = lambda X: float((w * X[m.n_u:]).sum().item())
+    out = {}
+    for i, T in enumerate((1800.0, 3600.0, 7200.0)):
+        U = torch.from_numpy(harmonic_state(verts, cells, 2104 + i, 16)[0]).cuda()
+        m0 = mass(U)
+        scale = float((w * U[m.n_u:].abs()).sum().item())
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        m.timestep(900.0, T, 32, U, 96)
+        e1.record()
+        torch.cuda.synchronize()
+        m.sync()
+        out[f"T{int(T)}"] = {"steps_per_s": 96 / (e0.elapsed_time(e1) / 1e3), "seconds_per_day": e0.elapsed_time(e1) / 1e3,
+                             "mass_drift_rel": abs(mass(U) - m0) / scale, "finite": bool(torch.isfinite(U).all().item())}
+    m.close()
+    return {"workload": "refinement 5, M 32, dt 900 s, 96 steps (1 day) per T, FP64", **out}
 
 
 def _precision_days(pavg, cfg, U, days):
@@ -544,8 +598,10 @@ def run_pavg(args):
 
     # mixed-precision mode on the same state: throughput and error against the FP64 result above
     mixed = _mixed_mode(pavg, cfg, Ud, out, args, stream) if "mixed" in legs else None
+    literal = _literal_leg(model, cfg, Ud, out) if "literal" in legs else None
     batch = _batch_leg(pavg, batch_states) if "batch" in legs else None
     days = _precision_days(pavg, cfg, U, args.days) if "precision_days" in legs else None
+    day_r5 = _day_r5(pavg) if "day_r5" in legs else None
     surrogate = _surrogate_leg(pavg, sur_states) if "surrogate" in legs else None
 
     # parity of the small configuration against the oracle (computed by the spawned leg)
@@ -601,7 +657,7 @@ def run_pavg(args):
             "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": 8 * model.n,
                     "d2h_bytes_per_step": 8 * model.n},
             "gpu_launches": st["kernel_launches"] * args.steps,
-            "roofline": roof, "cpu_baseline": cpu, "parity": parity, "precision_mixed": mixed, "precision_days": days, "batch": batch, "surrogate": surrogate,
+            "roofline": roof, "cpu_baseline": cpu, "parity": parity, "precision_mixed": mixed, "literal": literal, "precision_days": days, "day_r5": day_r5, "batch": batch, "surrogate": surrogate,
             "clocks": clk,
             "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
             "error_flags": st["error_flags"]}
@@ -621,8 +677,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-n", type=int, default=None, help="instances of the batched leg (profiling only)")
     ap.add_argument("--batch-max-r", type=int, default=None, help="largest refinement of the batched leg (profiling only)")
-    ap.add_argument("--legs", default="fp64,mixed,batch,surrogate",
-                    help="comma list: fp64 (always), mixed, batch, surrogate, precision_days (single GPU only)")
+    ap.add_argument("--legs", default="fp64,mixed,literal,batch,surrogate",
+                    help="comma list: fp64 (always), mixed, literal, batch, surrogate, precision_days, "
+                         "day_r5 (single GPU only)")
     ap.add_argument("--days", type=float, default=1.0, help="simulated days of the precision_days leg")
     ap.add_argument("--refinement", type=int, default=None, help="smaller case (profiling only)")
     ap.add_argument("--M", type=int, default=None, help="number of shifts (profiling only)")
