@@ -53,3 +53,21 @@ def test_default_params_and_invalid_create_without_gpu(libpath):
     assert lib.pavg_destroy(None) == -1
     assert lib.pavg_averaged_rhs(None, 1.0, 4, None, None, None) == -1
     assert lib.pavg_last_error(None) == b"null context"
+
+
+def test_batch_and_surrogate_argument_checks_without_gpu(libpath):
+    from paper_2103_07706_gb300 import pavg
+    lib = pavg.lib()
+    h = ctypes.c_void_p()
+    assert lib.pavg_batch_create(None, 0, ctypes.byref(h)) == -1
+    assert lib.pavg_batch_create(None, 2, ctypes.byref(h)) == -1
+    assert lib.pavg_batch_destroy(None) == -1
+    assert lib.pavg_batch_averaged_rhs(None, None, None, None, None, None) == -1
+    assert lib.pavg_batch_timestep(None, None, None, None, None, 1, None) == -1
+    assert lib.pavg_batch_set_config(None, None) == -1
+    assert lib.pavg_batch_last_error(None) == b"null batch"
+    assert lib.pavg_surrogate_create(0, 1, ctypes.byref(h)) == -1
+    assert lib.pavg_surrogate_create(5000, 1, ctypes.byref(h)) == -1
+    assert lib.pavg_surrogate_destroy(None) == -1
+    assert lib.pavg_surrogate_train(None, 1, 16, 1e-3, 1, None, None) == -1
+    assert lib.pavg_surrogate_last_error(None) == b"null surrogate"
