@@ -45,6 +45,9 @@ PARITY_CASE = {"refinement": 3, "M": 8, "T_s": 3600.0, "lambda_max": 0.00286, "l
 # lanes x 2 flops (FMA) x 2.07 GHz.  FP64: 1.25 TFLOP/s (nominal).
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_PEAK_TFLOPS = 1.25
+# DRAM bytes (read + write) of one k_cg_ir launch at refinement 6, from one ncu
+# capture of the current kernel (profiles/k_cg_ir_r6.md)
+K_CG_IR_DRAM_BYTES_R6 = (206.434304 + 80.506624) * 1e6
 
 
 def _cg_flops(F, n_u, iters, sweeps):
@@ -640,7 +643,8 @@ def run_pavg(args):
         f32, f64 = _cg_flops(F, n_u, iters, st["cg_sweeps_mean"])
         achieved = f32 / dur_s / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": K_CG_IR_DRAM_BYTES_R6 if cfg["refinement"] == 6 else None,
                 "kernel": "k_cg_ir (persistent mixed-precision M1 solve: FP32 CG + FP64 residual sweeps)",
                 "fp64_achieved": f64 / dur_s / 1e12, "fp64_peak": FP64_PEAK_TFLOPS,
                 "launch_ms": cg_ms / cg_n, "launches_per_step": cg_n, "iters_per_launch": iters,
