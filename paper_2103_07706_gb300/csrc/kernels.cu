@@ -1,4 +1,6 @@
-// CUDA kernels of libpavg for sm_103a (FP64 path).
+// CUDA kernels of libpavg for sm_103a: the operators K-hat and N (FP64, and
+// the FP32 variants of the mixed-precision mode), the shift/coefficient
+// contractions, small vector kernels, and the FP64 Jacobi CG.
 //
 // Layout: per-cell data in structure-of-arrays form ([k][F]) so that a warp of
 // consecutive cells reads consecutive addresses; element matrices carry the
@@ -440,7 +442,9 @@ __global__ void __launch_bounds__(128) k_facets(DeviceMesh m, const double* __re
 // The cell integrand in reference form is, with v = G u_hat and the
 // derivative d_tau = v1 d/dx - v0 d/dy:
 //   [d_tau cross2(u_hat, psi_i) + div psi_i (u_hat . v) / 2] / det^2.
-// Sums over quadrature points are accumulated in FP64.
+// This kernel forms the cell integrals and adds the facet integrals that
+// k_facets stored for the cell's three edges.  Sums over quadrature points
+// are accumulated in FP64.
 // In FP32 (R = float) the elevation terms use the equivalent strong form
 //   re_k = -int_K phi_k div(u (eta - b)) + int_dK phi_k (u . n) ((eta - b)_own - (eta - b)~),
 // identical under exact integration (the divergence theorem on each cell;
