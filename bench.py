@@ -346,12 +346,23 @@ def _surrogate_leg(pavg, states):
         ev[2].record()
         torch.cuda.synchronize()
         t_sur, t_full = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        # plain Riemann sums with more shifts: error (same judge) and time
+        plain = {}
+        for Mp in (16, 32):
+            err_p = zero.averaged_rhs(mr, T, Mp, Mf, tests[0], threshold=1.0)[2]
+            mr.averaged_rhs(T, Mp, tests[0], out)
+            torch.cuda.synchronize()
+            ev[0].record()
+            mr.averaged_rhs(T, Mp, tests[0], out)
+            ev[1].record()
+            torch.cuda.synchronize()
+            plain[f"M{Mp}"] = {"rel_err_energy": float(err_p), "ms": ev[0].elapsed_time(ev[1])}
         res[f"r{r}"] = {"cells": mr.n_cells, "rel_err_energy_cheap_M8": float(np.mean(e_cheap)),
                         "rel_err_energy_surrogate": float(np.mean(e_sur)),
                         "rel_err_energy_surrogate_bf16": float(np.mean(e_bf)),
                         "gain": float(np.mean(e_cheap) / np.mean(e_sur)),
                         "surrogate_ms": t_sur, "full_M128_ms": t_full, "speedup_vs_full": t_full / t_sur,
-                        "would_fall_back": bool(np.mean(e_sur) > 1e-3)}
+                        "plain_riemann": plain, "would_fall_back": bool(np.mean(e_sur) > 1e-3)}
         del tests, out
         mr.close()
     sur.close()
