@@ -317,6 +317,7 @@ def _surrogate_leg(pavg, states):
     rows = sur.rows()
     del U, Vc, Vf
     mt.close()
+    peaks = _peaks()
     zero = pavg.Surrogate(hidden=8)
     zero.set_params(np.zeros(zero.nparams, dtype=np.float32))
     res = {"workload": f"train r{S['train_refinement']} ({S['pairs']} pairs, {rows} cell rows), T = 4 h, "
@@ -357,12 +358,35 @@ def _surrogate_leg(pavg, states):
             ev[1].record()
             torch.cuda.synchronize()
             plain[f"M{Mp}"] = {"rel_err_energy": float(err_p), "ms": ev[0].elapsed_time(ev[1])}
+        # the network alone (features, three GEMMs, scatter), FP32 and BF16
+        vc = mr.averaged_rhs(T, Mc, tests[0])
+        mlp = {}
+        flop = 2.0 * mr.n_cells * (pavg.N_SUR_IN * S["hidden"] + S["hidden"] ** 2 + S["hidden"] * pavg.N_SUR_OUT)
+        io_bytes = 3.0 * 8 * mr.n  # U and V read, out written
+        for name, bf in (("fp32", False), ("bf16", True)):
+            sur.apply(mr, tests[0], vc, out, bf16=bf)
+            torch.cuda.synchronize()
+            ev[0].record()
+            for _ in range(20):
+                sur.apply(mr, tests[0], vc, out, bf16=bf)
+            ev[1].record()
+            torch.cuda.synchronize()
+            ms = ev[0].elapsed_time(ev[1]) / 20
+            peak = peaks.get("bf16_tflops", 1900.0) if bf else FP32_PEAK_TFLOPS
+            mlp[name] = {"ms": ms, "tflops": flop / ms * 1e-9, "frac_of_peak": flop / ms * 1e-9 / peak,
+                         "peak_tflops": peak, "io_gbs": io_bytes / ms * 1e-6,
+                         "io_frac_of_hbm": io_bytes / ms * 1e-6 / peaks.get("hbm_gbs", 6800.0)}
+        mlp["flop_per_apply"] = flop
+        mlp["peak_source"] = (("bf16: measured cuBLAS bf16 burst" if "bf16_tflops" in peaks else "bf16: fallback 1.9 PF")
+                              + "; fp32: FP32 ALU from unit counts and clock "
+                              "(152 SMs x 128 lanes x 2 x 2.07 GHz)")
+        del vc
         res[f"r{r}"] = {"cells": mr.n_cells, "rel_err_energy_cheap_M8": float(np.mean(e_cheap)),
                         "rel_err_energy_surrogate": float(np.mean(e_sur)),
                         "rel_err_energy_surrogate_bf16": float(np.mean(e_bf)),
                         "gain": float(np.mean(e_cheap) / np.mean(e_sur)),
                         "surrogate_ms": t_sur, "full_M128_ms": t_full, "speedup_vs_full": t_full / t_sur,
-                        "plain_riemann": plain, "would_fall_back": bool(np.mean(e_sur) > 1e-3)}
+                        "plain_riemann": plain, "mlp_inference": mlp, "would_fall_back": bool(np.mean(e_sur) > 1e-3)}
         del tests, out
         mr.close()
     sur.close()
