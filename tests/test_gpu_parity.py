@@ -226,12 +226,46 @@ def test_full_size_properties():
     du = np.linalg.norm(S[:nu] - L[:nu]) / np.linalg.norm(L[:nu])
     de = np.linalg.norm(S[nu:] - L[nu:]) / np.linalg.norm(L[nu:])
     assert du <= RTOL and de <= RTOL, (du, de)
+    # mass: N and L conserve the integral of eta, and a polynomial in L maps a
+    # zero-mass field to a zero-mass field, so the eta part of N-bar has none.
+    # DG1 on a flat facet: each of a cell's three eta values weighs area / 3.
+    a, b = v[c[:, 1]] - v[c[:, 0]], v[c[:, 2]] - v[c[:, 0]]
+    w = np.repeat(0.5 * np.linalg.norm(np.cross(a, b), axis=1) / 3.0, 3)
+    we = w * S[nu:]
+    assert abs(we.sum()) <= 1e-13 * np.abs(we).sum(), (we.sum(), np.abs(we).sum())
     N = g.nonlinear(Ud).cpu().numpy()
     d1 = np.linalg.norm(g.averaged_rhs(20.0, 2, Ud).cpu().numpy() - N)
     d2 = np.linalg.norm(g.averaged_rhs(2.0, 2, Ud).cpu().numpy() - N)
     assert 60.0 < d1 / d2 < 140.0
     assert g.stats()["error_flags"] == 0
     del torch
+    g.close()
+
+
+def test_full_size_expL_group_law():
+    """Refinement 6 with the benchmark's lambda_max: e^{-tL} e^{tL} U = U,
+    e^{700 L} e^{500 L} U = e^{1200 L} U and e^{tL} of a state at rest is the
+    state (Sec. 2.4: the series approximates the exact group, to its
+    truncation tolerance, here 1e-13; bound 100 times that)."""
+    from paper_2103_07706_gb300 import pavg
+    from paper_2103_07706_gb300.inputs import harmonic_state
+    g = pavg.Model(6, lambda_max=0.02335, cheb_tol=1e-13)
+    v, c = g.mesh()
+    U, _ = harmonic_state(v, c, 2103, 16)
+    Ud = dev(U)
+    a = g.expL(1200.0, Ud)
+    back = g.expL(-1200.0, a).cpu().numpy()
+    ab = g.expL(700.0, g.expL(500.0, Ud)).cpu().numpy()
+    a = a.cpu().numpy()
+    assert np.linalg.norm(back - U) <= 1e-11 * np.linalg.norm(U)
+    assert np.linalg.norm(ab - a) <= 1e-11 * np.linalg.norm(a)
+    rest = np.zeros(g.n)
+    rest[g.n_u:] = 3.0
+    out = g.expL(2000.0, dev(rest)).cpu().numpy()
+    assert np.abs(out[: g.n_u]).max() < 1e-9  # edge-flux DOFs: ~1e-15 m/s
+    assert np.abs(out[g.n_u:] - 3.0).max() < 1e-11
+    g.sync()
+    assert g.stats()["error_flags"] == 0
     g.close()
 
 
