@@ -196,21 +196,27 @@ SURROGATE = {"train_refinement": 5, "tests": {6: 2, 7: 1}, "T_s": 4 * 3600.0, "M
 
 
 def _state_job(job):
-    """One seeded state (runs in a spawned pool worker; no CUDA)."""
-    r, seed = job
-    from oracle.mesh import build_mesh
+    """One seeded state on a given mesh (runs in a spawned pool worker; no CUDA)."""
+    verts, cells, seed = job
     from paper_2103_07706_gb300.inputs import harmonic_state
-    m = build_mesh(r, CONFIG["R"])
-    return harmonic_state(m.verts, m.cells, seed, 16)[0]
+    return harmonic_state(verts, cells, seed, 16)[0]
 
 
-def _make_states(jobs):
-    """States of the batched and surrogate legs, built on the host cores in a
-    spawned pool before the first CUDA call (in this process when few)."""
-    if len(jobs) <= 8:
-        return [_state_job(j) for j in jobs]
+def _make_states(pavg, jobs):
+    """States of the batched and surrogate legs on the library's own meshes
+    (exported once per refinement), built on the host cores in a spawned pool
+    (in this process when few)."""
+    from paper_2103_07706_gb300.inputs import lambda_max_for
+    meshes = {}
+    for r in sorted({r for r, _ in jobs}):
+        m = pavg.Model(r, lambda_max=lambda_max_for(r), radius=CONFIG["R"])
+        meshes[r] = m.mesh()
+        m.close()
+    work = [(*meshes[r], seed) for r, seed in jobs]
+    if len(work) <= 8:
+        return [_state_job(w) for w in work]
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
-        return pool.map(_state_job, jobs)
+        return pool.map(_state_job, work)
 
 
 BATCH = {"n": 64, "max_refinement": 6}  # the workload; smaller only for profiling
@@ -558,18 +564,6 @@ def run_pavg(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
     legs = set(args.legs.split(",")) if world == 1 else {"fp64"}
-    batch_states = sur_states = None
-    if legs & {"batch", "surrogate"}:  # host work in a spawned pool, before any CUDA call
-        jobs = (_batch_jobs() if "batch" in legs else []) + (_surrogate_jobs() if "surrogate" in legs else [])
-        states = _make_states(jobs)
-        nb = len(_batch_jobs()) if "batch" in legs else 0
-        batch_states, sur_states = states[:nb], states[nb:]
-    q = proc = None
-    if want_cpu:  # spawned before any CUDA call
-        ctxmp = mp.get_context("spawn")
-        q = ctxmp.Queue()
-        proc = ctxmp.Process(target=_oracle_worker, args=(q, CONFIG, PARITY_CASE), daemon=True)
-        proc.start()
 
     import numpy as np
     import torch
@@ -582,6 +576,18 @@ def run_pavg(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    batch_states = sur_states = None
+    if legs & {"batch", "surrogate"}:  # host work, finished before the oracle sample is timed
+        jobs = (_batch_jobs() if "batch" in legs else []) + (_surrogate_jobs() if "surrogate" in legs else [])
+        states = _make_states(pavg, jobs)
+        nb = len(_batch_jobs()) if "batch" in legs else 0
+        batch_states, sur_states = states[:nb], states[nb:]
+    q = proc = None
+    if want_cpu:  # a spawned process (no CUDA state is inherited), timed on one host core
+        ctxmp = mp.get_context("spawn")
+        q = ctxmp.Queue()
+        proc = ctxmp.Process(target=_oracle_worker, args=(q, CONFIG, PARITY_CASE), daemon=True)
+        proc.start()
     cfg = CONFIG
     model = pavg.Model(cfg["refinement"], lambda_max=cfg["lambda_max"], g=cfg["g"], H=cfg["H"], omega=cfg["Omega"],
                        radius=cfg["R"], cheb_tol=cfg["cheb_tol"], cg_rtol=cfg["cg_rtol"])
