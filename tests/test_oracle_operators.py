@@ -94,6 +94,24 @@ def test_upwind_elevation_flux_dissipates(om):
     assert abs(m.ops.D @ U[: m.n_u]).max() < 1e-12 * abs(m.ops.D).max() * abs(U[: m.n_u]).max()
 
 
+@pytest.mark.parametrize("upwind", [0, UPWIND_AS_PRINTED])
+def test_velocity_terms_do_no_work_on_divergence_free_flow(om, upwind):
+    """Tested against w = u, the vorticity term's cell and facet integrands
+    carry u^perp . u = 0, and the kinetic-energy term carries div u.  So for a
+    discretely divergence-free u the velocity part of N does no work,
+    u . r_u = 0 to rounding, whichever side u~ is taken from (Sec. 2.5).  For
+    the same reason the energy of a long run cannot tell the two readings of
+    the velocity upwind rule apart.  Dropping a product-rule term in the
+    derivative of u^perp . w, or taking the other cell's u in a facet's
+    u^perp . w, leaves a residual of 1e-5 or more of sum |u_i r_i|."""
+    m = om(3, upwind=upwind)
+    U = _state(m)
+    u = U[: m.n_u]
+    assert abs(m.ops.D @ u).max() < 1e-12 * abs(m.ops.D).max() * abs(u).max()
+    r = m.ops.nonlinear_rhs(U)[: m.n_u]
+    assert abs(u @ r) <= 1e-13 * np.abs(u * r).sum()
+
+
 def _solid_body_errors(m, omega_body=1e-5, amp=100.0):
     ops = m.ops
     ub = lambda x: omega_body * np.stack([-x[..., 1], x[..., 0], 0 * x[..., 0]], -1)  # noqa: E731
