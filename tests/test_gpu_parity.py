@@ -242,6 +242,35 @@ def test_full_size_properties():
     g.close()
 
 
+def test_full_size_nonlinear_invariants():
+    """Refinement 6, the benchmark's N kernels on a discretely divergence-free
+    state.  Properties that hold at any size (Sec. 2.5):
+    * the velocity part does no work: u . M1 N_u = u . r_u = 0, since the
+      vorticity integrands carry u^perp . u = 0 and the kinetic-energy term
+      carries div u = 0;
+    * the elevation part conserves mass: each facet flux enters its two cells
+      with opposite signs.
+    The M1 product uses the oracle's assembled matrix."""
+    from oracle.assembly import Assembly
+    from oracle.mesh import build_mesh
+    from paper_2103_07706_gb300 import pavg
+    from paper_2103_07706_gb300.inputs import harmonic_state
+    g = pavg.Model(6, lambda_max=0.02335)
+    v, c = g.mesh()
+    U, _ = harmonic_state(v, c, 2103, 16)
+    N = g.nonlinear(dev(U)).cpu().numpy()
+    g.sync()
+    assert g.stats()["error_flags"] == 0
+    nu = g.n_u
+    g.close()
+    M1 = Assembly(build_mesh(6, 6.37122e6), 7.292e-5, 6.37122e6).global_matrices()[0]
+    u, ru = U[:nu], M1 @ N[:nu]
+    assert abs(u @ ru) <= 1e-12 * np.abs(u * ru).sum(), (u @ ru, np.abs(u * ru).sum())
+    a, b = v[c[:, 1]] - v[c[:, 0]], v[c[:, 2]] - v[c[:, 0]]
+    we = np.repeat(0.5 * np.linalg.norm(np.cross(a, b), axis=1) / 3.0, 3) * N[nu:]
+    assert abs(we.sum()) <= 1e-13 * np.abs(we).sum(), (we.sum(), np.abs(we).sum())
+
+
 def test_full_size_expL_group_law():
     """Refinement 6 with the benchmark's lambda_max: e^{-tL} e^{tL} U = U,
     e^{700 L} e^{500 L} U = e^{1200 L} U and e^{tL} of a state at rest is the
