@@ -55,6 +55,10 @@ extern "C" {
 #define PAVG_ERR_NONFINITE (-5) /* NaN or Inf detected */
 #define PAVG_ERR_TIMEOUT (-6)   /* a bounded device-side wait gave up */
 
+/* Widest exponential accepted: lambda_max |t| of one e^{tL} (Sec. 2.4).  The
+ * series then has about that many terms, each one mass solve. */
+#define PAVG_MAX_CHEB_ARG 16384.0
+
 #define PAVG_QUAD_MIDPOINT 0     /* s_m = -T/2 + (m + 1/2) T / M            */
 #define PAVG_QUAD_CLOSED 1       /* odd M = 2N+1, s_k = k (T/2) / N, k=-N..N */
 #define PAVG_UPWIND_STANDARD 0   /* u~, (eta-b)~ from the side the flow leaves */
@@ -123,7 +127,8 @@ int pavg_nonlinear(pavg_ctx* ctx, const double* U, double* NU, int B, void* stre
 
 /* out = e^{tL} U for B states by the truncated Chebyshev series (Sec. 2.4,
  * Eq. cheby, truncation at cheb_tol).  t in seconds, any sign; t = 0 copies.
- * U and out are device [B][n] and may not alias. */
+ * U and out are device [B][n] and may not alias.  INVAL when t is not
+ * finite or lambda_max |t| > PAVG_MAX_CHEB_ARG. */
 int pavg_expL_apply(pavg_ctx* ctx, double t, const double* U, double* out, int B, void* stream);
 
 /* out = N-bar(U) = sum_m w_m e^{-s_m L} N(e^{s_m L} U) (Sec. 2.2, Eq. vt_discretised),
@@ -131,7 +136,9 @@ int pavg_expL_apply(pavg_ctx* ctx, double t, const double* U, double* out, int B
  * evaluation: one Chebyshev chain of L / lambda_max serves every shift and the
  * backward maps are summed by a Clenshaw recurrence (exact rewriting of the
  * sum; see the design notes).  U, out: device, n doubles, may not alias.
- * The work for each (T, M) is captured once in a CUDA graph and replayed. */
+ * The work for each (T, M) is captured once in a CUDA graph and replayed.
+ * INVAL when T is negative or not finite, M < 1, or lambda_max T / 2 >
+ * PAVG_MAX_CHEB_ARG (the widest shift's exponential). */
 int pavg_averaged_rhs(pavg_ctx* ctx, double T, int M, const double* U, double* out, void* stream);
 
 /* The same sum in its literal form: for each shift its own forward exponential,
@@ -140,7 +147,8 @@ int pavg_averaged_rhs_literal(pavg_ctx* ctx, double T, int M, const double* U, d
                               void* stream);
 
 /* nsteps averaged Lawson RK4 steps of size dt (Sec. 2.3, Eqs. stage1_c to stage4),
- * in place on the device state U_inout (n doubles). */
+ * in place on the device state U_inout (n doubles).  INVAL for a
+ * non-finite dt or T, and under the limits of the two calls above. */
 int pavg_timestep(pavg_ctx* ctx, double dt, double T, int M, double* U_inout, int nsteps,
                   void* stream);
 

@@ -143,6 +143,7 @@ int enq_expL(pavg_ctx* ctx, double t, const double* U, double* out, cudaStream_t
     return PAVG_OK;
   }
   std::vector<double> c = cheb_coefficients(ctx->lam * std::fabs(t), ctx->p.cheb_tol);
+  if (c.empty()) return set_err(ctx, PAVG_ERR_INVAL, cheb_limit_msg(ctx->lam * std::fabs(t)));
   const int K = (int)c.size() - 1;
   ctx->last_degree = K;
   const double sgn = t > 0 ? 1.0 : -1.0;
@@ -200,6 +201,7 @@ int get_plan(pavg_ctx* ctx, double T, int M, AvgPlan** out) {
   int K = 0;
   for (int m = 0; m < M; ++m) {
     cs[m] = cheb_coefficients(ctx->lam * std::fabs(s[m]), ctx->p.cheb_tol);
+    if (cs[m].empty()) return set_err(ctx, PAVG_ERR_INVAL, cheb_limit_msg(ctx->lam * std::fabs(s[m])));
     K = std::max(K, (int)cs[m].size() - 1);
   }
   AvgPlan pl;
@@ -731,7 +733,7 @@ int pavg_averaged_rhs_literal(pavg_ctx* ctx, double T, int M, const double* U, d
 //   U+ = E(dt) U + dt/6 [E(dt) k1 + 2 E(dt/2) k2 + 2 E(dt/2) k3 + k4]
 // evaluated as E(dt)(U + dt/6 k1) + dt/6 [2 E(dt/2)(k2 + k3) + k4] (E is linear).
 int pavg_timestep(pavg_ctx* ctx, double dt, double T, int M, double* U, int nsteps, void* stream) {
-  if (!ctx || !U || M < 1 || nsteps < 0 || !(T >= 0) || !std::isfinite(dt)) return PAVG_ERR_INVAL;
+  if (!ctx || !U || M < 1 || nsteps < 0 || !(T >= 0) || !std::isfinite(T) || !std::isfinite(dt)) return PAVG_ERR_INVAL;
   CallScope scope_(ctx);
   cudaStream_t st = S(stream);
   const int64_t n = ctx->dm.n;

@@ -469,11 +469,18 @@ int batch_expL(pavg_batch* b, const std::vector<double>& t, const std::vector<co
     for (int i = 0; i < n; ++i) {
       pavg_ctx* c = b->ctx[i];
       std::vector<double> cf = cheb_coefficients(c->lam * std::fabs(t[i]), c->p.cheb_tol);
+      if (cf.empty()) {
+        for (int j = 0; j < i; ++j) cudaFree(ep.coef[j]);
+        return bset_err(b, PAVG_ERR_INVAL, "instance " + std::to_string(i) + ": " + cheb_limit_msg(c->lam * std::fabs(t[i])));
+      }
       ep.K[i] = (int)cf.size() - 1;
       const double sg = t[i] >= 0 ? 1.0 : -1.0;
       double f = 1.0;
       for (auto& x : cf) { x *= f; f *= sg; }
-      if (upload(&ep.coef[i], cf) != cudaSuccess) return bset_err(b, PAVG_ERR_NOMEM, "coefficient upload");
+      if (upload(&ep.coef[i], cf) != cudaSuccess) {
+        for (int j = 0; j < i; ++j) cudaFree(ep.coef[j]);
+        return bset_err(b, PAVG_ERR_NOMEM, "coefficient upload");
+      }
     }
     it = b->exps.emplace(t, std::move(ep)).first;
   }
@@ -637,11 +644,18 @@ int pavg_batch_timestep(pavg_batch* b, const double* dt, const double* T, const 
   for (int i = 0; i < n; ++i)
     if (!U[i] || !std::isfinite(dt[i])) return bset_err(b, PAVG_ERR_INVAL, "null state or non-finite dt");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (b->stage.empty()) {
-    b->stage.assign(n, std::vector<double*>(7, nullptr));
-    for (int i = 0; i < n; ++i)
-      for (auto*& x : b->stage[i])
-        if (dalloc(&x, b->ctx[i]->dm.n) != cudaSuccess) return bset_err(b, PAVG_ERR_NOMEM, "timestep buffers");
+  if (b->stage.empty()) {  // all seven buffers per instance, or none
+    std::vector<std::vector<double*>> stage(n, std::vector<double*>(7, nullptr));
+    bool ok = true;
+    for (int i = 0; i < n && ok; ++i)
+      for (auto*& x : stage[i])
+        if (ok && dalloc(&x, b->ctx[i]->dm.n) != cudaSuccess) ok = false;
+    if (!ok) {
+      for (auto& v : stage)
+        for (auto* x : v) cudaFree(x);
+      return bset_err(b, PAVG_ERR_NOMEM, "timestep buffers");
+    }
+    b->stage = std::move(stage);
   }
   auto col = [&](int j) {
     std::vector<double*> v(n);

@@ -93,9 +93,20 @@ struct HostCellData {
 void build_cell_data(const Mesh& m, const RefElement& el, double omega, HostCellData* out,
                      ConstTables* tab);
 
+// Largest lambda_max |t| accepted for one exponential.  The coefficients
+// are a direct O(N^2) transform with N >= Lb + 64, and the series has about
+// Lb terms, each one mass solve; 16384 is 50 times the widest benchmark
+// window (refinement 7, T = 4 h: 336).
+constexpr double kMaxChebArg = PAVG_MAX_CHEB_ARG;
+
 // Chebyshev coefficients c_k of e^{tL} in the real recurrence (Sec. 2.4):
-// returns the truncated list (degree K = size - 1) for Lb = lambda_max |t|.
+// returns the truncated list (degree K = size - 1) for Lb = lambda_max |t|,
+// or an empty list when Lb is negative, not finite or above kMaxChebArg.
 std::vector<double> cheb_coefficients(double Lb, double tol);
+inline std::string cheb_limit_msg(double Lb) {
+  return "lambda_max |t| = " + std::to_string(Lb) + " is not finite or above " + std::to_string(kMaxChebArg) +
+         " (the widest exponential accepted)";
+}
 
 // Riemann-sum shifts and weights (Sec. 2.2).
 int shifts_weights(double T, int M, int rule, std::vector<double>* s, std::vector<double>* w);

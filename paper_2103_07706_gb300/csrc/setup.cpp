@@ -518,6 +518,7 @@ void build_cell_data(const Mesh& m, const RefElement& el, double omega, HostCell
 // then c_k = a_k i^{-k} for the real recurrence Q_{k+1} = 2 X Q_k + Q_{k-1};
 // truncation: the smallest K with sum_{j > K} |c_j| <= tol.
 std::vector<double> cheb_coefficients(double Lb, double tol) {
+  if (!(Lb >= 0.0) || !(Lb <= kMaxChebArg)) return {};
   if (Lb == 0.0) return {1.0};
   int N = 1;
   while (N < Lb + 64.0) N <<= 1;

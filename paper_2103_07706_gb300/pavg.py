@@ -23,6 +23,7 @@ PAVG_SOLVER_MIXED = 0
 PAVG_SOLVER_FP64 = 1
 PAVG_PRECISION_FP64 = 0
 PAVG_PRECISION_MIXED = 1
+PAVG_MAX_CHEB_ARG = 16384.0  # widest exponential accepted: lambda_max |t|
 
 ERRORS = {
     -1: "PAVG_ERR_INVAL", -2: "PAVG_ERR_NOMEM", -3: "PAVG_ERR_CUDA", -4: "PAVG_ERR_NOCONV",

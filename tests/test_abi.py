@@ -37,6 +37,19 @@ def test_binding_names_match_header(libpath):
     assert sorted(pavg.EXPORTED) == declared_symbols()
 
 
+def test_binding_constants_match_header():
+    """Every numeric #define of the header that the binding names has the
+    same value there (error codes, modes, the exponential width limit)."""
+    from paper_2103_07706_gb300 import pavg
+    text = open(os.path.join(ROOT, "include", "pavg.h")).read()
+    defs = dict(re.findall(r"#define\s+(PAVG_\w+)\s+\(?(-?[0-9.]+)\)?", text))
+    assert "PAVG_MAX_CHEB_ARG" in defs and "PAVG_ERR_INVAL" in defs
+    named = {k: v for k, v in defs.items() if hasattr(pavg, k)}
+    assert "PAVG_MAX_CHEB_ARG" in named
+    for k, v in named.items():
+        assert float(getattr(pavg, k)) == float(v), k
+
+
 def test_default_params_and_invalid_create_without_gpu(libpath):
     """Host-only calls: defaults, argument checks (no device work happens)."""
     from paper_2103_07706_gb300 import pavg

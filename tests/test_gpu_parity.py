@@ -206,6 +206,28 @@ def test_error_paths_are_reported():
     g.close()
 
 
+def test_exponential_width_limit():
+    """lambda_max |t| above PAVG_MAX_CHEB_ARG, or a non-finite window, is an
+    argument error raised before any exponential is built; the context stays
+    usable."""
+    from paper_2103_07706_gb300 import pavg
+    g = pavg.Model(2, lambda_max=LAM[2])
+    U = dev(np.zeros(g.n))
+    t_big = 1.5 * pavg.PAVG_MAX_CHEB_ARG / LAM[2]
+    calls = [lambda: g.expL(t_big, U), lambda: g.expL(-t_big, U), lambda: g.averaged_rhs(4.0 * t_big, 4, U),
+             lambda: g.timestep(900.0, float("inf"), 4, U, 1), lambda: g.timestep(4.0 * t_big, 3600.0, 4, U, 1)]
+    for call in calls:
+        with pytest.raises(pavg.PavgError) as e:
+            call()
+        assert e.value.code == -1
+    rest = np.zeros(g.n)
+    rest[g.n_u:] = 2.0
+    out = g.expL(900.0, dev(rest)).cpu().numpy()
+    assert np.abs(out[g.n_u:] - 2.0).max() < 1e-5
+    g.sync()
+    g.close()
+
+
 def test_full_size_properties():
     """Refinement 6, M = 64, T = 1 h (the benchmark configuration): properties
     that hold at any size: shared-basis equals the literal sum, mass is
