@@ -663,6 +663,7 @@ int pavg_lambda_max(const pavg_ctx* ctx, double* out) {
 
 int pavg_linear(pavg_ctx* ctx, const double* U, double* LU, int B, void* stream) {
   if (!ctx || B < 0 || (B > 0 && (!U || !LU))) return PAVG_ERR_INVAL;
+  if (B > 0 && LU == U) return set_err(ctx, PAVG_ERR_INVAL, "pavg_linear: the output aliases the input");
   CallScope scope_(ctx);
   const int64_t n = ctx->dm.n;
   for (int b = 0; b < B; ++b) {
@@ -674,6 +675,7 @@ int pavg_linear(pavg_ctx* ctx, const double* U, double* LU, int B, void* stream)
 
 int pavg_nonlinear(pavg_ctx* ctx, const double* U, double* NU, int B, void* stream) {
   if (!ctx || B < 0 || (B > 0 && (!U || !NU))) return PAVG_ERR_INVAL;
+  if (B > 0 && NU == U) return set_err(ctx, PAVG_ERR_INVAL, "pavg_nonlinear: the output aliases the input");
   CallScope scope_(ctx);
   const int64_t n = ctx->dm.n;
   for (int b = 0; b < B; ++b) {
@@ -685,6 +687,7 @@ int pavg_nonlinear(pavg_ctx* ctx, const double* U, double* NU, int B, void* stre
 
 int pavg_expL_apply(pavg_ctx* ctx, double t, const double* U, double* out, int B, void* stream) {
   if (!ctx || B < 0 || (B > 0 && (!U || !out)) || !std::isfinite(t)) return PAVG_ERR_INVAL;
+  if (B > 0 && out == U) return set_err(ctx, PAVG_ERR_INVAL, "pavg_expL_apply: the output aliases the input");
   CallScope scope_(ctx);
   const int64_t n = ctx->dm.n;
   for (int b = 0; b < B; ++b) {
@@ -696,12 +699,14 @@ int pavg_expL_apply(pavg_ctx* ctx, double t, const double* U, double* out, int B
 
 int pavg_averaged_rhs(pavg_ctx* ctx, double T, int M, const double* U, double* out, void* stream) {
   if (!ctx || !U || !out || M < 1 || !(T >= 0) || !std::isfinite(T)) return PAVG_ERR_INVAL;
+  if (out == U) return set_err(ctx, PAVG_ERR_INVAL, "pavg_averaged_rhs: the output aliases the input");
   CallScope scope_(ctx);
   return run_avg(ctx, T, M, U, out, S(stream));
 }
 
 int pavg_averaged_rhs_literal(pavg_ctx* ctx, double T, int M, const double* U, double* out, void* stream) {
   if (!ctx || !U || !out || M < 1 || !(T >= 0) || !std::isfinite(T)) return PAVG_ERR_INVAL;
+  if (out == U) return set_err(ctx, PAVG_ERR_INVAL, "pavg_averaged_rhs_literal: the output aliases the input");
   CallScope scope_(ctx);
   cudaStream_t st = S(stream);
   const int64_t n = ctx->dm.n;

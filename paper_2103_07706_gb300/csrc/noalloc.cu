@@ -62,7 +62,7 @@ int scratch_for_current_device(double** out, std::string* msg) {
 }  // namespace
 
 extern "C" int pavg_linear_noalloc(pavg_ctx* ctx, const double* U, double* LU, void* stream) {
-  if (!ctx || !U || !LU) return PAVG_ERR_INVAL;
+  if (!ctx || !U || !LU || LU == U) return PAVG_ERR_INVAL;
   const pavg::DeviceMesh& m = ctx->dm;
   if (m.n_u > kMaxNu) {
     ctx->err = "pavg_linear_noalloc: " + std::to_string(m.n_u) + " velocity DOFs exceed the static scratch (at most " +

@@ -228,6 +228,27 @@ def test_exponential_width_limit():
     g.close()
 
 
+def test_aliasing_outputs_are_rejected():
+    """The state calls forbid an output that aliases the input: an output
+    pointer equal to the input's is an argument error, and the input is left
+    as it was."""
+    import torch
+    from paper_2103_07706_gb300 import pavg
+    g = pavg.Model(2, lambda_max=LAM[2])
+    U = dev(state(orc(2)))
+    before = U.clone()
+    calls = [lambda: g.linear(U, U), lambda: g.nonlinear(U, U), lambda: g.expL(600.0, U, U),
+             lambda: g.averaged_rhs(3600.0, 4, U, U), lambda: g.averaged_rhs_literal(3600.0, 4, U, U),
+             lambda: g.linear_noalloc(U, U)]
+    for call in calls:
+        with pytest.raises(pavg.PavgError) as e:
+            call()
+        assert e.value.code == -1
+    g.sync()
+    assert torch.equal(U, before)
+    g.close()
+
+
 def test_full_size_properties():
     """Refinement 6, M = 64, T = 1 h (the benchmark configuration): properties
     that hold at any size: shared-basis equals the literal sum, mass is
