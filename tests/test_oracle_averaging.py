@@ -66,6 +66,32 @@ def test_T_to_zero_recovers_N(r1_model):
     assert 80.0 < e[0] / e[1] < 120.0
 
 
+def test_average_settles_beyond_four_points_per_period(om):
+    """Sec. 2.2: the average stops depending on M once the shifts sample the
+    fastest oscillation at four points per period, M >= 2 lambda_max T / pi
+    (3.25 here).  Against M = 64: errors of percents below that, under 1e-3
+    from M = 8 on.  Shifts spread over [-T, T] instead of [-T/2, T/2] would
+    halve the effective M and break the second bound."""
+    m = om(2, lambda_max=0.00142)
+    m.lam = 0.00142
+    T = 3600.0
+    assert 3.0 < 2 * m.lam * T / np.pi < 4.0
+    U, _ = harmonic_state(m.mesh.verts, m.mesh.cells, 2103, 8)
+    ref = m.averaged_rhs(T, 64, U)
+    nu = m.n_u
+
+    def err(M):
+        d = m.averaged_rhs(T, M, U) - ref
+        return (np.linalg.norm(d[:nu]) / np.linalg.norm(ref[:nu]),
+                np.linalg.norm(d[nu:]) / np.linalg.norm(ref[nu:]))
+
+    below = [err(M) for M in (2, 3)]
+    above = [err(M) for M in (8, 16)]
+    for k in range(2):
+        assert min(e[k] for e in below) > 20 * max(e[k] for e in above)
+        assert max(e[k] for e in above) < 1e-3
+
+
 def test_rest_state_and_mass(om):
     m = om(2)
     m.lam = 0.00142
