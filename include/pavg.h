@@ -148,7 +148,8 @@ int pavg_averaged_rhs_literal(pavg_ctx* ctx, double T, int M, const double* U, d
 
 /* nsteps averaged Lawson RK4 steps of size dt (Sec. 2.3, Eqs. stage1_c to stage4),
  * in place on the device state U_inout (n doubles).  INVAL for a
- * non-finite dt or T, and under the limits of the two calls above. */
+ * non-finite dt or T, for lambda_max |dt| > PAVG_MAX_CHEB_ARG (each step
+ * applies e^{dt L}), and under pavg_averaged_rhs's limits on T and M. */
 int pavg_timestep(pavg_ctx* ctx, double dt, double T, int M, double* U_inout, int nsteps,
                   void* stream);
 
