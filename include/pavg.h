@@ -250,7 +250,9 @@ int pavg_batch_destroy(pavg_batch* b);
 /* T, M: host arrays of n windows (seconds, >= 0) and shift counts (>= 1).
  * U, out: host arrays of n device pointers, instance i's state and result
  * (n_i doubles each, not aliasing).  Autotunes on the first call when no
- * configuration is set. */
+ * configuration is set.  INVAL (with the instance named in
+ * pavg_batch_last_error) for a null or aliasing pointer, a negative or
+ * non-finite T_i, M_i < 1, or lambda_max_i T_i / 2 > PAVG_MAX_CHEB_ARG. */
 int pavg_batch_averaged_rhs(pavg_batch* b, const double* T, const int* M, const double* const* U,
                             double* const* out, void* stream);
 
@@ -260,7 +262,9 @@ int pavg_batch_averaged_rhs(pavg_batch* b, const double* T, const int* M, const 
  * a step run as batched evaluations; the six exponentials of a step run as
  * one persistent launch of all instances' Chebyshev chains each, followed by
  * a one-row contraction per instance.  Results equal pavg_timestep on each
- * context up to rounding. */
+ * context up to rounding.  INVAL for a null pointer, a non-finite dt_i, the
+ * limits of pavg_batch_averaged_rhs, or lambda_max_i |dt_i| >
+ * PAVG_MAX_CHEB_ARG. */
 int pavg_batch_timestep(pavg_batch* b, const double* dt, const double* T, const int* M, double* const* U,
                         int nsteps, void* stream);
 
