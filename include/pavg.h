@@ -250,8 +250,8 @@ int pavg_batch_destroy(pavg_batch* b);
 /* T, M: host arrays of n windows (seconds, >= 0) and shift counts (>= 1).
  * U, out: host arrays of n device pointers, instance i's state and result
  * (n_i doubles each, not aliasing).  Autotunes on the first call when no
- * configuration is set.  INVAL (with the instance named in
- * pavg_batch_last_error) for a null or aliasing pointer, a negative or
+ * configuration is set.  INVAL (pavg_batch_last_error says why) for a
+ * null or aliasing pointer, a negative or
  * non-finite T_i, M_i < 1, or lambda_max_i T_i / 2 > PAVG_MAX_CHEB_ARG. */
 int pavg_batch_averaged_rhs(pavg_batch* b, const double* T, const int* M, const double* const* U,
                             double* const* out, void* stream);
