@@ -7,7 +7,7 @@
 // triples of DOFs that share an edge or a cell interior), adds d ||r|| to the
 // FP64 iterate and recomputes the FP64 residual r = b - M1 x with the FP64
 // element matrices.  The FP64 residual makes the result FP64-accurate; the
-// FP32 iterations run at the FP32 rate, 58x the FP64 rate of GB300.
+// FP32 iterations run at the FP32 rate, 64x the FP64 rate of GB300.
 //
 // Thread layout: four threads per cell, one per DOF triple (the three moments
 // of an edge, or the three interior moments).  Each thread applies its
