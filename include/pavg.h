@@ -134,8 +134,9 @@ int pavg_expL_apply(pavg_ctx* ctx, double t, const double* U, double* out, int B
 /* out = N-bar(U) = sum_m w_m e^{-s_m L} N(e^{s_m L} U) (Sec. 2.2, Eq. vt_discretised),
  * window T >= 0 seconds, M >= 1 shifts; T = 0 gives N(U).  Shared-basis
  * evaluation: one Chebyshev chain of L / lambda_max serves every shift and the
- * backward maps are summed by a Clenshaw recurrence (exact rewriting of the
- * sum; see the design notes).  U, out: device, n doubles, may not alias.
+ * backward maps are summed by a Clenshaw recurrence.  This is an exact
+ * rewriting of the sum: every term is a polynomial in the one operator L, so
+ * the terms commute.  U, out: device, n doubles, may not alias.
  * The work for each (T, M) is captured once in a CUDA graph and replayed.
  * INVAL when T is negative or not finite, M < 1, or lambda_max T / 2 >
  * PAVG_MAX_CHEB_ARG (the widest shift's exponential). */

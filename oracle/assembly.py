@@ -1,8 +1,10 @@
 """Cell geometry, element matrices and global sparse matrices (paper Sec. 2.5).
 
 Geometry: flat triangles through the mesh vertices (piecewise-linear
-approximation of the sphere; the paper uses a piecewise-cubic one, see the
-design notes).  For cell (v0, v1, v2) with a = x_v0:
+approximation of the sphere; the paper uses a piecewise-cubic one).  On a flat
+cell every integrand of L and N is a polynomial in the reference
+coordinates, so a rule of high enough degree integrates it exactly.  For
+cell (v0, v1, v2) with a = x_v0:
   J = [x_v1 - a, x_v2 - a] (3 x 2),  det = |J0 x J1|,  G = J^T J,
   k = (J0 x J1) / det (outward unit normal; cells are counter-clockwise),
   x(xi) = a + J xi.

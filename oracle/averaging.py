@@ -4,7 +4,8 @@ Eq. vt_averaged weights the phase shift s by rho(s / T) with rho a smooth bump
 supported on (-1/2, 1/2); Eq. vt_discretised replaces the integral by
 sum_m w_m e^{-s_m L} N(e^{s_m L} U).
 
-Readings (the printed bump and point set are garbled; see the design notes):
+Readings (the printed bump and point set are garbled, so these are this
+implementation's choices):
   * rho(x) = exp(-1 / (1/4 - x^2)) on |x| < 1/2, 0 elsewhere (the printed
     exponent has the wrong sign and would blow up at the ends);
   * the weights are normalised discretely, sum_m w_m = 1 (rho_0 cancels);

@@ -8,7 +8,8 @@ N(u, eta) = (u2, eta2) with (the two weak forms following Eq. ueq_int)
     int w . u2   = int u . grad_perp(u_perp . w) - int_Gamma [[n_perp (u_perp . w)]] . u~
                    + int div w (|u|^2 / 2)
     int phi eta2 = int grad phi . u (eta - b) - int_Gamma [[phi u]] (eta - b)~
-Readings (the printed facet terms are garbled; see the design notes):
+Readings (the printed facet terms are garbled, so these are this
+implementation's choices):
   * [[n_perp q]] = t (q+ - q-) with t the edge's low -> high unit tangent;
   * the elevation facet term carries a minus sign (integration by parts with
     outward normals) and the upwind value of (eta - b);

@@ -57,8 +57,9 @@ def test_table1_refinement3():
     """Paper Table 1, refinement 3: degrees 10 / 15 / 24 for 15 / 30 / 60 min
     with lambda_max from power iteration (g = 9.8, H = 5960 as in Sec. 3).
     Refinements 4 and 5 come out 3 and 9 terms lower at 1 h with this build's
-    flat-facet geometry (lambda_max doubles per refinement here); see the
-    design notes."""
+    flat-facet geometry: lambda_max doubles per refinement here, while the
+    printed degrees imply a factor of about 2.3 (cubic geometry, or another
+    lambda_max estimate)."""
     from tests.conftest import oracle_model
     rows = np.loadtxt(os.path.join(GOLDEN, "paper_table1.txt"), comments="#")
     m = oracle_model(3, g=9.8, H=5960.0)
