@@ -8,6 +8,15 @@
 //                         then one coefficient per line (count 0: refused)
 //   shifts T M RULE       the Riemann-sum shifts and weights (Sec. 2.2):
 //                         prints the status, then "s w" per line
+//   cells R RADIUS OMEGA PREFIX
+//                         the per-cell element matrices of M1 and C (Sec. 2.5)
+//                         as the kernels store them (signed, packed), expanded
+//                         and placed at their global DOFs: writes
+//                         PREFIX.{m1,c}.{row,col} (int64) and .val (float64)
+//                         triplets and PREFIX.det; prints "n_u F"
+//   tables                the reference tables the kernels read from constant
+//                         memory: prints D (3 x 12), then M2 and M2^{-1} (3 x 3)
+//                         of the reference cell, one row per line
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -51,6 +60,60 @@ int main(int argc, char** argv) {
     const int rc = pavg::shifts_weights(std::strtod(argv[2], nullptr), std::atoi(argv[3]), std::atoi(argv[4]), &s, &w);
     std::printf("%d\n", rc);
     for (size_t i = 0; i < s.size(); ++i) std::printf("%.17g %.17g\n", s[i], w[i]);
+    return 0;
+  }
+  if (cmd == "cells" && argc == 6) {
+    pavg::Mesh m;
+    pavg::build_mesh(std::atoi(argv[2]), std::strtod(argv[3], nullptr), &m);
+    pavg::RefElement el;
+    pavg::build_reference_element(&el);
+    pavg::HostCellData cd;
+    pavg::ConstTables tab;
+    pavg::build_cell_data(m, el, std::strtod(argv[4], nullptr), &cd, &tab);
+    const int64_t F = m.F();
+    std::vector<int64_t> r1, c1, rc, cc;
+    std::vector<double> v1, vc;
+    for (int64_t c = 0; c < F; ++c) {
+      int64_t g[12];
+      for (int l = 0; l < 12; ++l) g[l] = 3 * (int64_t)(cd.tri[4 * c + l / 3] & 0x7fffffff) + l % 3;
+      for (int i = 0; i < 12; ++i)
+        for (int j = 0; j < 12; ++j) {
+          const int a = i < j ? i : j, b = i < j ? j : i;
+          r1.push_back(g[i]);
+          c1.push_back(g[j]);
+          v1.push_back(cd.M1[(int64_t)pavg::packed_sym(a, b) * F + c]);
+          if (i != j) {
+            const double x = cd.C[(int64_t)pavg::packed_asym(a, b) * F + c];
+            rc.push_back(g[i]);
+            cc.push_back(g[j]);
+            vc.push_back(i < j ? x : -x);
+          }
+        }
+    }
+    const std::string p = argv[5];
+    if (!write_all(p + ".m1.row", r1.data(), 8 * r1.size()) || !write_all(p + ".m1.col", c1.data(), 8 * c1.size()) ||
+        !write_all(p + ".m1.val", v1.data(), 8 * v1.size()) || !write_all(p + ".c.row", rc.data(), 8 * rc.size()) ||
+        !write_all(p + ".c.col", cc.data(), 8 * cc.size()) || !write_all(p + ".c.val", vc.data(), 8 * vc.size()) ||
+        !write_all(p + ".det", cd.det.data(), 8 * cd.det.size()))
+      return 3;
+    std::printf("%lld %lld\n", (long long)(3 * m.E() + 3 * F), (long long)F);
+    return 0;
+  }
+  if (cmd == "tables" && argc == 2) {
+    pavg::Mesh m;
+    pavg::build_mesh(0, 1.0, &m);
+    pavg::RefElement el;
+    pavg::build_reference_element(&el);
+    pavg::HostCellData cd;
+    pavg::ConstTables tab;
+    pavg::build_cell_data(m, el, 0.0, &cd, &tab);
+    for (int i = 0; i < 3; ++i) {
+      for (int j = 0; j < 12; ++j) std::printf("%.17g ", tab.D[i][j]);
+      std::printf("\n");
+    }
+    for (int i = 0; i < 3; ++i) std::printf("%.17g %.17g %.17g\n", tab.M2_ref[i][0], tab.M2_ref[i][1], tab.M2_ref[i][2]);
+    for (int i = 0; i < 3; ++i)
+      std::printf("%.17g %.17g %.17g\n", tab.M2inv_ref[i][0], tab.M2inv_ref[i][1], tab.M2inv_ref[i][2]);
     return 0;
   }
   return 2;

@@ -79,3 +79,45 @@ def test_shifts_and_weights_match_oracle(harness, T, M, rule):
 def test_invalid_point_sets_are_refused(harness, T, M, rule):
     """The closed rule needs an odd M >= 3; M >= 1; the rule must exist."""
     assert run(harness, "shifts", repr(T), M, rule)[0] != "0"
+
+
+@pytest.mark.parametrize("r", [1, 2])
+def test_element_matrices_assemble_to_the_oracles(harness, tmp_path, r):
+    """The signed, packed element matrices of M1 and C (Sec. 2.5) that the
+    kernels read, placed at their global DOFs, sum to the oracle's global
+    matrices.  A wrong sign on reversed edges, a transposed or negated
+    Coriolis matrix, or a mis-packed triangle gives O(1) differences."""
+    import scipy.sparse as sp
+
+    from oracle.assembly import Assembly
+    omega = 7.292e-5
+    n, F = map(int, run(harness, "cells", r, repr(R), repr(omega), tmp_path / "c")[0].split())
+
+    def load(k):
+        rows = np.fromfile(tmp_path / f"c.{k}.row", dtype=np.int64)
+        cols = np.fromfile(tmp_path / f"c.{k}.col", dtype=np.int64)
+        vals = np.fromfile(tmp_path / f"c.{k}.val", dtype=np.float64)
+        return sp.coo_matrix((vals, (rows, cols)), shape=(n, n)).tocsr()
+
+    asm = Assembly(build_mesh(r, R), omega, R)
+    M1, C, _, _ = asm.global_matrices()
+    assert M1.shape == (n, n) and F == 20 * 4 ** r
+    assert abs(load("m1") - M1).max() <= 1e-13 * abs(M1).max()
+    assert abs(load("c") - C).max() <= 1e-12 * abs(C).max()
+    assert np.abs(np.fromfile(tmp_path / "c.det", dtype=np.float64) - asm.det).max() <= 1e-14 * asm.det.max()
+
+
+def test_reference_tables_match_the_oracle(harness):
+    """The constant-memory tables the kernels scale per cell: D-hat (the
+    oracle's D_e with its orientation signs divided out, the same for every
+    cell under the Piola map) and the DG1 mass M2-hat = (1 + delta_ij) / 24
+    of the reference triangle, with its inverse."""
+    from oracle.assembly import Assembly
+    rows = [list(map(float, line.split())) for line in run(harness, "tables")]
+    D, M2, M2inv = np.array(rows[:3]), np.array(rows[3:6]), np.array(rows[6:9])
+    asm = Assembly(build_mesh(1, R), 7.292e-5, R)
+    Dref = asm.D_e / asm.sign[:, None, :]
+    assert np.abs(Dref - D[None]).max() <= 1e-13
+    assert np.abs(M2 - (np.ones((3, 3)) + np.eye(3)) / 24.0).max() <= 1e-15
+    assert np.abs(asm.M2_e / asm.det[:, None, None] - M2[None]).max() <= 1e-15
+    assert np.abs(M2inv @ M2 - np.eye(3)).max() <= 1e-13
