@@ -17,6 +17,13 @@
 //   tables                the reference tables the kernels read from constant
 //                         memory: prints D (3 x 12), then M2 and M2^{-1} (3 x 3)
 //                         of the reference cell, one row per line
+//   solver R RADIUS PREFIX
+//                         the mixed solver's and the facet kernels' set-up
+//                         data, raw: PREFIX.tri (int32 [F][4]), .pinv (float32
+//                         [E + F][8]), .dinv (float64 [n_u]), .m1 (float64
+//                         [78][F]), .m1p (float32 [78][F]), .m1f (float32
+//                         [36][F][4]), .eplus / .eminus (int32 [E]), .elpos
+//                         (uint8 [E]); prints "E F"
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -114,6 +121,27 @@ int main(int argc, char** argv) {
     for (int i = 0; i < 3; ++i) std::printf("%.17g %.17g %.17g\n", tab.M2_ref[i][0], tab.M2_ref[i][1], tab.M2_ref[i][2]);
     for (int i = 0; i < 3; ++i)
       std::printf("%.17g %.17g %.17g\n", tab.M2inv_ref[i][0], tab.M2inv_ref[i][1], tab.M2inv_ref[i][2]);
+    return 0;
+  }
+  if (cmd == "solver" && argc == 5) {
+    pavg::Mesh m;
+    pavg::build_mesh(std::atoi(argv[2]), std::strtod(argv[3], nullptr), &m);
+    pavg::RefElement el;
+    pavg::build_reference_element(&el);
+    pavg::HostCellData cd;
+    pavg::ConstTables tab;
+    pavg::build_cell_data(m, el, 7.292e-5, &cd, &tab);
+    const std::string p = argv[4];
+    if (!write_all(p + ".tri", cd.tri.data(), 4 * cd.tri.size()) ||
+        !write_all(p + ".pinv", cd.Pinv.data(), 4 * cd.Pinv.size()) ||
+        !write_all(p + ".dinv", cd.dinv.data(), 8 * cd.dinv.size()) ||
+        !write_all(p + ".m1", cd.M1.data(), 8 * cd.M1.size()) || !write_all(p + ".m1p", cd.M1p.data(), 4 * cd.M1p.size()) ||
+        !write_all(p + ".m1f", cd.M1f.data(), 4 * cd.M1f.size()) ||
+        !write_all(p + ".eplus", m.edge_plus.data(), 4 * m.edge_plus.size()) ||
+        !write_all(p + ".eminus", m.edge_minus.data(), 4 * m.edge_minus.size()) ||
+        !write_all(p + ".elpos", m.edge_lpos.data(), m.edge_lpos.size()))
+      return 3;
+    std::printf("%lld %lld\n", (long long)m.E(), (long long)m.F());
     return 0;
   }
   return 2;

@@ -121,3 +121,52 @@ def test_reference_tables_match_the_oracle(harness):
     assert np.abs(M2 - (np.ones((3, 3)) + np.eye(3)) / 24.0).max() <= 1e-15
     assert np.abs(asm.M2_e / asm.det[:, None, None] - M2[None]).max() <= 1e-15
     assert np.abs(M2inv @ M2 - np.eye(3)).max() <= 1e-13
+
+
+def test_solver_and_facet_setup(harness, tmp_path):
+    """Set-up data of the mixed M1 solver and the facet kernels at r2 against
+    the oracle.  Edge incidence: plus cell = the one running the edge
+    low -> high, with local indices.  DOF triples: a cell's three edges and
+    its interior, each triple owned by exactly one cell.  Preconditioner:
+    FP32 inverses of M1's 3x3 diagonal blocks.  Jacobi diagonal.  The FP32
+    matrix copies in both layouts are roundings of the FP64 element
+    matrices."""
+    from oracle.assembly import Assembly
+    r = 2
+    E, F = map(int, run(harness, "solver", r, repr(R), tmp_path / "s")[0].split())
+    ld = lambda k, dt: np.fromfile(tmp_path / f"s.{k}", dtype=dt)  # noqa: E731
+    mesh = build_mesh(r, R)
+    # edge incidence
+    assert np.array_equal(ld("eplus", np.int32), mesh.edge_cells[:, 0])
+    assert np.array_equal(ld("eminus", np.int32), mesh.edge_cells[:, 1])
+    lpos = ld("elpos", np.uint8).astype(np.int64)
+    assert np.array_equal(lpos & 3, mesh.edge_local[:, 0]) and np.array_equal((lpos >> 2) & 3, mesh.edge_local[:, 1])
+    # DOF triples and owners
+    tri = ld("tri", np.int32).view(np.uint32).reshape(F, 4).astype(np.int64)
+    idx, own = tri & 0x7FFFFFFF, tri >> 31
+    assert np.array_equal(idx[:, :3], mesh.cell_edges) and np.array_equal(idx[:, 3], E + np.arange(F))
+    assert np.array_equal(own[:, :3].astype(bool), mesh.cell_edge_aligned) and own[:, 3].all()
+    assert np.array_equal(np.bincount(idx[own == 1], minlength=E + F), np.ones(E + F, dtype=np.int64))
+    # preconditioner blocks and Jacobi diagonal against the oracle's M1
+    M1 = Assembly(mesh, 7.292e-5, R).global_matrices()[0].toarray()
+    P = ld("pinv", np.float32).reshape(E + F, 8).astype(np.float64)
+    sym = np.array([[0, 1, 2], [1, 3, 4], [2, 4, 5]])
+    for t in range(E + F):
+        blk = M1[3 * t:3 * t + 3, 3 * t:3 * t + 3]
+        assert np.abs(P[t][sym] @ blk - np.eye(3)).max() <= 1e-5
+    assert np.abs(ld("dinv", np.float64) * np.diag(M1) - 1.0).max() <= 1e-14
+    # FP32 copies: packed [78][F] and row blocks [36][F][4]
+    m1 = ld("m1", np.float64)
+    assert np.array_equal(ld("m1p", np.float32), m1.astype(np.float32))
+    m1 = m1.reshape(78, F)
+    full = np.zeros((F, 12, 12))
+    k = 0
+    for i in range(12):
+        for j in range(i, 12):
+            full[:, i, j] = full[:, j, i] = m1[k]
+            k += 1
+    m1f = ld("m1f", np.float32).reshape(36, F, 4)
+    e = np.arange(36)
+    for q in range(4):
+        want = full[:, 3 * q + e // 12, e % 12].T.astype(np.float32)  # (36, F)
+        assert np.array_equal(m1f[:, :, q], want)
