@@ -24,6 +24,13 @@
 //                         [78][F]), .m1p (float32 [78][F]), .m1f (float32
 //                         [36][F][4]), .eplus / .eminus (int32 [E]), .elpos
 //                         (uint8 [E]); prints "E F"
+//   element X1 Y1 X2 Y2 ...
+//                         the reference BDM2 basis at each point: one line of
+//                         24 values psi_i[c], then one of 48 derivatives
+//                         d psi_i[c] / d xi_a (order i, c, a)
+//   gauss N               the N-point Gauss-Legendre rule on [0, 1]: "x w" lines
+//   cellrule              the cell rule of the nonlinear kernels: "w phi0 phi1
+//                         phi2" per point (phi = the DG1 basis at the point)
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -142,6 +149,42 @@ int main(int argc, char** argv) {
         !write_all(p + ".elpos", m.edge_lpos.data(), m.edge_lpos.size()))
       return 3;
     std::printf("%lld %lld\n", (long long)m.E(), (long long)m.F());
+    return 0;
+  }
+  if (cmd == "element" && argc >= 4 && argc % 2 == 0) {
+    pavg::RefElement el;
+    pavg::build_reference_element(&el);
+    for (int a = 2; a + 1 < argc; a += 2) {
+      const double x = std::strtod(argv[a], nullptr), y = std::strtod(argv[a + 1], nullptr);
+      double v[12][2], g[12][2][2];
+      el.eval(x, y, v);
+      el.eval_grad(x, y, g);
+      for (int i = 0; i < 12; ++i) std::printf("%.17g %.17g ", v[i][0], v[i][1]);
+      std::printf("\n");
+      for (int i = 0; i < 12; ++i)
+        for (int c = 0; c < 2; ++c) std::printf("%.17g %.17g ", g[i][c][0], g[i][c][1]);
+      std::printf("\n");
+    }
+    return 0;
+  }
+  if (cmd == "gauss" && argc == 3) {
+    const int n = std::atoi(argv[2]);
+    if (n < 1 || n > 64) return 2;
+    std::vector<double> x(n), w(n);
+    pavg::gauss_legendre01(n, x.data(), w.data());
+    for (int i = 0; i < n; ++i) std::printf("%.17g %.17g\n", x[i], w[i]);
+    return 0;
+  }
+  if (cmd == "cellrule" && argc == 2) {
+    pavg::Mesh m;
+    pavg::build_mesh(0, 1.0, &m);
+    pavg::RefElement el;
+    pavg::build_reference_element(&el);
+    pavg::HostCellData cd;
+    pavg::ConstTables tab;
+    pavg::build_cell_data(m, el, 0.0, &cd, &tab);
+    for (int q = 0; q < pavg::kCellQ; ++q)
+      std::printf("%.17g %.17g %.17g %.17g\n", tab.cq_w[q], tab.cq_phi[q][0], tab.cq_phi[q][1], tab.cq_phi[q][2]);
     return 0;
   }
   return 2;

@@ -170,3 +170,44 @@ def test_solver_and_facet_setup(harness, tmp_path):
     for q in range(4):
         want = full[:, 3 * q + e // 12, e % 12].T.astype(np.float32)  # (36, F)
         assert np.array_equal(m1f[:, :, q], want)
+
+
+def test_reference_basis_matches_the_oracle(harness):
+    """The library's BDM2 basis (values and derivatives at any reference point)
+    equals the oracle's: the same degrees of freedom fix the same basis."""
+    from oracle.elements import BDM2
+    rng = np.random.default_rng(11)
+    pts = rng.random((16, 2))
+    pts = np.where(pts.sum(1, keepdims=True) > 1, 1 - pts, pts)
+    out = run(harness, "element", *[f"{v:.17g}" for v in pts.ravel()])
+    el = BDM2()
+    want_v, want_g = el.values(pts), el.grads(pts)
+    for q in range(len(pts)):
+        v = np.array(out[2 * q].split(), dtype=np.float64).reshape(12, 2)
+        g = np.array(out[2 * q + 1].split(), dtype=np.float64).reshape(12, 2, 2)
+        assert np.abs(v - want_v[q]).max() <= 1e-12
+        assert np.abs(g - want_g[q]).max() <= 1e-11
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 8])
+def test_gauss_legendre_on_unit_interval(harness, n):
+    from scipy.special import roots_legendre
+    xw = np.array([line.split() for line in run(harness, "gauss", n)], dtype=np.float64)
+    x, w = roots_legendre(n)
+    assert np.abs(xw[:, 0] - (x + 1) / 2).max() <= 1e-15
+    assert np.abs(xw[:, 1] - w / 2).max() <= 1e-15
+
+
+def test_cell_rule_of_the_nonlinear_kernels_is_degree_five(harness):
+    """Every integrand of N on a flat cell has degree <= 5, so the 7-point rule
+    must integrate x^a y^b exactly over the reference triangle for a + b <= 5:
+    a! b! / (a + b + 2)!."""
+    from math import factorial
+    rows = np.array([line.split() for line in run(harness, "cellrule")], dtype=np.float64)
+    w, phi = rows[:, 0], rows[:, 1:]
+    assert np.abs(phi.sum(1) - 1).max() <= 1e-15
+    x, y = phi[:, 1], phi[:, 2]
+    for a in range(6):
+        for b in range(6 - a):
+            want = factorial(a) * factorial(b) / factorial(a + b + 2)
+            assert abs(np.sum(w * x ** a * y ** b) - want) <= 1e-15
