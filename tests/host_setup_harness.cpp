@@ -31,6 +31,10 @@
 //   gauss N               the N-point Gauss-Legendre rule on [0, 1]: "x w" lines
 //   cellrule              the cell rule of the nonlinear kernels: "w phi0 phi1
 //                         phi2" per point (phi = the DG1 basis at the point)
+//   ntables               the remaining constant tables of the nonlinear
+//                         kernels, one per line, flattened in C order:
+//                         cq_psi, cq_dpsi, fq_w, fq_psi, fq_phi, edge_dir,
+//                         div_vert
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -185,6 +189,27 @@ int main(int argc, char** argv) {
     pavg::build_cell_data(m, el, 0.0, &cd, &tab);
     for (int q = 0; q < pavg::kCellQ; ++q)
       std::printf("%.17g %.17g %.17g %.17g\n", tab.cq_w[q], tab.cq_phi[q][0], tab.cq_phi[q][1], tab.cq_phi[q][2]);
+    return 0;
+  }
+  if (cmd == "ntables" && argc == 2) {
+    pavg::Mesh m;
+    pavg::build_mesh(0, 1.0, &m);
+    pavg::RefElement el;
+    pavg::build_reference_element(&el);
+    pavg::HostCellData cd;
+    pavg::ConstTables tab;
+    pavg::build_cell_data(m, el, 0.0, &cd, &tab);
+    auto line = [](const double* p, size_t n) {
+      for (size_t i = 0; i < n; ++i) std::printf("%.17g ", p[i]);
+      std::printf("\n");
+    };
+    line(&tab.cq_psi[0][0][0], sizeof(tab.cq_psi) / sizeof(double));
+    line(&tab.cq_dpsi[0][0][0][0], sizeof(tab.cq_dpsi) / sizeof(double));
+    line(&tab.fq_w[0], sizeof(tab.fq_w) / sizeof(double));
+    line(&tab.fq_psi[0][0][0][0][0], sizeof(tab.fq_psi) / sizeof(double));
+    line(&tab.fq_phi[0][0][0][0], sizeof(tab.fq_phi) / sizeof(double));
+    line(&tab.edge_dir[0][0], sizeof(tab.edge_dir) / sizeof(double));
+    line(&tab.div_vert[0][0], sizeof(tab.div_vert) / sizeof(double));
     return 0;
   }
   return 2;

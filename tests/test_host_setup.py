@@ -211,3 +211,32 @@ def test_cell_rule_of_the_nonlinear_kernels_is_degree_five(harness):
         for b in range(6 - a):
             want = factorial(a) * factorial(b) / factorial(a + b + 2)
             assert abs(np.sum(w * x ** a * y ** b) - want) <= 1e-15
+
+
+def test_nonlinear_kernel_tables_match_the_oracle(harness):
+    """The constant tables of the nonlinear kernels are the reference basis
+    sampled where the oracle samples it (Sec. 2.5).  That means the 7 cell
+    points and the 4 Gauss points of each local edge: the + side at tau,
+    the - side at 1 - tau (each side runs the edge its own way).  Also the
+    edge directions and the basis divergences at the reference vertices."""
+    from oracle.elements import BDM2, EDGE_DIR, EDGE_START, dg1_values
+    from oracle.quadrature import gauss_legendre_01
+    lines = run(harness, "ntables")
+    arr = [np.array(line.split(), dtype=np.float64) for line in lines]
+    cq_psi, cq_dpsi, fq_w, fq_psi, fq_phi, edge_dir, div_vert = arr
+    rule = np.array([line.split() for line in run(harness, "cellrule")], dtype=np.float64)
+    xq = rule[:, 2:4]
+    el = BDM2()
+    assert np.abs(cq_psi.reshape(7, 12, 2) - el.values(xq)).max() <= 1e-12
+    assert np.abs(cq_dpsi.reshape(7, 12, 2, 2) - el.grads(xq)).max() <= 1e-11
+    tau, wt = gauss_legendre_01(4)
+    assert np.abs(fq_w - wt).max() <= 1e-15
+    fq_psi, fq_phi = fq_psi.reshape(2, 3, 4, 12, 2), fq_phi.reshape(2, 3, 4, 3)
+    for e in range(3):
+        for side, t in ((0, tau), (1, 1.0 - tau)):
+            x = EDGE_START[e][None, :] + t[:, None] * EDGE_DIR[e][None, :]
+            assert np.abs(fq_psi[side, e] - el.values(x)).max() <= 1e-12
+            assert np.abs(fq_phi[side, e] - dg1_values(x)).max() <= 1e-15
+    assert np.array_equal(edge_dir.reshape(3, 2), EDGE_DIR)
+    verts = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    assert np.abs(div_vert.reshape(12, 3) - el.divs(verts).T).max() <= 1e-11
