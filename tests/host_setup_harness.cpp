@@ -13,7 +13,8 @@
 //                         as the kernels store them (signed, packed), expanded
 //                         and placed at their global DOFs: writes
 //                         PREFIX.{m1,c}.{row,col} (int64) and .val (float64)
-//                         triplets and PREFIX.det; prints "n_u F"
+//                         triplets, PREFIX.det and PREFIX.g (float64 [3][F]:
+//                         G00, G01, G11 of G = J^T J); prints "n_u F"
 //   tables                the reference tables the kernels read from constant
 //                         memory: prints D (3 x 12), then M2 and M2^{-1} (3 x 3)
 //                         of the reference cell, one row per line
@@ -112,7 +113,7 @@ int main(int argc, char** argv) {
     if (!write_all(p + ".m1.row", r1.data(), 8 * r1.size()) || !write_all(p + ".m1.col", c1.data(), 8 * c1.size()) ||
         !write_all(p + ".m1.val", v1.data(), 8 * v1.size()) || !write_all(p + ".c.row", rc.data(), 8 * rc.size()) ||
         !write_all(p + ".c.col", cc.data(), 8 * cc.size()) || !write_all(p + ".c.val", vc.data(), 8 * vc.size()) ||
-        !write_all(p + ".det", cd.det.data(), 8 * cd.det.size()))
+        !write_all(p + ".det", cd.det.data(), 8 * cd.det.size()) || !write_all(p + ".g", cd.G.data(), 8 * cd.G.size()))
       return 3;
     std::printf("%lld %lld\n", (long long)(3 * m.E() + 3 * F), (long long)F);
     return 0;

@@ -85,7 +85,7 @@ def test_invalid_point_sets_are_refused(harness, T, M, rule):
 def test_element_matrices_assemble_to_the_oracles(harness, tmp_path, r):
     """The signed, packed element matrices of M1 and C (Sec. 2.5) that the
     kernels read, placed at their global DOFs, sum to the oracle's global
-    matrices.  A wrong sign on reversed edges, a transposed or negated
+    matrices; det and the metric G = J^T J match per cell.  A wrong sign on reversed edges, a transposed or negated
     Coriolis matrix, or a mis-packed triangle gives O(1) differences."""
     import scipy.sparse as sp
 
@@ -105,6 +105,10 @@ def test_element_matrices_assemble_to_the_oracles(harness, tmp_path, r):
     assert abs(load("m1") - M1).max() <= 1e-13 * abs(M1).max()
     assert abs(load("c") - C).max() <= 1e-12 * abs(C).max()
     assert np.abs(np.fromfile(tmp_path / "c.det", dtype=np.float64) - asm.det).max() <= 1e-14 * asm.det.max()
+    G = np.fromfile(tmp_path / "c.g", dtype=np.float64).reshape(3, F)
+    want = np.stack([asm.G[:, 0, 0], asm.G[:, 0, 1], asm.G[:, 1, 1]])
+    assert np.abs(G - want).max() <= 1e-14 * np.abs(want).max()
+    assert np.abs(asm.G[:, 0, 1] - asm.G[:, 1, 0]).max() == 0.0
 
 
 def test_reference_tables_match_the_oracle(harness):
