@@ -89,6 +89,28 @@ def dense_r1(om):
 
 
 @pytest.mark.parametrize("t", [450.0, -1800.0, 3600.0, 14400.0])
+def test_expL_matches_eigendecomposition(dense_r1, t):
+    """e^{tL} from the eigendecomposition of L (r1).  L is skew-adjoint in the
+    energy inner product W = diag(H M1, g M2) (Sec. 2.5), so with W = R^T R
+    the matrix S = R L R^{-1} is real skew-symmetric, iS is Hermitian, and
+    e^{tL} = R^{-1} V e^{-i t theta} V^H R with (theta, V) = eigh(iS): an
+    orthonormal eigenbasis, so no ill-conditioned eigenvectors enter."""
+    import scipy.linalg as sla
+    m, A, U = dense_r1
+    W = sla.block_diag(m.ops.H * m.ops.M1.toarray(), m.ops.g * m.ops.M2.toarray())
+    Rc = sla.cholesky(W)                                 # W = R^T R, R upper
+    S = sla.solve_triangular(Rc, (Rc @ A).T, trans=1).T  # R A R^{-1}
+    assert np.abs(S + S.T).max() <= 1e-10 * np.abs(S).max()
+    theta, V = np.linalg.eigh(1j * S)
+    y = V @ (np.exp(-1j * t * theta) * (V.conj().T @ (Rc @ U)))
+    ref = sla.solve_triangular(Rc, y.real)
+    assert np.abs(y.imag).max() <= 1e-10 * np.abs(y).max()
+    got = m.expL(t, U)
+    assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
+    assert np.linalg.norm(expm(t * A) @ U - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("t", [450.0, -1800.0, 3600.0, 14400.0])
 def test_expL_matches_dense_expm(dense_r1, t):
     m, A, U = dense_r1
     ref = expm(t * A) @ U
