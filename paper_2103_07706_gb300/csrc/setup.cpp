@@ -552,7 +552,7 @@ std::vector<double> cheb_coefficients(double Lb, double tol) {
 // Sec. 2.2: weights w_m = rho(s_m / T) / sum_j rho(s_j / T) with the C-infinity
 // bump rho(x) = exp(-1 / (1/4 - x^2)) on |x| < 1/2.
 int shifts_weights(double T, int M, int rule, std::vector<double>* s, std::vector<double>* w) {
-  if (M < 1 || T < 0) return PAVG_ERR_INVAL;
+  if (M < 1 || !(T >= 0) || !std::isfinite(T)) return PAVG_ERR_INVAL;
   s->assign(M, 0.0);
   w->assign(M, 0.0);
   if (rule == PAVG_QUAD_MIDPOINT) {

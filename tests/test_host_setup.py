@@ -64,20 +64,24 @@ def test_exponentials_beyond_the_limit_are_refused(harness, Lb):
     assert run(harness, "cheb", Lb, "1e-6") == ["0"]
 
 
-@pytest.mark.parametrize("T,M,rule", [(3600.0, 8, 0), (3600.0, 5, 0), (7200.0, 7, 1), (14400.0, 128, 0)])
+@pytest.mark.parametrize("T,M,rule", [(3600.0, 8, 0), (3600.0, 5, 0), (7200.0, 7, 1), (14400.0, 128, 0),
+                                      (0.0, 4, 0), (0.0, 1, 0)])
 def test_shifts_and_weights_match_oracle(harness, T, M, rule):
+    """Including T = 0: every shift 0, equal weights (the average is N)."""
     out = run(harness, "shifts", repr(T), M, rule)
     assert out[0] == "0"
     sw = np.array([[float(v) for v in line.split()] for line in out[1:]])
     s, w = averaging.shifts_and_weights(T, M, rule)
     assert sw.shape == (M, 2)
-    assert np.abs(sw[:, 0] - s).max() <= 1e-12 * T
+    assert np.abs(sw[:, 0] - s).max() <= 1e-12 * max(T, 1.0)
     assert np.abs(sw[:, 1] - w).max() <= 1e-15
 
 
-@pytest.mark.parametrize("T,M,rule", [(3600.0, 4, 1), (3600.0, 1, 1), (3600.0, 0, 0), (3600.0, 3, 7)])
+@pytest.mark.parametrize("T,M,rule", [(3600.0, 4, 1), (3600.0, 1, 1), (3600.0, 0, 0), (3600.0, 3, 7),
+                                      (-1.0, 4, 0), (float("inf"), 4, 0), (float("nan"), 4, 0)])
 def test_invalid_point_sets_are_refused(harness, T, M, rule):
-    """The closed rule needs an odd M >= 3; M >= 1; the rule must exist."""
+    """The closed rule needs an odd M >= 3; M >= 1; the rule must exist; the
+    window must be finite and non-negative."""
     assert run(harness, "shifts", repr(T), M, rule)[0] != "0"
 
 
