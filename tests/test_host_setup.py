@@ -36,7 +36,7 @@ def run(exe, *args):
     return out.strip().split("\n")
 
 
-@pytest.mark.parametrize("r", [0, 1, 2, 3])
+@pytest.mark.parametrize("r", [0, 1, 2, 3, 4, 5])
 def test_mesh_matches_oracle(harness, tmp_path, r):
     V, F, E = map(int, run(harness, "mesh", r, repr(R), tmp_path / "m")[0].split())
     assert (F, E, V) == (20 * 4 ** r, 30 * 4 ** r, 10 * 4 ** r + 2)
