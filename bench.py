@@ -504,6 +504,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def _workload(cfg):
+    """The evaluated configuration by name, e.g. "averaged_rhs r6 M64 T1h"."""
+    return f"averaged_rhs r{cfg['refinement']} M{cfg['M']} T{cfg['T_s'] / 3600.0:g}h"
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -548,10 +553,11 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": eval_s * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "averaged_rhs r6 M64 T1h (oracle, literal per-shift form)", **cfg},
+            "config": {"workload": f"{_workload(cfg)} (oracle, literal per-shift form)", **cfg},
             "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
-                             "sample": "each step: 2 L-applies and 1 N at refinement 6 timed, scaled by the literal "
-                                       f"form's {n_ops} L-applies and {cfg['M']} N per evaluation"},
+                             "sample": f"each step: 2 L-applies and 1 N at refinement {cfg['refinement']} timed, "
+                                       f"scaled by the literal form's {n_ops} L-applies and {cfg['M']} N per "
+                                       "evaluation"},
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -695,7 +701,7 @@ def run_pavg(args):
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "averaged_rhs r6 M64 T1h FP64 shared-basis", **cfg,
+            "config": {"workload": f"{_workload(cfg)} FP64 shared-basis", **cfg,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "working set ~1.4 GB > L2 (no flush needed)", "rossby": info["rossby"],
                        "K_max": st["last_degree"]},
