@@ -41,13 +41,16 @@ CONFIG = {"refinement": 6, "cells": 81920, "M": 64, "T_s": 3600.0, "state": "har
 PARITY_CASE = {"refinement": 3, "M": 8, "T_s": 3600.0, "lambda_max": 0.00286, "lmax": 8, "seed": 2103}
 
 
-# FP32 ALU peak of GB300 from its unit counts and clock: 152 SMs x 128 FP32
-# lanes x 2 flops (FMA) x 2.07 GHz.  FP64: 1.25 TFLOP/s (nominal).
+# FP32 and FP64 FMA rates measured at the start of the GPU arm
+# (pavg_measure_fma_peak); the unit-count FP32 figure (152 SMs x 128 lanes x 2 x
+# 2.07 GHz) is only the fallback when the measurement fails.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-FP64_PEAK_TFLOPS = 1.25
-# DRAM bytes (read + write) of one k_cg_ir launch at refinement 6, from one ncu
-# capture of the current kernel (profiles/k_cg_ir_r6.md)
-K_CG_IR_DRAM_BYTES_R6 = (206.434304 + 80.506624) * 1e6
+ALU_PEAKS = {}
+# The mass-solve kernel the default context runs, and the DRAM bytes (read +
+# write) of one of its launches from an ncu capture of the current kernel
+# (profiles/), per refinement; absent when the kernel changed since.
+SOLVER_KERNEL = "k_cg_ir (persistent mixed-precision M1 solve: FP32 CG + FP64 residual sweeps)"
+SOLVER_DRAM_BYTES = {(SOLVER_KERNEL, 6): (206.434304 + 80.506624) * 1e6}
 
 
 def _cg_flops(F, n_u, iters, sweeps):
@@ -59,6 +62,13 @@ def _cg_flops(F, n_u, iters, sweeps):
     Per FP64 refinement sweep: the element product (288 per cell) and the
     residual update (6 per velocity DOF)."""
     return iters * 530.0 * F, sweeps * (288.0 * F + 6.0 * n_u)
+
+
+def _cg_bytes(F, n_u, iters, sweeps):
+    """Algorithmic bytes of one mixed-precision M1 solve without cache reuse:
+    per FP32 iteration the packed FP32 element matrices and five FP32 vector
+    passes, per FP64 sweep the packed FP64 matrices and five FP64 passes."""
+    return iters * (78 * 4.0 * F + 5 * 4.0 * n_u) + sweeps * (78 * 8.0 * F + 5 * 8.0 * n_u)
 
 
 def job_throughput(ms_local, steps, dist=None, device="cpu"):
@@ -289,8 +299,8 @@ def _batch_leg(pavg, states):
            "max_rel_l2_vs_single_instance": diff, "first_call_s": first_s, "config": b.config(),
            "forward_chain_ms": fwd, "clenshaw_ms": bwd,
            "roofline": {"bound": "alu", "kernel": "k_chain (persistent recurrences, all instances)",
-                        "achieved": f32 / chain_s / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                        "frac": f32 / chain_s / 1e12 / FP32_PEAK_TFLOPS, "fp64_achieved": f64 / chain_s / 1e12,
+                        "achieved": f32 / chain_s / 1e12, "peak": ALU_PEAKS.get("fp32", FP32_PEAK_TFLOPS),
+                        "unit": "TFLOP/s", "frac": f32 / chain_s / 1e12 / ALU_PEAKS.get("fp32", FP32_PEAK_TFLOPS), "fp64_achieved": f64 / chain_s / 1e12,
                         "note": "FP32 CG flops of every solve in both launches over their summed duration"},
            "K_max": max(m.stats()["last_degree"] for m in ms)}
     b.close()
@@ -378,14 +388,13 @@ def _surrogate_leg(pavg, states):
             ev[1].record()
             torch.cuda.synchronize()
             ms = ev[0].elapsed_time(ev[1]) / 20
-            peak = peaks.get("bf16_tflops", 1900.0) if bf else FP32_PEAK_TFLOPS
+            peak = peaks.get("bf16_tflops", 1900.0) if bf else ALU_PEAKS.get("fp32", FP32_PEAK_TFLOPS)
             mlp[name] = {"ms": ms, "tflops": flop / ms * 1e-9, "frac_of_peak": flop / ms * 1e-9 / peak,
                          "peak_tflops": peak, "io_gbs": io_bytes / ms * 1e-6,
                          "io_frac_of_hbm": io_bytes / ms * 1e-6 / peaks.get("hbm_gbs", 6800.0)}
         mlp["flop_per_apply"] = flop
         mlp["peak_source"] = (("bf16: measured cuBLAS bf16 burst" if "bf16_tflops" in peaks else "bf16: fallback 1.9 PF")
-                              + "; fp32: FP32 ALU from unit counts and clock "
-                              "(152 SMs x 128 lanes x 2 x 2.07 GHz)")
+                              + "; fp32: FMA rate measured in this run (pavg_measure_fma_peak)")
         del vc
         res[f"r{r}"] = {"cells": mr.n_cells, "rel_err_energy_cheap_M8": float(np.mean(e_cheap)),
                         "rel_err_energy_surrogate": float(np.mean(e_sur)),
@@ -400,61 +409,129 @@ def _surrogate_leg(pavg, states):
     return res
 
 
+def _shift_groups_leg(model, cfg, Ud, ms_full, full):
+    """The shift-group partition (Sec. 2.5) emulated on one GPU: each group of
+    G contiguous shift groups timed on its own (CUDA events, graph replays);
+    G ranks would take the slowest group's time plus one reduction.  Also the
+    relative difference of the fixed-order sum of the partials from the whole
+    average."""
+    import torch
+
+    from paper_2103_07706_gb300 import shift_groups
+    T, M = cfg["T_s"], cfg["M"]
+    res = {"full_ms": ms_full}
+    o = torch.empty_like(Ud)
+    for G in (2, 4, 8):
+        times, tot = [], torch.zeros_like(Ud)
+        for m0, m1 in shift_groups.groups(M, G):
+            model.averaged_rhs_group(T, M, m0, m1, Ud, o)  # capture + warm-up
+            tot += o
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                model.averaged_rhs_group(T, M, m0, m1, Ud, o)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 3)
+        model.sync()
+        nu = model.n_u
+        diff = max(float((tot[sl] - full[sl]).norm() / full[sl].norm()) for sl in (slice(0, nu), slice(nu, None)))
+        res[f"G{G}"] = {"group_ms": times, "parallel_ms": max(times), "speedup_vs_one_gpu": ms_full / max(times),
+                        "rel_l2_sum_vs_whole": diff}
+    res["note"] = ("G ranks would each run one group (shared-basis chain of the group's largest degree, its "
+                   "shifts' N) and one all-gather of an n-vector; parallel_ms excludes that exchange")
+    return res
+
+
 # ----------------------------------------------------------------------------- CPU oracle leg
-def _oracle_worker(q, cfg, parity):
-    """Runs in a spawned process (no CUDA): oracle timing sample + parity case."""
+# The oracle's sample at the benchmark configuration: the complete literal
+# terms w_m e^{-s_m L} N(e^{s_m L} U) of the ORACLE_GROUP central shifts
+# (smallest |s_m|, shortest chains), one per worker process in parallel.  The
+# GPU evaluates the same group through pavg_averaged_rhs_group, which gives a
+# parity entry at full size.
+ORACLE_GROUP = (28, 36)
+
+
+def _oracle_term(args):
+    """Forked worker: one complete term of the literal sum, and its wall time."""
+    import oracle.parallel as op
+    from oracle import averaging
+    s, U = args
+    t0 = time.perf_counter()
+    v = averaging.averaged_rhs_term(op._M, s, U)
+    return v, time.perf_counter() - t0
+
+
+def _oracle_master(q_out, q_in, cfg, parity):
+    """Spawned process (no CUDA state): builds the oracle once, then forks its
+    workers from itself so that they share the set-up."""
     try:
         import numpy as np
 
+        import oracle.parallel as op
         from oracle import averaging
         from oracle.model import OracleModel, OracleParams
         from paper_2103_07706_gb300.inputs import harmonic_state
         out = {}
+        try:
+            os.nice(5)
+        except OSError:
+            pass
         # parity case: the small configuration the oracle finishes in seconds
         pm = OracleModel(OracleParams(refinement=parity["refinement"], lambda_max=parity["lambda_max"]))
         U, _ = harmonic_state(pm.mesh.verts, pm.mesh.cells, parity["seed"], parity["lmax"])
-        out["parity_ref"] = pm.averaged_rhs(parity["T_s"], parity["M"], U)
-        out["parity_M1"] = None
-        u = out["parity_ref"][: pm.n_u]
-        e = out["parity_ref"][pm.n_u:]
-        out["parity_norms"] = (float(np.sqrt(u @ (pm.ops.M1 @ u))), float(np.sqrt(e @ (pm.ops.M2 @ e))))
-        out["parity_n_u"] = pm.n_u
-        out["parity_M1_csr"] = (pm.ops.M1.data, pm.ops.M1.indices, pm.ops.M1.indptr)
-        out["parity_M2_csr"] = (pm.ops.M2.data, pm.ops.M2.indices, pm.ops.M2.indptr)
-        # timing sample at the benchmark configuration
+        ref = pm.averaged_rhs(parity["T_s"], parity["M"], U)
+        u, e = ref[: pm.n_u], ref[pm.n_u:]
+        out["parity_small"] = (ref, pm.n_u, float(np.sqrt(u @ (pm.ops.M1 @ u))), float(np.sqrt(e @ (pm.ops.M2 @ e))),
+                               (pm.ops.M1.data, pm.ops.M1.indices, pm.ops.M1.indptr),
+                               (pm.ops.M2.data, pm.ops.M2.indices, pm.ops.M2.indptr))
+        del pm
         t0 = time.time()
         m = OracleModel(OracleParams(refinement=cfg["refinement"], lambda_max=cfg["lambda_max"],
                                      g=cfg["g"], H=cfg["H"], omega=cfg["Omega"], radius=cfg["R"]))
-        out["setup_s"] = time.time() - t0
+        setup_s = time.time() - t0
         U, _ = harmonic_state(m.mesh.verts, m.mesh.cells, 2103, 16)
-        nl = 6
-        t0 = time.perf_counter()
-        V = U
-        for _ in range(nl):
-            V = m.L(V) * (1.0 / cfg["lambda_max"])
-        tL = (time.perf_counter() - t0) / nl
-        t0 = time.perf_counter()
-        m.N(U)
-        tN = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        for _ in range(nl):
-            V = 2.0 * V + U
-        tax = (time.perf_counter() - t0) / nl
+        op._M = m
         s, w = averaging.shifts_and_weights(cfg["T_s"], cfg["M"])
+        m0, m1 = ORACLE_GROUP
         Ks = [m.degree(x) for x in s]
-        # literal form: per shift a forward and a backward chain of K_m L-applies
-        # and K_m vector updates each, one N with its mass solves, one weighted add
-        est = sum(2 * K * (tL + tax) + tN + tax for K in Ks)
-        out["cpu"] = {"value": 1.0 / est, "unit": "evals/s", "cores": 1, "kind": "oracle",
-                      "sample": f"refinement-6 unit costs timed on this host: {nl} L applications "
-                                f"({tL:.3f} s each, sparse-LU mass solve), 1 N ({tN:.2f} s), {nl} vector updates; "
-                                f"scaled by the literal per-shift operation counts (sum_m 2 K_m = {2 * sum(Ks)} "
-                                f"L-applies, {cfg['M']} N) to one evaluation ({est:.0f} s); oracle setup "
-                                f"({out['setup_s']:.0f} s) excluded",
-                      "est_eval_s": est}
-        q.put(out)
+        workers = min(m1 - m0, os.cpu_count() or 1)
+        order = sorted(range(m0, m1), key=lambda k: -Ks[k])
+        with mp.get_context("fork").Pool(workers) as pool:
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_term, [(s[k], U) for k in order], chunksize=1)
+            wall = time.perf_counter() - t0
+        terms = dict(zip(order, res))
+        part = np.zeros_like(U)
+        for k in range(m0, m1):
+            part += w[k] * terms[k][0]
+        # per-term cost model 2 K_m a + b (a: one L application and a vector
+        # update, b: one N with its mass solves), least squares over the sample
+        A = np.array([[2.0 * Ks[k], 1.0] for k in range(m0, m1)])
+        t = np.array([terms[k][1] for k in range(m0, m1)])
+        (a, b), *_ = np.linalg.lstsq(A, t, rcond=None)
+        eval_s = sum(2.0 * K * a + b for K in Ks) / workers   # the whole sum, balanced over the same workers
+        out["cpu"] = {"value": 1.0 / eval_s, "unit": "evals/s", "cores": workers, "kind": "oracle",
+                      "sample": f"complete literal terms e^(-s_m L) N(e^(s_m L) U) of the {m1 - m0} central shifts "
+                                f"m = {m0}..{m1 - 1} of the refinement-6, M = {cfg['M']}, T = 1 h sum "
+                                f"(K_m = {min(Ks[m0:m1])}..{max(Ks[m0:m1])}), one per worker process on {workers} "
+                                f"host cores, {wall:.1f} s wall; per-term times fit 2 K_m x {a:.3f} s + {b:.2f} s, "
+                                f"scaled to all {cfg['M']} terms (sum_m 2 K_m = {2 * sum(Ks)} L applications) "
+                                f"balanced over the same cores: {eval_s:.0f} s per evaluation; oracle set-up "
+                                f"({setup_s:.0f} s, once) excluded",
+                      "sample_wall_s": wall, "est_eval_s": eval_s, "t_L_s": float(a), "t_N_s": float(b)}
+        q_out.put(out)
+        # the parent sends its GPU result of the same group; the FE norms need M1, M2
+        got = q_in.get(timeout=3600)
+        d = got - part
+        nu = m.n_u
+        M1, M2 = m.ops.M1, m.ops.M2
+        q_out.put({"rel_l2_u_M1": float(np.sqrt(d[:nu] @ (M1 @ d[:nu])) / np.sqrt(part[:nu] @ (M1 @ part[:nu]))),
+                   "rel_l2_eta_M2": float(np.sqrt(d[nu:] @ (M2 @ d[nu:])) / np.sqrt(part[nu:] @ (M2 @ part[nu:])))})
     except Exception as e:  # pragma: no cover - reported in the JSON line
-        q.put({"error": repr(e)})
+        import traceback
+        q_out.put({"error": repr(e) + traceback.format_exc()[-400:]})
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -518,12 +595,26 @@ def _peaks():
 
 
 # ----------------------------------------------------------------------------- reference arm
+def _ref_sample(_):
+    """Forked worker of the reference arm: two L applications and one N."""
+    import oracle.parallel as op
+    m, U = op._M, op._U
+    t0 = time.perf_counter()
+    V = m.L(U)
+    m.L(V)
+    t1 = time.perf_counter()
+    m.N(U)
+    t2 = time.perf_counter()
+    return (t1 - t0) / 2.0, t2 - t1
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import numpy as np  # noqa: F401
 
+    import oracle.parallel as op
     from oracle import averaging
     from oracle.model import OracleModel, OracleParams
     from paper_2103_07706_gb300.inputs import harmonic_state
@@ -534,30 +625,33 @@ def run_reference(args):
     s, w = averaging.shifts_and_weights(cfg["T_s"], cfg["M"])
     Ks = [m.degree(x) for x in s]
     n_ops = sum(2 * K for K in Ks)
-
-    def sample():
-        # one step: 2 L-applies and one N of the literal form, scaled to an evaluation
-        t0 = time.perf_counter()
-        V = m.L(U)
-        V = m.L(V)
-        t1 = time.perf_counter()
-        m.N(U)
-        t2 = time.perf_counter()
-        return (t1 - t0) / 2.0 * n_ops + (t2 - t1) * cfg["M"]
-
-    for _ in range(args.warmup):
-        sample()
-    est = [sample() for _ in range(args.steps)]
-    eval_s = statistics.mean(est)
+    op._M, op._U = m, U
+    workers = max(1, min(16, os.cpu_count() or 1))
+    walls, tl, tn = [], [], []
+    # this process never touches CUDA, so its workers may be forked (they share the set-up)
+    with mp.get_context("fork").Pool(workers) as pool:
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            res = pool.map(_ref_sample, range(workers), chunksize=1)
+            if i >= args.warmup:
+                walls.append(time.perf_counter() - t0)
+                tl += [r[0] for r in res]
+                tn += [r[1] for r in res]
+    t_L, t_N = statistics.mean(tl), statistics.mean(tn)
+    eval_s = (n_ops * t_L + cfg["M"] * t_N) / workers
     value = 1.0 / eval_s
+    step_ms = statistics.mean(walls) * 1e3
+    sample = (f"each step: 2 L applications and 1 N at refinement {cfg['refinement']} in each of {workers} worker "
+              f"processes at once ({step_ms / 1e3:.1f} s wall; L {t_L:.2f} s, N {t_N:.2f} s per core under full "
+              f"load), scaled by the literal form's {n_ops} L applications and {cfg['M']} N per evaluation, "
+              f"balanced over the {workers} cores: {eval_s:.0f} s per evaluation")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": eval_s * 1e3, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"{_workload(cfg)} (oracle, literal per-shift form)", **cfg},
-            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
-                             "sample": f"each step: 2 L-applies and 1 N at refinement {cfg['refinement']} timed, "
-                                       f"scaled by the literal form's {n_ops} L-applies and {cfg['M']} N per "
-                                       "evaluation"},
+            "ms_per_step_is": "the measured wall time of one sample step (not of an evaluation)",
+            "est_eval_s": eval_s,
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": workers, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -578,6 +672,11 @@ def run_pavg(args):
     from paper_2103_07706_gb300.inputs import harmonic_state
 
     torch.cuda.set_device(local)
+    for key, fp64 in (("fp32", False), ("fp64", True)):
+        try:
+            ALU_PEAKS[key] = pavg.measure_fma_peak(fp64)
+        except Exception:
+            pass
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -588,11 +687,11 @@ def run_pavg(args):
         states = _make_states(pavg, jobs)
         nb = len(_batch_jobs()) if "batch" in legs else 0
         batch_states, sur_states = states[:nb], states[nb:]
-    q = proc = None
-    if want_cpu:  # a spawned process (no CUDA state is inherited), timed on one host core
+    q = q_in = proc = None
+    if want_cpu:  # a spawned process (no CUDA state is inherited); it forks its own workers
         ctxmp = mp.get_context("spawn")
-        q = ctxmp.Queue()
-        proc = ctxmp.Process(target=_oracle_worker, args=(q, CONFIG, PARITY_CASE), daemon=True)
+        q, q_in = ctxmp.Queue(), ctxmp.Queue()
+        proc = ctxmp.Process(target=_oracle_master, args=(q, q_in, CONFIG, PARITY_CASE))
         proc.start()
     cfg = CONFIG
     model = pavg.Model(cfg["refinement"], lambda_max=cfg["lambda_max"], g=cfg["g"], H=cfg["H"], omega=cfg["Omega"],
@@ -653,13 +752,14 @@ def run_pavg(args):
     days = _precision_days(pavg, cfg, U, args.days) if "precision_days" in legs else None
     day_r5 = _day_r5(pavg) if "day_r5" in legs else None
     surrogate = _surrogate_leg(pavg, sur_states) if "surrogate" in legs else None
+    groups = _shift_groups_leg(model, cfg, Ud, ms / args.steps, out) if "groups" in legs else None
 
-    # parity of the small configuration against the oracle (computed by the spawned leg)
+    # parity against the oracle (computed by the spawned leg): the small
+    # configuration in full, and the central shift group at the benchmark size
     cpu = None
     parity = None
     if proc is not None:
-        res = q.get(timeout=1800)
-        proc.join(timeout=60)
+        res = q.get(timeout=3600)
         if "error" in res:
             cpu = {"error": res["error"]}
         else:
@@ -670,16 +770,24 @@ def run_pavg(args):
             Up, _ = harmonic_state(pv, pc, PARITY_CASE["seed"], PARITY_CASE["lmax"])
             got = pm.averaged_rhs(PARITY_CASE["T_s"], PARITY_CASE["M"], torch.from_numpy(Up).cuda()).cpu().numpy()
             pm.sync()
-            ref = res["parity_ref"]
-            nu = res["parity_n_u"]
-            M1 = sp.csr_matrix(res["parity_M1_csr"], shape=(nu, nu))
+            ref, nu, n_u_ref, n_e_ref, M1c, M2c = res["parity_small"]
+            M1 = sp.csr_matrix(M1c, shape=(nu, nu))
             ne = len(ref) - nu
-            M2 = sp.csr_matrix(res["parity_M2_csr"], shape=(ne, ne))
+            M2 = sp.csr_matrix(M2c, shape=(ne, ne))
             du, de = got[:nu] - ref[:nu], got[nu:] - ref[nu:]
-            parity = {"case": "refinement 3, M=8, T=1h, harmonic l<=8 seed 2103",
-                      "rel_l2_u_M1": float(np.sqrt(du @ (M1 @ du))) / res["parity_norms"][0],
-                      "rel_l2_eta_M2": float(np.sqrt(de @ (M2 @ de))) / res["parity_norms"][1]}
+            parity = {"small": {"case": "refinement 3, M=8, T=1h, harmonic l<=8 seed 2103, whole average",
+                                "rel_l2_u_M1": float(np.sqrt(du @ (M1 @ du))) / n_u_ref,
+                                "rel_l2_eta_M2": float(np.sqrt(de @ (M2 @ de))) / n_e_ref}}
             pm.close()
+            m0, m1 = ORACLE_GROUP
+            gpart = model.averaged_rhs_group(T, M, m0, m1, Ud).cpu().numpy()
+            model.sync()
+            q_in.put(gpart)
+            r6 = q.get(timeout=3600)
+            parity["benchmark_size"] = {"case": f"{_workload(cfg)}, harmonic l<=16 seed 2103: partial sum of the "
+                                                f"shifts m = {m0}..{m1 - 1} (pavg_averaged_rhs_group vs the "
+                                                "oracle's literal terms)", **r6}
+        proc.join(timeout=120)
 
     peaks = _peaks()
     F, n_u = model.n_cells, model.n_u
@@ -687,17 +795,28 @@ def run_pavg(args):
     roof = None
     if cg_n > 0:
         dur_s = cg_ms / cg_n / 1e3
-        f32, f64 = _cg_flops(F, n_u, iters, st["cg_sweeps_mean"])
-        achieved = f32 / dur_s / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS,
-                "traffic": K_CG_IR_DRAM_BYTES_R6 if cfg["refinement"] == 6 else None,
-                "kernel": "k_cg_ir (persistent mixed-precision M1 solve: FP32 CG + FP64 residual sweeps)",
-                "fp64_achieved": f64 / dur_s / 1e12, "fp64_peak": FP64_PEAK_TFLOPS,
+        sweeps = st["cg_sweeps_mean"]
+        f32, f64 = _cg_flops(F, n_u, iters, sweeps)
+        alg = _cg_bytes(F, n_u, iters, sweeps)
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        achieved = alg / dur_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": SOLVER_DRAM_BYTES.get((SOLVER_KERNEL, cfg["refinement"])),
+                "kernel": SOLVER_KERNEL, "algorithmic_bytes_per_launch": alg,
+                "bytes_rule": "per FP32 iteration the packed FP32 element matrices (78 x 4 B per cell) and five "
+                              "FP32 vector passes (5 x 4 B per velocity DOF); per FP64 refinement sweep the packed "
+                              "FP64 matrices (78 x 8 B per cell) and five FP64 vector passes; no cache reuse",
+                "peak_source": "measured HBM copy bandwidth (MEASURED_PEAKS.json)" if "hbm_gbs" in peaks
+                               else "fallback 6.8 TB/s",
+                "alu": {"fp32_achieved_tflops": f32 / dur_s / 1e12, "fp32_peak_tflops": ALU_PEAKS.get("fp32"),
+                        "fp32_frac": f32 / dur_s / 1e12 / ALU_PEAKS["fp32"] if ALU_PEAKS.get("fp32") else None,
+                        "fp64_achieved_tflops": f64 / dur_s / 1e12, "fp64_peak_tflops": ALU_PEAKS.get("fp64"),
+                        "fp64_frac": f64 / dur_s / 1e12 / ALU_PEAKS["fp64"] if ALU_PEAKS.get("fp64") else None,
+                        "peak_source": "measured in this run: independent FMA chains on every SM "
+                                       "(pavg_measure_fma_peak), best of five"},
                 "launch_ms": cg_ms / cg_n, "launches_per_step": cg_n, "iters_per_launch": iters,
-                "sweeps_per_launch": st["cg_sweeps_mean"], "share_of_step": cg_ms / (ms / args.steps),
-                "peak_source": "FP32 ALU from unit counts and clock (152 SMs x 128 lanes x 2 x 2.07 GHz)",
-                "note": "latency-bound: one grid-synchronised phase per CG iteration"}
+                "sweeps_per_launch": sweeps, "share_of_step": cg_ms / (ms / args.steps),
+                "note": "latency-bound: one synchronised phase per inner iteration"}
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -709,8 +828,10 @@ def run_pavg(args):
                     "d2h_bytes_per_step": 8 * model.n},
             "gpu_launches": st["kernel_launches"] * args.steps,
             "roofline": roof, "cpu_baseline": cpu, "parity": parity, "precision_mixed": mixed, "literal": literal, "precision_days": days, "day_r5": day_r5, "batch": batch, "surrogate": surrogate,
+            "shift_groups": groups,
             "clocks": clk,
             "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
+            "alu_peaks_measured_tflops": ALU_PEAKS,
             "error_flags": st["error_flags"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -728,8 +849,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-n", type=int, default=None, help="instances of the batched leg (profiling only)")
     ap.add_argument("--batch-max-r", type=int, default=None, help="largest refinement of the batched leg (profiling only)")
-    ap.add_argument("--legs", default="fp64,mixed,literal,batch,surrogate",
-                    help="comma list: fp64 (always), mixed, literal, batch, surrogate, precision_days, "
+    ap.add_argument("--legs", default="fp64,mixed,literal,batch,surrogate,groups",
+                    help="comma list: fp64 (always), mixed, literal, batch, surrogate, groups, precision_days, "
                          "day_r5 (single GPU only)")
     ap.add_argument("--days", type=float, default=1.0, help="simulated days of the precision_days leg")
     ap.add_argument("--refinement", type=int, default=None, help="smaller case (profiling only)")

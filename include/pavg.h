@@ -142,6 +142,20 @@ int pavg_expL_apply(pavg_ctx* ctx, double t, const double* U, double* out, int B
  * PAVG_MAX_CHEB_ARG (the widest shift's exponential). */
 int pavg_averaged_rhs(pavg_ctx* ctx, double T, int M, const double* U, double* out, void* stream);
 
+/* Part of N-bar(U): the terms of the shifts m0 <= m < m1 of the M-point rule,
+ *   out = sum_{m0 <= m < m1} w_m e^{-s_m L} N(e^{s_m L} U),
+ * with the weights w_m of the whole rule (normalised over all M shifts), so
+ * that the partial sums of any partition of 0..M-1 into groups add up to
+ * pavg_averaged_rhs(T, M).  This is the paper's parallel decomposition: the
+ * Riemann terms are independent and are distributed over groups of processes
+ * whose partial sums are reduced once (Sec. 2.5, last paragraph; Sec. 2.2).
+ * Evaluated in the shared-basis form restricted to the group: one Chebyshev
+ * chain of degree max_{m in group} K_m, so a group of small |s_m| has a
+ * short chain.  With T = 0 every weight is 1/M and out = (m1 - m0)/M N(U).
+ * INVAL unless 0 <= m0 < m1 <= M, and under pavg_averaged_rhs's limits. */
+int pavg_averaged_rhs_group(pavg_ctx* ctx, double T, int M, int m0, int m1, const double* U, double* out,
+                            void* stream);
+
 /* The same sum in its literal form: for each shift its own forward exponential,
  * N with its mass solves and backward exponential, summed in shift order. */
 int pavg_averaged_rhs_literal(pavg_ctx* ctx, double T, int M, const double* U, double* out,
@@ -150,25 +164,38 @@ int pavg_averaged_rhs_literal(pavg_ctx* ctx, double T, int M, const double* U, d
 /* nsteps averaged Lawson RK4 steps of size dt (Sec. 2.3, Eqs. stage1_c to stage4),
  * in place on the device state U_inout (n doubles).  INVAL for a
  * non-finite dt or T, for lambda_max |dt| > PAVG_MAX_CHEB_ARG (each step
- * applies e^{dt L}), and under pavg_averaged_rhs's limits on T and M. */
+ * applies e^{dt L}), and under pavg_averaged_rhs's limits on T and M.
+ * Asynchronous on `stream` like the other state calls (no synchronisation,
+ * no allocation per step): the seven stage vectors of a step are context
+ * workspace, allocated by the first call (NOMEM if that fails). */
 int pavg_timestep(pavg_ctx* ctx, double dt, double T, int M, double* U_inout, int nsteps,
                   void* stream);
 
-/* LU = L U for ONE state (device, n doubles each; may not alias), the same
- * result as pavg_linear with B = 1, computed without any device allocation:
- * all scratch (assembled right-hand side, conjugate-gradient work vectors)
- * comes from a file-scope device array of the library sized for at most
- * 153600 velocity DOFs (refinement <= 5, about 12.5 MB, held by every GPU that
- * loads the library until the process exits).  It is for callers that cannot
- * call cudaMalloc where they apply L (inside a global-mode stream capture,
- * real-time loops, capped external memory pools).  The paper has no
- * counterpart: this is an interface convenience.
+/* LU = L U for ONE state (device, n doubles each; may not alias), computed
+ * without any device allocation: all scratch (assembled right-hand side,
+ * conjugate-gradient work vectors) comes from a file-scope device array of the
+ * library sized for at most 153600 velocity DOFs (refinement <= 5, about
+ * 12.5 MB, held by every GPU that loads the library until the process exits).
+ * It is for callers that cannot call cudaMalloc where they apply L (inside a
+ * global-mode stream capture, real-time loops, capped external memory pools).
+ * The paper has no counterpart: this is an interface convenience.
+ * Solver: always the FP64 Jacobi CG on M1 to the context's mass-solve
+ * tolerance, whatever the context's `solver` setting.  With PAVG_PRECISION_FP64
+ * that tolerance is cg_rtol (1e-14 by default) and the result equals
+ * pavg_linear's to about 1e-13; with PAVG_PRECISION_MIXED both solves stop at
+ * a relative residual of 1e-5 and the two results agree to about that level.
  * Errors: INVAL for a null argument, a mesh larger than the limit or when the
  * context's device is not current; CUDA when the set-up lookup fails.  The
  * first call on each device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and caches it for the life of the process; make that
+ * first call before any stream capture.  The cached address dies with the
+ * device's primary context: after cudaDeviceReset no pavg call may be made
+ * (contexts must be destroyed before a reset in any case).
  * Every call shares the one array, so calls that overlap on the GPU race;
- * serialise them (one stream, or events). */
+ * serialise them (one stream, or events).  As for the other state calls, a
+ * device-side failure (iteration cap, non-finite value, a bounded wait that
+ * gave up, or a failure latched by an earlier call on the context) is reported
+ * by the next pavg_sync: LU is valid only once pavg_sync returns PAVG_OK. */
 int pavg_linear_noalloc(pavg_ctx* ctx, const double* U, double* LU, void* stream);
 
 /* Wait for the context's work on `stream` and report latched device errors. */
@@ -190,6 +217,13 @@ int pavg_get_stats(pavg_ctx* ctx, pavg_stats* out);
 
 /* Clear the latched device error flags and the CG counters. */
 int pavg_reset_stats(pavg_ctx* ctx);
+
+/* Measurement aid: the current device's fused multiply-add rate in TFLOP/s
+ * (fp64 != 0: FP64, else FP32), from a kernel of independent FMA chains on
+ * every SM timed with CUDA events on `stream` (best of five launches after a
+ * warm-up; synchronises; allocates a few KB).  The paper has no counterpart:
+ * the benchmark uses it as the peak of ALU-bound kernels. */
+int pavg_measure_fma_peak(int fp64, double* tflops, void* stream);
 
 /* Measurement aid: when enabled, every M1 CG launch (the dominant kernel) is
  * bracketed by CUDA events on its stream, also inside captured graphs (plans

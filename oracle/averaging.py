@@ -67,6 +67,21 @@ def averaged_rhs(model, T, M, U, rule=QUAD_MIDPOINT):
     return out
 
 
+def averaged_rhs_group(model, T, M, m0, m1, U, rule=QUAD_MIDPOINT):
+    """The terms m0 <= m < m1 of the M-point sum, with the whole rule's weights
+    (the paper distributes the independent terms over process groups and
+    reduces their partial sums once, Sec. 2.5)."""
+    s, w = shifts_and_weights(T, M, rule)
+    if T == 0.0:
+        return (m1 - m0) / M * model.N(U)
+    out = np.zeros_like(U)
+    for m in range(m0, m1):
+        if w[m] == 0.0:
+            continue
+        out += w[m] * model.expL(-s[m], model.N(model.expL(s[m], U)))
+    return out
+
+
 def averaged_rhs_term(model, s, U):
     """One term e^{-sL} N(e^{sL} U) of the sum (unweighted)."""
     return model.expL(-s, model.N(model.expL(s, U)))

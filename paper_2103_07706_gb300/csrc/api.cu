@@ -190,13 +190,18 @@ int ensure_avg_workspace(pavg_ctx* ctx, int K, int M) {
   return PAVG_OK;
 }
 
-int get_plan(pavg_ctx* ctx, double T, int M, AvgPlan** out) {
-  auto key = std::make_pair(T, M);
+int get_plan(pavg_ctx* ctx, double T, int M, AvgPlan** out, int m0, int m1) {
+  if (m1 < 0) m1 = M;
+  if (M < 1 || m0 < 0 || m1 > M || m0 >= m1) return set_err(ctx, PAVG_ERR_INVAL, "invalid shift group");
+  auto key = std::make_tuple(T, M, m0, m1);
   auto it = ctx->plans.find(key);
   if (it != ctx->plans.end()) { *out = &it->second; return PAVG_OK; }
-  std::vector<double> s, w;
-  int rc = shifts_weights(T, M, ctx->p.quad_rule, &s, &w);
+  std::vector<double> s_all, w_all;
+  int rc = shifts_weights(T, M, ctx->p.quad_rule, &s_all, &w_all);
   if (rc) return set_err(ctx, rc, "invalid T / M / quadrature rule");
+  const std::vector<double> s(s_all.begin() + m0, s_all.begin() + m1), w(w_all.begin() + m0, w_all.begin() + m1);
+  const int Mrule = M;
+  M = m1 - m0;
   std::vector<std::vector<double>> cs(M);
   int K = 0;
   for (int m = 0; m < M; ++m) {
@@ -205,7 +210,7 @@ int get_plan(pavg_ctx* ctx, double T, int M, AvgPlan** out) {
     K = std::max(K, (int)cs[m].size() - 1);
   }
   AvgPlan pl;
-  pl.T = T; pl.M = M; pl.K = K;
+  pl.T = T; pl.M = M; pl.K = K; pl.M_rule = Mrule; pl.m0 = m0;
   // Shifts ordered by decreasing degree K_m: each 8-row tile of the forward
   // table then uses a prefix of the k range, and each 8-row tile of the
   // backward table a prefix of the shifts; the contractions skip the zeros.
@@ -269,7 +274,12 @@ int enq_avg(pavg_ctx* ctx, const AvgPlan& pl, const double* U, double* out, cuda
   const DeviceMesh& m = ctx->dm;
   const int64_t n = m.n;
   const int K = pl.K;
-  if (pl.T == 0.0) return enq_nonlinear(ctx, U, out, ctx->Rm, st);
+  if (pl.T == 0.0) {  // every weight is 1/M: the group's share of N(U)
+    int rc = enq_nonlinear(ctx, U, out, ctx->Rm, st);
+    if (rc || pl.M == pl.M_rule) return rc;
+    KL(launch_lincomb(out, (double)pl.M / pl.M_rule, out, 0.0, nullptr, 0.0, nullptr, n, st));
+    return PAVG_OK;
+  }
   double* Q = ctx->Q;
   CK(cudaMemcpyAsync(Q, U, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   for (int k = 0; k < K; ++k) {
@@ -295,11 +305,11 @@ int enq_avg(pavg_ctx* ctx, const AvgPlan& pl, const double* U, double* out, cuda
   return PAVG_OK;
 }
 
-int run_avg(pavg_ctx* ctx, double T, int M, const double* U, double* out, cudaStream_t st) {
+int run_avg(pavg_ctx* ctx, double T, int M, const double* U, double* out, cudaStream_t st, int m0, int m1) {
   AvgPlan* pl = nullptr;
-  int rc = get_plan(ctx, T, M, &pl);
+  int rc = get_plan(ctx, T, M, &pl, m0, m1);
   if (rc) return rc;
-  rc = ensure_avg_workspace(ctx, pl->K, M);
+  rc = ensure_avg_workspace(ctx, pl->K, pl->M);
   if (rc) return rc;
   const int64_t n = ctx->dm.n;
   if (!ctx->use_graphs) return enq_avg(ctx, *pl, U, out, st);
@@ -483,6 +493,7 @@ void free_ctx(pavg_ctx* c) {
   cudaFree(c->facets);
   for (auto* v : c->vec) cudaFree(v);
   cudaFree(c->io_in); cudaFree(c->io_out); cudaFree(c->Q); cudaFree(c->Um); cudaFree(c->Rm);
+  cudaFree(c->ts);
   cudaFree(c->dpart);
   if (c->host_part) cudaFreeHost(c->host_part);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -704,6 +715,15 @@ int pavg_averaged_rhs(pavg_ctx* ctx, double T, int M, const double* U, double* o
   return run_avg(ctx, T, M, U, out, S(stream));
 }
 
+int pavg_averaged_rhs_group(pavg_ctx* ctx, double T, int M, int m0, int m1, const double* U, double* out,
+                            void* stream) {
+  if (!ctx || !U || !out || M < 1 || !(T >= 0) || !std::isfinite(T)) return PAVG_ERR_INVAL;
+  if (m0 < 0 || m1 > M || m0 >= m1) return set_err(ctx, PAVG_ERR_INVAL, "pavg_averaged_rhs_group: need 0 <= m0 < m1 <= M");
+  if (out == U) return set_err(ctx, PAVG_ERR_INVAL, "pavg_averaged_rhs_group: the output aliases the input");
+  CallScope scope_(ctx);
+  return run_avg(ctx, T, M, U, out, S(stream), m0, m1);
+}
+
 int pavg_averaged_rhs_literal(pavg_ctx* ctx, double T, int M, const double* U, double* out, void* stream) {
   if (!ctx || !U || !out || M < 1 || !(T >= 0) || !std::isfinite(T)) return PAVG_ERR_INVAL;
   if (out == U) return set_err(ctx, PAVG_ERR_INVAL, "pavg_averaged_rhs_literal: the output aliases the input");
@@ -747,41 +767,32 @@ int pavg_timestep(pavg_ctx* ctx, double dt, double T, int M, double* U, int nste
   if (rc) return rc;
   rc = ensure_avg_workspace(ctx, pl->K, M);
   if (rc) return rc;
-  // stage vectors live in the Rm workspace when it is large enough, else extra buffers
-  static_assert(sizeof(double) == 8, "");
-  double *k1, *k2, *k3, *k4, *EhU, *tmp, *tmp2;
-  std::vector<double*> own;
-  auto getbuf = [&](double** p) -> bool {
-    double* b = nullptr;
-    if (cudaMalloc((void**)&b, sizeof(double) * n) != cudaSuccess) return false;
-    own.push_back(b);
-    *p = b;
-    return true;
-  };
-  if (!(getbuf(&k1) && getbuf(&k2) && getbuf(&k3) && getbuf(&k4) && getbuf(&EhU) && getbuf(&tmp) && getbuf(&tmp2))) {
-    for (auto* b : own) cudaFree(b);
-    return set_err(ctx, PAVG_ERR_NOMEM, "timestep buffers");
+  // stage vectors: context workspace, allocated once by the first call
+  if (!ctx->ts && dalloc(&ctx->ts, (size_t)7 * n) != cudaSuccess) {
+    ctx->ts = nullptr;
+    return set_err(ctx, PAVG_ERR_NOMEM, "timestep workspace allocation failed");
   }
-  auto fin = [&](int code) { cudaStreamSynchronize(st); for (auto* b : own) cudaFree(b); return code; };
+  double* k1 = ctx->ts;
+  double *k2 = k1 + n, *k3 = k2 + n, *k4 = k3 + n, *EhU = k4 + n, *tmp = EhU + n, *tmp2 = tmp + n;
   for (int step = 0; step < nsteps; ++step) {
-    if ((rc = run_avg(ctx, T, M, U, k1, st))) return fin(rc);
-    if ((rc = enq_expL(ctx, 0.5 * dt, U, EhU, st))) return fin(rc);
-    if (launch_lincomb(tmp, 1.0, U, 0.5 * dt, k1, 0, nullptr, n, st) != cudaSuccess) return fin(PAVG_ERR_CUDA);
-    if ((rc = enq_expL(ctx, 0.5 * dt, tmp, tmp2, st))) return fin(rc);
-    if ((rc = run_avg(ctx, T, M, tmp2, k2, st))) return fin(rc);
-    if (launch_lincomb(tmp, 1.0, EhU, 0.5 * dt, k2, 0, nullptr, n, st) != cudaSuccess) return fin(PAVG_ERR_CUDA);
-    if ((rc = run_avg(ctx, T, M, tmp, k3, st))) return fin(rc);
-    if (launch_lincomb(tmp, 1.0, EhU, dt, k3, 0, nullptr, n, st) != cudaSuccess) return fin(PAVG_ERR_CUDA);
-    if ((rc = enq_expL(ctx, 0.5 * dt, tmp, tmp2, st))) return fin(rc);
-    if ((rc = run_avg(ctx, T, M, tmp2, k4, st))) return fin(rc);
+    if ((rc = run_avg(ctx, T, M, U, k1, st))) return rc;
+    if ((rc = enq_expL(ctx, 0.5 * dt, U, EhU, st))) return rc;
+    if (launch_lincomb(tmp, 1.0, U, 0.5 * dt, k1, 0, nullptr, n, st) != cudaSuccess) return PAVG_ERR_CUDA;
+    if ((rc = enq_expL(ctx, 0.5 * dt, tmp, tmp2, st))) return rc;
+    if ((rc = run_avg(ctx, T, M, tmp2, k2, st))) return rc;
+    if (launch_lincomb(tmp, 1.0, EhU, 0.5 * dt, k2, 0, nullptr, n, st) != cudaSuccess) return PAVG_ERR_CUDA;
+    if ((rc = run_avg(ctx, T, M, tmp, k3, st))) return rc;
+    if (launch_lincomb(tmp, 1.0, EhU, dt, k3, 0, nullptr, n, st) != cudaSuccess) return PAVG_ERR_CUDA;
+    if ((rc = enq_expL(ctx, 0.5 * dt, tmp, tmp2, st))) return rc;
+    if ((rc = run_avg(ctx, T, M, tmp2, k4, st))) return rc;
     // U+ = E(dt)(U + dt/6 k1) + dt/6 [2 E(dt/2)(k2 + k3) + k4]
-    if (launch_lincomb(tmp, 1.0, k2, 1.0, k3, 0, nullptr, n, st) != cudaSuccess) return fin(PAVG_ERR_CUDA);
-    if ((rc = enq_expL(ctx, 0.5 * dt, tmp, tmp2, st))) return fin(rc);
-    if (launch_lincomb(tmp, 1.0, U, dt / 6.0, k1, 0, nullptr, n, st) != cudaSuccess) return fin(PAVG_ERR_CUDA);
-    if ((rc = enq_expL(ctx, dt, tmp, EhU, st))) return fin(rc);
-    if (launch_lincomb(U, 1.0, EhU, dt / 3.0, tmp2, dt / 6.0, k4, n, st) != cudaSuccess) return fin(PAVG_ERR_CUDA);
+    if (launch_lincomb(tmp, 1.0, k2, 1.0, k3, 0, nullptr, n, st) != cudaSuccess) return PAVG_ERR_CUDA;
+    if ((rc = enq_expL(ctx, 0.5 * dt, tmp, tmp2, st))) return rc;
+    if (launch_lincomb(tmp, 1.0, U, dt / 6.0, k1, 0, nullptr, n, st) != cudaSuccess) return PAVG_ERR_CUDA;
+    if ((rc = enq_expL(ctx, dt, tmp, EhU, st))) return rc;
+    if (launch_lincomb(U, 1.0, EhU, dt / 3.0, tmp2, dt / 6.0, k4, n, st) != cudaSuccess) return PAVG_ERR_CUDA;
   }
-  return fin(PAVG_OK);
+  return PAVG_OK;
 }
 
 int pavg_sync(pavg_ctx* ctx, void* stream) {

@@ -50,15 +50,18 @@ cudaError_t upload(T** p, const std::vector<T>& v) {
 int enq_nonlinear(pavg_ctx* ctx, const double* U, double* out, double* scratch, cudaStream_t st);
 // Workspace of the shared-basis average for degree K and M shifts.
 int ensure_avg_workspace(pavg_ctx* ctx, int K, int M);
-// Shifts, weights, coefficient tables of (T, M), cached on the context.
-int get_plan(pavg_ctx* ctx, double T, int M, AvgPlan** out);
+// Shifts, weights, coefficient tables of (T, M), cached on the context; with
+// 0 <= m0 < m1 <= M only the shifts m0 .. m1-1 of the M-point rule (their
+// weights normalised over all M), m1 < 0 meaning M.
+int get_plan(pavg_ctx* ctx, double T, int M, AvgPlan** out, int m0 = 0, int m1 = -1);
 // Middle of the shared-basis average: U_m = sum_k A[m][k] Q_k, r_m = N(U_m)
 // (weak form), y_k = sum_m B[k][m] r_m written over Q_k.
 int enq_avg_shifts(pavg_ctx* ctx, const AvgPlan& pl, cudaStream_t st);
 // Energy inner product <U, V>_W = H u^T M1 v + g eta^T M2 zeta (synchronous, legacy stream).
 double host_winner(pavg_ctx* ctx, const double* U, const double* V);
 // The shared-basis average through the context's cached graph.
-int run_avg(pavg_ctx* ctx, double T, int M, const double* U, double* out, cudaStream_t st);
+int run_avg(pavg_ctx* ctx, double T, int M, const double* U, double* out, cudaStream_t st, int m0 = 0,
+            int m1 = -1);
 // Error flags latched on the device, as a return code.
 int check_flags(pavg_ctx* ctx);
 

@@ -18,7 +18,9 @@ using EventPair = std::pair<cudaEvent_t, cudaEvent_t>;
 
 struct AvgPlan {
   double T = 0;
-  int M = 0;
+  int M = 0;                 // shifts in the plan (m1 - m0)
+  int M_rule = 0;            // points of the quadrature rule the shifts come from
+  int m0 = 0;                // first shift of the rule in the plan
   int K = 0;                 // K_max over shifts
   double* dA = nullptr;      // [M][K+1]  forward combine
   double* dB = nullptr;      // [K+1][M]  backward combine
@@ -67,10 +69,11 @@ struct pavg_ctx {
   double* Um = nullptr;         // [Mcap][n] shifted states
   double* Rm = nullptr;         // [Mcap][n] weak-form N of the shifted states
   int Kcap = -1, Mcap = 0;
+  double* ts = nullptr;         // [7][n] Lawson RK4 stage vectors, allocated by the first pavg_timestep
   double* host_part = nullptr;
   double* dpart = nullptr;
   cudaStream_t cap_stream = nullptr;
-  std::map<std::pair<double, int>, AvgPlan> plans;
+  std::map<std::tuple<double, int, int, int>, AvgPlan> plans;  // (T, M, m0, m1)
   int last_degree = 0;
   bool use_graphs = true;
   std::string err;

@@ -33,8 +33,8 @@ ERRORS = {
 EXPORTED = [
     "pavg_default_params", "pavg_create", "pavg_destroy", "pavg_sizes", "pavg_mesh_export",
     "pavg_set_topography", "pavg_lambda_max", "pavg_linear", "pavg_nonlinear", "pavg_expL_apply",
-    "pavg_averaged_rhs", "pavg_averaged_rhs_literal", "pavg_timestep", "pavg_sync", "pavg_get_stats",
-    "pavg_reset_stats", "pavg_last_error", "pavg_kernel_timing", "pavg_kernel_time", "pavg_linear_noalloc",
+    "pavg_averaged_rhs", "pavg_averaged_rhs_group", "pavg_averaged_rhs_literal", "pavg_timestep", "pavg_sync", "pavg_get_stats",
+    "pavg_reset_stats", "pavg_last_error", "pavg_kernel_timing", "pavg_kernel_time", "pavg_linear_noalloc", "pavg_measure_fma_peak",
     "pavg_batch_create", "pavg_batch_destroy", "pavg_batch_averaged_rhs", "pavg_batch_autotune",
     "pavg_batch_set_config", "pavg_batch_get_config", "pavg_batch_kernel_time", "pavg_batch_sync",
     "pavg_batch_last_error", "pavg_batch_timestep",
@@ -111,6 +111,7 @@ def load(path=LIB_PATH):
         "pavg_nonlinear": (I, [P, P, P, I, V]),
         "pavg_expL_apply": (I, [P, D, P, P, I, V]),
         "pavg_averaged_rhs": (I, [P, D, I, P, P, V]),
+        "pavg_averaged_rhs_group": (I, [P, D, I, I, I, P, P, V]),
         "pavg_averaged_rhs_literal": (I, [P, D, I, P, P, V]),
         "pavg_timestep": (I, [P, D, D, I, P, I, V]),
         "pavg_sync": (I, [P, V]),
@@ -120,6 +121,7 @@ def load(path=LIB_PATH):
         "pavg_kernel_timing": (I, [P, I]),
         "pavg_kernel_time": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I)]),
         "pavg_linear_noalloc": (I, [P, P, P, V]),
+        "pavg_measure_fma_peak": (I, [I, ctypes.POINTER(D), V]),
         "pavg_batch_create": (I, [P, I, ctypes.POINTER(P)]),
         "pavg_batch_destroy": (I, [P]),
         "pavg_batch_averaged_rhs": (I, [P, P, P, P, P, V]),
@@ -188,6 +190,15 @@ def _ptr(t, n, B=None):
 
 def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def measure_fma_peak(fp64):
+    """Measured FP64 (fp64=True) or FP32 fused multiply-add rate of the current GPU, TFLOP/s."""
+    v = ctypes.c_double()
+    rc = lib().pavg_measure_fma_peak(1 if fp64 else 0, ctypes.byref(v), _stream())
+    if rc:
+        raise PavgError(rc, "pavg_measure_fma_peak")
+    return v.value
 
 
 class Model:
@@ -300,6 +311,13 @@ class Model:
         out = self._out(U, out)
         self._check(self._lib.pavg_averaged_rhs(self._h, float(T), int(M), _ptr(U, self.n), _ptr(out, self.n),
                                                 _stream()))
+        return out
+
+    def averaged_rhs_group(self, T, M, m0, m1, U, out=None):
+        """Terms m0 .. m1-1 of the M-shift average (weights of the whole rule)."""
+        out = self._out(U, out)
+        self._check(self._lib.pavg_averaged_rhs_group(self._h, float(T), int(M), int(m0), int(m1), _ptr(U, self.n),
+                                                      _ptr(out, self.n), _stream()))
         return out
 
     def averaged_rhs_literal(self, T, M, U, out=None):

@@ -2,7 +2,7 @@
 the benchmark's JSON contract: one line with the GPU arm's metric, unit and
 direction, `impl: "reference"`, a `cpu_baseline` describing the sample and an
 `e2e` object with no host-device traffic.  Ranks other than 0 exit 0 without
-work.  Run at refinement 3 (the profiling option) so that it takes a second."""
+work.  Run at refinement 3 (the profiling option) so that it takes seconds."""
 
 import json
 import os
@@ -27,10 +27,12 @@ def test_reference_arm_json_line():
     assert d["metric"].startswith("phase-averaged RHS evals/sec")
     assert d["unit"] == "evals/s" and d["higher_is_better"] is True
     assert d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
-    assert d["value"] > 0 and abs(d["ms_per_step"] - 1e3 / d["value"]) <= 1e-9 * d["ms_per_step"]
+    # ms_per_step is the measured wall time of one sample step; value extrapolates to an evaluation
+    assert d["value"] > 0 and d["ms_per_step"] > 0 and abs(d["est_eval_s"] * d["value"] - 1.0) <= 1e-12
     assert d["config"]["workload"].startswith("averaged_rhs r3 M64 T1h")
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and "refinement 3" in cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] == min(16, os.cpu_count()) and cb["value"] == d["value"]
+    assert "refinement 3" in cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 

@@ -117,6 +117,62 @@ def test_averaged_rhs_parity(r, T, M):
     g.sync()
 
 
+@pytest.mark.parametrize("r", [1, 2])
+def test_lambda_max_estimate_brackets_the_spectral_radius(r):
+    """With lambda_max = 0 the library estimates |lambda_max| (Sec. 2.4 needs it;
+    the paper does not say how) by power iteration on -L^2, widened by 2 %.
+    The Chebyshev series is only valid on [-lambda_max, lambda_max], so an
+    underestimate would be an error: the estimate must lie within 1.0-1.05
+    times the true spectral radius of the oracle's L (dense eigenvalues at
+    refinement 1, ARPACK at refinement 2)."""
+    import scipy.sparse.linalg as spla
+    g = gpu(r, lambda_max=0.0)
+    o = orc(r)
+    if r == 1:
+        from oracle import spectrum
+        true = np.abs(np.linalg.eigvals(spectrum.dense_L(o.ops))).max()
+    else:
+        op = spla.LinearOperator((o.n, o.n), matvec=o.ops.L, dtype=np.float64)
+        true = np.abs(spla.eigs(op, k=4, which="LM", tol=1e-12, return_eigenvectors=False)).max()
+    est = g.lambda_max
+    assert 1.0 * true <= est <= 1.05 * true, (est, true)
+
+
+@pytest.fixture(scope="module")
+def oracle_pool_r5():
+    from oracle.model import OracleParams
+    from oracle.parallel import OraclePool
+    with OraclePool(OracleParams(refinement=5, lambda_max=0.011675)) as pool:
+        yield pool
+
+
+@pytest.mark.parametrize("T,seed", [(1800.0, 2104), (3600.0, 2105), (7200.0, 2106)])
+def test_averaged_rhs_parity_refinement5(oracle_pool_r5, T, seed):
+    """The plain method on the GPU against the oracle at refinement 5 (20480
+    cells), degree-16 harmonic states, M = 32, T = 0.5, 1 and 2 h.  This
+    size runs the full solver grid of the paper's mesh and several facet
+    chunks of N.  The oracle's literal sum runs its terms in spawned
+    processes (bitwise the sequential sum)."""
+    from paper_2103_07706_gb300 import pavg
+    from paper_2103_07706_gb300.inputs import harmonic_state
+    g = pavg.Model(5, lambda_max=0.011675)
+    verts, cells = g.mesh()
+    U, _ = harmonic_state(verts, cells, seed, 16)
+    got = g.averaged_rhs(T, 32, dev(U)).cpu().numpy()
+    g.sync()
+    g.close()
+    want = oracle_pool_r5.averaged_rhs(T, 32, U)
+    nu = len(U) - 3 * 20480
+    du = np.concatenate([got[:nu] - want[:nu], np.zeros(len(U) - nu)])
+    de = np.concatenate([np.zeros(nu), got[nu:] - want[nu:]])
+    wu = np.concatenate([want[:nu], np.zeros(len(U) - nu)])
+    we = np.concatenate([np.zeros(nu), want[nu:]])
+    eu = oracle_pool_r5.norms(du)[0] / oracle_pool_r5.norms(wu)[0]
+    ee = oracle_pool_r5.norms(de)[1] / oracle_pool_r5.norms(we)[1]
+    print(f"refinement 5, M 32, T {T:g} s: rel L2 u {eu:.2e}, eta {ee:.2e}")
+    assert eu <= RTOL and ee <= RTOL, (eu, ee)
+
+
 def test_averaged_rhs_closed_rule_parity():
     g = gpu(2, quad_rule=1)
     o = orc(2, quad_rule=1)

@@ -172,3 +172,37 @@ def test_timestep_rest_state_and_mass(om):
     U, _ = harmonic_state(m.mesh.verts, m.mesh.cells, 2103, 4)
     out = m.timestep(900.0, 3600.0, 4, U, 2)
     assert abs(m.ops.mass(out) - m.ops.mass(U)) < 1e-12 * abs(U[m.n_u:]).max() * 4 * np.pi * 6.37122e6 ** 2
+
+
+def test_parallel_literal_sum_is_bitwise_the_sequential_one():
+    """oracle/parallel.py spreads the terms of Eq. vt_discretised over spawned
+    processes and adds them in shift order: the result must be the sequential
+    oracle's, bit for bit."""
+    from oracle.model import OracleModel, OracleParams
+    from oracle.parallel import OraclePool
+    from paper_2103_07706_gb300.inputs import harmonic_state
+    p = OracleParams(refinement=1, lambda_max=0.00072)
+    m = OracleModel(p)
+    U, _ = harmonic_state(m.mesh.verts, m.mesh.cells, 2103, 4)
+    want = m.averaged_rhs(3600.0, 6, U)
+    with OraclePool(p, workers=2) as pool:
+        got = pool.averaged_rhs(3600.0, 6, U)
+        nu, ne = pool.norms(want)
+    assert np.array_equal(got, want)
+    u, e = want[: m.n_u], want[m.n_u:]
+    assert nu == np.sqrt(u @ (m.ops.M1 @ u)) and ne == np.sqrt(e @ (m.ops.M2 @ e))
+
+
+def test_shift_groups_partition_the_sum():
+    """Partial sums over contiguous shift groups (Sec. 2.5's distribution of
+    the independent terms) add up to the whole Riemann sum, for uneven groups,
+    the closed rule with its zero-weight endpoints, and T = 0."""
+    from tests.conftest import oracle_model
+    m = oracle_model(1, lambda_max=0.00072)
+    U, _ = harmonic_state(m.mesh.verts, m.mesh.cells, 2103, 4)
+    for T, M, rule, cuts in [(3600.0, 8, 0, [0, 3, 4, 8]), (1800.0, 7, 1, [0, 1, 6, 7]), (0.0, 4, 0, [0, 1, 4])]:
+        full = m.averaged_rhs(T, M, U, rule)
+        parts = [averaging.averaged_rhs_group(m, T, M, a, b, U, rule) for a, b in zip(cuts[:-1], cuts[1:])]
+        tot = sum(parts)
+        assert np.abs(tot - full).max() <= 1e-13 * np.abs(full).max()
+        assert all(np.abs(p).max() > 0 for p, a, b in zip(parts, cuts[:-1], cuts[1:]) if rule == 0 or 0 < a < M - 1)
