@@ -65,6 +65,10 @@ extern "C" {
 #define PAVG_UPWIND_AS_PRINTED 1 /* u~ = u+ when u.n+ < 0, as printed in Sec. 2.5 */
 #define PAVG_SOLVER_MIXED 0      /* M1 solves: FP32 block-Jacobi CG refined by FP64 residuals */
 #define PAVG_SOLVER_FP64 1       /* M1 solves: FP64 Jacobi CG */
+#define PAVG_SOLVER_SUBDOMAIN 2  /* M1 solves: FP32 block-Jacobi Chebyshev iterations on one part of
+                                    the mesh per SM (neighbour-only exchange), refined by FP64
+                                    residuals; falls back to PAVG_SOLVER_MIXED where the parts do not
+                                    fit in shared memory (refinement 7 and above on 152 SMs) */
 #define PAVG_PRECISION_FP64 0    /* every result FP64-accurate (mass solves to cg_rtol) */
 #define PAVG_PRECISION_MIXED 1   /* N and the forward shift contraction in FP32 arithmetic (FP64 sums
                                     over quadrature points), mass solves to max(cg_rtol, 1e-5) (one FP32
@@ -86,15 +90,17 @@ typedef struct {
   double lambda_max;      /* |lambda_max| of L [1/s]; 0 -> estimate by power iteration at create */
   int quad_rule;          /* PAVG_QUAD_MIDPOINT or PAVG_QUAD_CLOSED */
   int upwind_convention;  /* PAVG_UPWIND_STANDARD or PAVG_UPWIND_AS_PRINTED */
-  int solver;             /* PAVG_SOLVER_MIXED (default) or PAVG_SOLVER_FP64; both reach cg_rtol
-                             in FP64; cg_maxit caps the iterations of one solve (FP64) or of one
-                             refinement sweep (mixed, at most 8 sweeps) */
+  int solver;             /* PAVG_SOLVER_SUBDOMAIN (default), PAVG_SOLVER_MIXED or PAVG_SOLVER_FP64;
+                             all reach cg_rtol in FP64; cg_maxit caps the iterations of one solve
+                             (FP64) or of one refinement sweep (mixed, at most 8 sweeps); the
+                             subdomain solver runs a fixed number of Chebyshev iterations per
+                             sweep (at most 8 sweeps) */
   int precision;          /* PAVG_PRECISION_FP64 (default) or PAVG_PRECISION_MIXED */
 } pavg_params;
 
 /* Fill `p` with the defaults: r = 3, R = 6.37122e6, Omega = 7.292e-5,
  * g = 9.80616, H = 5000, cheb_tol = 1e-6, cg_rtol = 1e-14, cg_maxit = 400,
- * lambda_max = 0, midpoint rule, standard upwinding, mixed solver, FP64 precision. */
+ * lambda_max = 0, midpoint rule, standard upwinding, subdomain solver, FP64 precision. */
 int pavg_default_params(pavg_params* p);
 
 /* Build the mesh and FE data (Sec. 2.5, Sec. 3) on the current CUDA device and
@@ -215,8 +221,21 @@ typedef struct {
 /* Synchronises the device, then fills *out. */
 int pavg_get_stats(pavg_ctx* ctx, pavg_stats* out);
 
-/* Clear the latched device error flags and the CG counters. */
+/* Clear the latched device error flags and the CG counters, and the subdomain
+ * solver's exchange and synchronisation words (after a timed-out launch they
+ * are inconsistent; the context is usable again once this returns). */
 int pavg_reset_stats(pavg_ctx* ctx);
+
+/* Test aid for the bounded waits of the subdomain solver (no counterpart in
+ * the paper).  mode 1: block `part` leaves the next solves before it arrives
+ * at their first grid-wide sum; mode 2: block `part` never publishes its
+ * contributions to the triples it shares; mode 0: off.  wait_us bounds every
+ * wait on another block (microseconds of the SM clock, at 2.07 GHz; 0 keeps
+ * the default of about 2 s).  With a stall on, the other blocks' waits run
+ * out, PAVG_ERR_TIMEOUT is latched and reported by pavg_sync; every block
+ * leaves within a few wait bounds.  INVAL when the context does not use the
+ * subdomain solver or `part` is not one of its blocks. */
+int pavg_test_stall(pavg_ctx* ctx, int mode, int part, double wait_us);
 
 /* Measurement aid: the current device's fused multiply-add rate in TFLOP/s
  * (fp64 != 0: FP64, else FP32), from a kernel of independent FMA chains on

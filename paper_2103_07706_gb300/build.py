@@ -19,7 +19,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpavg.so")
-SOURCES = ["setup.cpp", "kernels.cu", "cg_mixed.cu", "batch.cu", "api.cu", "batch_api.cu", "surrogate.cu", "surrogate_api.cu", "noalloc.cu", "measure.cu"]
+SOURCES = ["setup.cpp", "kernels.cu", "cg_mixed.cu", "batch.cu", "api.cu", "batch_api.cu", "surrogate.cu", "surrogate_api.cu", "noalloc.cu", "measure.cu", "cheb_sd.cu", "sd_setup.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -28,6 +28,9 @@ namespace pavg_api {
 #endif
 // Relative residual at which mass solves stop in mixed precision.
 constexpr double kMixedSolveRtol = PAVG_MIXED_SOLVE_RTOL;
+// Bound of every wait of the subdomain solver on another block: about 2 s of
+// the SM clock (2.07 GHz).
+constexpr long long kSdWaitCycles = 4000000000LL;
 
 int set_err(pavg_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
@@ -78,10 +81,12 @@ int enq_cg(pavg_ctx* ctx, const double* b, double* out, double scale, const doub
     // cudaEventRecordExternal (a plain record is a capture dependency)
     CK(cudaEventRecordWithFlags(e0, st, ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
   }
-  if (ctx->p.solver == PAVG_SOLVER_MIXED)
-    KL(launch_cg_ir(ctx->dm, ctx->cgi, ctx->cgip, b, out, scale, add, st));
-  else
+  if (ctx->use_sd)
+    KL(launch_cheb_sd(ctx->dm, ctx->sd, ctx->sdw, ctx->sdp, b, out, scale, add, st));
+  else if (ctx->p.solver == PAVG_SOLVER_FP64)
     KL(launch_cg(ctx->dm, ctx->cg, ctx->cgp, b, out, scale, add, st));
+  else
+    KL(launch_cg_ir(ctx->dm, ctx->cgi, ctx->cgip, b, out, scale, add, st));
   if (ctx->timing) {
     CK(cudaEventRecordWithFlags(e1, st, ctx->capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
     ctx->cur_pairs.emplace_back(e0, e1);
@@ -438,6 +443,13 @@ int build_shared_mesh(const pavg_params* p, SharedMesh* sh, std::string* why) {
     *why = "device upload failed";
     return PAVG_ERR_NOMEM;
   }
+  // the subdomain solver's partition and Chebyshev interval (P = 0 when its
+  // parts do not fit in shared memory: contexts then use the global solver)
+  if (sd_configure(m.F, m.E, hc.tri, hc.M1, hc.Pinv, &sh->sd) != cudaSuccess) {
+    free_device_mesh(m);
+    *why = "subdomain solver set-up failed";
+    return PAVG_ERR_CUDA;
+  }
   return PAVG_OK;
 }
 
@@ -466,6 +478,7 @@ void release_mesh(SharedMesh* sh) {
   if (--sh->refs > 0) return;
   g_meshes.erase(sh->key);
   free_device_mesh(sh->dm);
+  sd_free(&sh->sd);
   delete sh;
 }
 
@@ -489,6 +502,7 @@ void free_ctx(pavg_ctx* c) {
   cudaFree(wi.x[0]); cudaFree(wi.x[1]); cudaFree(wi.ax); cudaFree(wi.r64); cudaFree(wi.fbuf);
   cudaFree(wi.partial); cudaFree(wi.partial_f);
   cudaFree(wi.bar); cudaFree(wi.scal); cudaFree(wi.tag);
+  sd_free_work(&c->sdw);
   cudaFree(c->ru);
   cudaFree(c->facets);
   for (auto* v : c->vec) cudaFree(v);
@@ -506,7 +520,7 @@ bool valid_params(const pavg_params* p) {
          p->cheb_tol > 0 && p->cg_rtol > 0 && p->cg_maxit > 0 && p->lambda_max >= 0 && std::isfinite(p->omega) &&
          (p->quad_rule == PAVG_QUAD_MIDPOINT || p->quad_rule == PAVG_QUAD_CLOSED) &&
          (p->upwind_convention == PAVG_UPWIND_STANDARD || p->upwind_convention == PAVG_UPWIND_AS_PRINTED) &&
-         (p->solver == PAVG_SOLVER_MIXED || p->solver == PAVG_SOLVER_FP64) &&
+         (p->solver == PAVG_SOLVER_MIXED || p->solver == PAVG_SOLVER_FP64 || p->solver == PAVG_SOLVER_SUBDOMAIN) &&
          (p->precision == PAVG_PRECISION_FP64 || p->precision == PAVG_PRECISION_MIXED);
 }
 
@@ -529,7 +543,7 @@ int pavg_default_params(pavg_params* p) {
   p->lambda_max = 0.0;
   p->quad_rule = PAVG_QUAD_MIDPOINT;
   p->upwind_convention = PAVG_UPWIND_STANDARD;
-  p->solver = PAVG_SOLVER_MIXED;
+  p->solver = PAVG_SOLVER_SUBDOMAIN;
   p->precision = PAVG_PRECISION_FP64;
   return PAVG_OK;
 }
@@ -559,6 +573,7 @@ int pavg_create(const pavg_params* p, pavg_ctx** out) {
     ctx->shared = sh;
     ctx->mesh = sh->mesh;
     ctx->dm = sh->dm;
+    ctx->sd = sh->sd;
     DeviceMesh& m = ctx->dm;
     bool ok = dalloc(&m.topo, m.n_eta) == cudaSuccess;
     if (!ok) { rc = set_err(ctx, PAVG_ERR_NOMEM, "device upload failed"); throw 0; }
@@ -593,6 +608,22 @@ int pavg_create(const pavg_params* p, pavg_ctx** out) {
          dalloc(&wi.bar, 2) == cudaSuccess;
     wi.flags = w.flags;
     wi.stats = w.stats;
+    if (ok && p->solver == PAVG_SOLVER_SUBDOMAIN && ctx->sd.P > 0) {
+      ok = sd_alloc_work(ctx->sd, m.F, &ctx->sdw) == cudaSuccess;
+      ctx->sdw.flags = w.flags;
+      ctx->sdw.stats = w.stats;
+      const double a = 0.95 * ctx->sd.lmin, bnd = 1.05 * ctx->sd.lmax;  // Lanczos estimates lie inside
+      SdParams& sp = ctx->sdp;
+      sp.rtol = ctx->cgip.rtol;
+      sp.max_sweeps = 8;
+      sp.iters = sd_iterations(a, bnd, mixed ? 1e-6 : 1e-5);
+      sp.theta = 0.5 * (bnd + a);
+      sp.delta = 0.5 * (bnd - a);
+      sp.wait_cycles = kSdWaitCycles;
+      sp.stall_mode = 0;
+      sp.stall_part = -1;
+      ctx->use_sd = ok;
+    }
     if (ok) {
       float* fb = wi.fbuf;
       const int64_t s4 = 4 * (m.E + m.F);
@@ -844,6 +875,19 @@ int pavg_reset_stats(pavg_ctx* ctx) {
   CK(cudaDeviceSynchronize());
   CK(cudaMemset(ctx->cg.stats, 0, 4 * sizeof(unsigned long long)));
   CK(cudaMemset(ctx->cg.flags, 0, sizeof(int)));
+  if (ctx->use_sd) CK(sd_reset_work(ctx->sd, ctx->dm.F, &ctx->sdw));
+  return PAVG_OK;
+}
+
+int pavg_test_stall(pavg_ctx* ctx, int mode, int part, double wait_us) {
+  if (!ctx || mode < 0 || mode > 2 || !(wait_us >= 0) || !std::isfinite(wait_us)) return PAVG_ERR_INVAL;
+  if (!ctx->use_sd) return set_err(ctx, PAVG_ERR_INVAL, "pavg_test_stall: the context does not use the subdomain solver");
+  if (mode != 0 && (part < 0 || part >= ctx->sd.P)) return set_err(ctx, PAVG_ERR_INVAL, "pavg_test_stall: no such block");
+  CK(cudaDeviceSynchronize());
+  for (auto& kv : ctx->plans) drop_graph(&kv.second);  // graphs hold the old kernel parameters
+  ctx->sdp.stall_mode = mode;
+  ctx->sdp.stall_part = mode ? part : -1;
+  ctx->sdp.wait_cycles = wait_us > 0 ? (long long)(wait_us * 2070.0) : kSdWaitCycles;
   return PAVG_OK;
 }
 

@@ -40,6 +40,7 @@ struct SharedMesh {
   pavg_detail::SharedMesh* shared = nullptr;
   pavg::Mesh mesh;
   pavg::DeviceMesh dm;  // topo stays per context
+  pavg::SdMesh sd;      // partition of the subdomain solver (P = 0: not available)
 };
 
 }  // namespace pavg_detail
@@ -56,6 +57,10 @@ struct pavg_ctx {
   pavg::CgParams cgp{};
   pavg::CgIrWork cgi;
   pavg::CgIrParams cgip{};
+  pavg::SdMesh sd;              // the shared mesh's partition (copy of the descriptor)
+  pavg::SdWork sdw;
+  pavg::SdParams sdp{};
+  bool use_sd = false;          // subdomain solver in use
   double lam = 0;
   int device = 0;
   // scratch

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "pavg_internal.h"
 
@@ -91,6 +92,63 @@ cudaError_t cg_ir_configure(int64_t F, CgIrWork* w);
 // out_u = scale_x * M1^{-1} b + add, mixed precision, FP64-accurate.
 cudaError_t launch_cg_ir(const DeviceMesh& m, const CgIrWork& w, const CgIrParams& cp, const double* b,
                          double* out, double scale_x, const double* add, cudaStream_t st);
+
+// Subdomain mass solver (cheb_sd.cu).  One block per part of a contiguous
+// partition of the cells; each part keeps its cells' FP32 element matrices
+// in shared memory and its DOF triples' FP32 vectors in registers, and
+// exchanges only the contributions to the triples it shares with a
+// neighbouring part (tagged words, no grid-wide wait per inner iteration).
+// Read-only partition data, shared by the contexts of one mesh:
+struct SdMesh {
+  int P = 0;                     // parts = blocks of the cooperative launch (0: not available)
+  int max_cells = 0, max_lt = 0, nslots = 0, total_lt = 0;
+  size_t smem = 0;               // dynamic shared memory per block
+  double lmin = 0, lmax = 0;     // Lanczos estimates of the spectrum of P M1
+  int32_t* cell0 = nullptr;      // [P+1]
+  int32_t* lt0 = nullptr;        // [P+1]
+  uint32_t* lt_gtri = nullptr;   // [lt] global triple | owner bit 31
+  uint32_t* lt_slot = nullptr;   // [lt] two 16-bit local (cell, q) positions, 0xffff = none
+  int32_t* lt_recv = nullptr;    // [lt] partner's send slot of a shared triple, -1 otherwise
+  ushort4* cell_lt = nullptr;    // [F] local triples of the cell's four (cell, q)
+  int4* cell_send = nullptr;     // [F] send slot of (cell, q), q < 3, -1 when not shared
+};
+
+// Per-context scratch of the subdomain solver.
+struct SdWork {
+  unsigned long long* xch32 = nullptr;  // [2][nslots][4] tagged FP32 words (3 used)
+  unsigned long long* xch64 = nullptr;  // [2][nslots][6] tagged 32-bit halves of FP64 values
+  double* y64 = nullptr;                // [F][12] FP64 cell contributions of a refinement product
+  double* x64 = nullptr;                // [lt][3] FP64 iterate, each part's own copy of its triples
+  double* r64 = nullptr;                // [lt][3] FP64 residual of the last sweep, likewise
+  double* part = nullptr;               // [P] block partial sums
+  double* pub = nullptr;                // [1] published grid sum
+  unsigned long long* sync = nullptr;   // [4]: arrivals (monotonic), published tag, epoch base, spare
+  int* flags = nullptr;
+  unsigned long long* stats = nullptr;
+};
+
+struct SdParams {
+  double rtol;          // FP64 relative residual target
+  int max_sweeps;       // FP64 refinement sweeps
+  int iters;            // Chebyshev iterations per sweep
+  double theta, delta;  // centre and half-width of the Chebyshev interval
+  long long wait_cycles;  // bound of every wait on another block (clock64 cycles)
+  int stall_mode;       // test hook, 0 = off; 1: block stall_part never arrives at the first grid sum;
+  int stall_part;       //            2: block stall_part never publishes its shared contributions
+};
+
+// Builds the partition for F cells on the current device (P = min(SMs, F/32)
+// parts) when its blocks fit in shared memory; sd->P = 0 otherwise.
+cudaError_t sd_configure(int64_t F, int64_t E, const std::vector<int32_t>& tri, const std::vector<double>& M1,
+                         const std::vector<float>& Pinv, SdMesh* sd);
+void sd_free(SdMesh* sd);
+cudaError_t sd_alloc_work(const SdMesh& sd, int64_t F, SdWork* w);
+void sd_free_work(SdWork* w);
+// Clears the exchange words and synchronisation counters (after a failed launch).
+cudaError_t sd_reset_work(const SdMesh& sd, int64_t F, SdWork* w);
+// out_u = scale_x * M1^{-1} b + add, FP64-accurate.
+cudaError_t launch_cheb_sd(const DeviceMesh& m, const SdMesh& sd, const SdWork& w, const SdParams& sp,
+                           const double* b, double* out, double scale_x, const double* add, cudaStream_t st);
 
 // One problem of the batched persistent recurrence kernel (k_chain): one
 // instance's whole forward Chebyshev chain (mode 0, K steps)

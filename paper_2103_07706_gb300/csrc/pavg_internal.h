@@ -93,6 +93,29 @@ struct HostCellData {
 void build_cell_data(const Mesh& m, const RefElement& el, double omega, HostCellData* out,
                      ConstTables* tab);
 
+// Partition of the cells for the subdomain mass solver: part p owns the
+// contiguous cells cell0[p] .. cell0[p+1]-1 and numbers the DOF triples its
+// cells touch locally (lt0[p] .. lt0[p+1]-1 in the arrays below).
+struct SdPartition {
+  int P = 0;
+  std::vector<int32_t> cell0;     // [P+1]
+  std::vector<int32_t> lt0;       // [P+1]
+  std::vector<uint32_t> lt_gtri;  // [lt] global triple | bit 31: this part owns it (writes it, counts it in norms)
+  std::vector<uint32_t> lt_slot;  // [lt] the local (cell - cell0) * 4 + q positions of the triple's local
+                                  //      cells: low 16 bits, high 16 bits; 0xffff = none
+  std::vector<int32_t> lt_recv;   // [lt] send slot of the other part for a triple shared with it, else -1
+  std::vector<int32_t> cell_lt;   // [F][4] local triple of (cell, q)
+  std::vector<int32_t> cell_send; // [F][4] send slot of (cell, q) when its triple is shared, else -1
+  int32_t nslots = 0;             // send slots (two per shared triple)
+  int32_t max_cells = 0, max_lt = 0, max_shared = 0;
+};
+void build_sd_partition(int64_t F, int64_t E, const std::vector<int32_t>& tri, int P, SdPartition* out);
+// Extreme eigenvalues of the block-Jacobi preconditioned M1 (preconditioned Lanczos, `iters` steps).
+void sd_spectrum(int64_t F, int64_t E, const std::vector<double>& M1, const std::vector<int32_t>& tri,
+                 const std::vector<float>& Pinv, int iters, double* lmin, double* lmax);
+// Chebyshev iterations on [a, b] that reduce the error by inner_rtol.
+int sd_iterations(double a, double b, double inner_rtol);
+
 // Largest lambda_max |t| accepted for one exponential.  The coefficients
 // are a direct O(N^2) transform with N >= Lb + 64, and the series has about
 // Lb terms, each one mass solve; 16384 is 50 times the widest benchmark

@@ -21,6 +21,7 @@ PAVG_UPWIND_STANDARD = 0
 PAVG_UPWIND_AS_PRINTED = 1
 PAVG_SOLVER_MIXED = 0
 PAVG_SOLVER_FP64 = 1
+PAVG_SOLVER_SUBDOMAIN = 2
 PAVG_PRECISION_FP64 = 0
 PAVG_PRECISION_MIXED = 1
 PAVG_MAX_CHEB_ARG = 16384.0  # widest exponential accepted: lambda_max |t|
@@ -34,7 +35,7 @@ EXPORTED = [
     "pavg_default_params", "pavg_create", "pavg_destroy", "pavg_sizes", "pavg_mesh_export",
     "pavg_set_topography", "pavg_lambda_max", "pavg_linear", "pavg_nonlinear", "pavg_expL_apply",
     "pavg_averaged_rhs", "pavg_averaged_rhs_group", "pavg_averaged_rhs_literal", "pavg_timestep", "pavg_sync", "pavg_get_stats",
-    "pavg_reset_stats", "pavg_last_error", "pavg_kernel_timing", "pavg_kernel_time", "pavg_linear_noalloc", "pavg_measure_fma_peak",
+    "pavg_reset_stats", "pavg_last_error", "pavg_kernel_timing", "pavg_kernel_time", "pavg_linear_noalloc", "pavg_measure_fma_peak", "pavg_test_stall",
     "pavg_batch_create", "pavg_batch_destroy", "pavg_batch_averaged_rhs", "pavg_batch_autotune",
     "pavg_batch_set_config", "pavg_batch_get_config", "pavg_batch_kernel_time", "pavg_batch_sync",
     "pavg_batch_last_error", "pavg_batch_timestep",
@@ -122,6 +123,7 @@ def load(path=LIB_PATH):
         "pavg_kernel_time": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I)]),
         "pavg_linear_noalloc": (I, [P, P, P, V]),
         "pavg_measure_fma_peak": (I, [I, ctypes.POINTER(D), V]),
+        "pavg_test_stall": (I, [P, I, I, D]),
         "pavg_batch_create": (I, [P, I, ctypes.POINTER(P)]),
         "pavg_batch_destroy": (I, [P]),
         "pavg_batch_averaged_rhs": (I, [P, P, P, P, P, V]),
@@ -265,6 +267,10 @@ class Model:
 
     def reset_stats(self):
         self._check(self._lib.pavg_reset_stats(self._h))
+
+    def test_stall(self, mode, part=0, wait_us=0.0):
+        """Test aid: make one block of the subdomain solver stall (pavg.h)."""
+        self._check(self._lib.pavg_test_stall(self._h, int(mode), int(part), float(wait_us)))
 
     def sync(self):
         self._check(self._lib.pavg_sync(self._h, _stream()))

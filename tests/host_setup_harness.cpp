@@ -25,6 +25,17 @@
 //                         [78][F]), .m1p (float32 [78][F]), .m1f (float32
 //                         [36][F][4]), .eplus / .eminus (int32 [E]), .elpos
 //                         (uint8 [E]); prints "E F"
+//   partition R RADIUS P PREFIX
+//                         the subdomain solver's partition of the cells into P
+//                         parts (csrc/sd_setup.cpp): writes PREFIX.cell0,
+//                         .lt0 (int32 [P+1]), .gtri, .slot (uint32 [lt]), .recv
+//                         (int32 [lt]), .celllt, .cellsend (int32 [F][4]);
+//                         prints "nslots max_cells max_lt max_shared"
+//   spectrum R RADIUS ITERS
+//                         Lanczos estimate of the extreme eigenvalues of the
+//                         block-Jacobi preconditioned M1: prints "lmin lmax"
+//   chebits A B TOL       Chebyshev iterations on [A, B] that reduce the error
+//                         by TOL
 //   element X1 Y1 X2 Y2 ...
 //                         the reference BDM2 basis at each point: one line of
 //                         24 values psi_i[c], then one of 48 derivatives
@@ -154,6 +165,39 @@ int main(int argc, char** argv) {
         !write_all(p + ".elpos", m.edge_lpos.data(), m.edge_lpos.size()))
       return 3;
     std::printf("%lld %lld\n", (long long)m.E(), (long long)m.F());
+    return 0;
+  }
+  if ((cmd == "partition" && argc == 6) || (cmd == "spectrum" && argc == 5)) {
+    pavg::Mesh m;
+    pavg::build_mesh(std::atoi(argv[2]), std::strtod(argv[3], nullptr), &m);
+    pavg::RefElement el;
+    pavg::build_reference_element(&el);
+    pavg::HostCellData cd;
+    pavg::ConstTables tab;
+    pavg::build_cell_data(m, el, 7.292e-5, &cd, &tab);
+    if (cmd == "spectrum") {
+      double lo = 0, hi = 0;
+      pavg::sd_spectrum(m.F(), m.E(), cd.M1, cd.tri, cd.Pinv, std::atoi(argv[4]), &lo, &hi);
+      std::printf("%.17g %.17g\n", lo, hi);
+      return 0;
+    }
+    pavg::SdPartition sp;
+    pavg::build_sd_partition(m.F(), m.E(), cd.tri, std::atoi(argv[4]), &sp);
+    const std::string p = argv[5];
+    if (!write_all(p + ".cell0", sp.cell0.data(), 4 * sp.cell0.size()) ||
+        !write_all(p + ".lt0", sp.lt0.data(), 4 * sp.lt0.size()) ||
+        !write_all(p + ".gtri", sp.lt_gtri.data(), 4 * sp.lt_gtri.size()) ||
+        !write_all(p + ".slot", sp.lt_slot.data(), 4 * sp.lt_slot.size()) ||
+        !write_all(p + ".recv", sp.lt_recv.data(), 4 * sp.lt_recv.size()) ||
+        !write_all(p + ".celllt", sp.cell_lt.data(), 4 * sp.cell_lt.size()) ||
+        !write_all(p + ".cellsend", sp.cell_send.data(), 4 * sp.cell_send.size()))
+      return 3;
+    std::printf("%d %d %d %d\n", sp.nslots, sp.max_cells, sp.max_lt, sp.max_shared);
+    return 0;
+  }
+  if (cmd == "chebits" && argc == 5) {
+    std::printf("%d\n", pavg::sd_iterations(std::strtod(argv[2], nullptr), std::strtod(argv[3], nullptr),
+                                             std::strtod(argv[4], nullptr)));
     return 0;
   }
   if (cmd == "element" && argc >= 4 && argc % 2 == 0) {

@@ -27,6 +27,7 @@ def harness(tmp_path_factory):
     csrc = os.path.join(ROOT, "paper_2103_07706_gb300", "csrc")
     subprocess.run([gxx, "-O2", "-std=c++17", "-ffp-contract=off", "-I", os.path.join(ROOT, "include"), "-I", csrc,
                     os.path.join(ROOT, "tests", "host_setup_harness.cpp"), os.path.join(csrc, "setup.cpp"),
+                    os.path.join(csrc, "sd_setup.cpp"),
                     "-o", str(exe)], check=True)
     return exe
 
@@ -248,3 +249,94 @@ def test_nonlinear_kernel_tables_match_the_oracle(harness):
     assert np.array_equal(edge_dir.reshape(3, 2), EDGE_DIR)
     verts = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
     assert np.abs(div_vert.reshape(12, 3) - el.divs(verts).T).max() <= 1e-11
+
+
+def _read(path, dtype):
+    return np.fromfile(path, dtype=dtype)
+
+
+@pytest.mark.parametrize("r,P", [(2, 10), (3, 40), (4, 152), (5, 152)])
+def test_subdomain_partition_reproduces_the_global_product(harness, tmp_path, r, P):
+    """The subdomain solver's data flow, replayed on the CPU from the set-up
+    data the kernel reads: every part multiplies its cells' element matrices
+    into per-(cell, q) slots, each local triple adds its local slots and, when
+    it is shared, the partner part's contribution read from the partner's send
+    slot.  Every part's copy of every triple must equal the assembled M1 x,
+    each triple must have exactly one owner, and at most two cells."""
+    E, F = map(int, run(harness, "solver", r, repr(R), tmp_path / "s")[0].split())
+    nslots, max_cells, max_lt, max_shared = map(int, run(harness, "partition", r, repr(R), P, tmp_path / "p")[0].split())
+    tri = _read(tmp_path / "s.tri", np.int32).reshape(F, 4) & 0x7fffffff
+    m1 = _read(tmp_path / "s.m1", np.float64).reshape(78, F)
+    cell0, lt0 = _read(tmp_path / "p.cell0", np.int32), _read(tmp_path / "p.lt0", np.int32)
+    gtri, slot = _read(tmp_path / "p.gtri", np.uint32), _read(tmp_path / "p.slot", np.uint32)
+    recv = _read(tmp_path / "p.recv", np.int32)
+    celllt = _read(tmp_path / "p.celllt", np.int32).reshape(F, 4)
+    cellsend = _read(tmp_path / "p.cellsend", np.int32).reshape(F, 4)
+    assert len(cell0) == P + 1 and cell0[0] == 0 and cell0[-1] == F
+    assert max_cells == np.diff(cell0).max() and max_lt == np.diff(lt0).max()
+    T = E + F
+    # full 12 x 12 element matrices and the global product
+    iu = np.triu_indices(12)
+    A = np.zeros((F, 12, 12))
+    A[:, iu[0], iu[1]] = m1.T
+    A = A + np.transpose(A, (0, 2, 1)) - A * np.eye(12)[None]
+    x = np.random.default_rng(1).standard_normal((T, 3))
+    y_loc = np.einsum("fij,fj->fi", A, x[tri].reshape(F, 12)).reshape(F, 4, 3)
+    want = np.zeros((T, 3))
+    np.add.at(want, tri.ravel(), y_loc.reshape(-1, 3))
+    # send buffer: contribution of (cell, q) at its send slot
+    send = np.full((nslots, 3), np.nan)
+    for c, q in zip(*np.nonzero(cellsend >= 0)):
+        send[cellsend[c, q]] = y_loc[c, q]
+    assert not np.isnan(send).any()
+    owners = np.zeros(T, dtype=int)
+    for p in range(P):
+        c0, c1 = cell0[p], cell0[p + 1]
+        for i in range(lt0[p], lt0[p + 1]):
+            t = gtri[i] & 0x7fffffff
+            owners[t] += gtri[i] >> 31
+            s0, s1 = slot[i] & 0xffff, slot[i] >> 16
+            assert s0 != 0xffff
+            got = y_loc[c0 + s0 // 4, s0 % 4].copy()
+            assert tri[c0 + s0 // 4, s0 % 4] == t and celllt[c0 + s0 // 4, s0 % 4] == i - lt0[p]
+            if s1 != 0xffff:
+                assert tri[c0 + s1 // 4, s1 % 4] == t and recv[i] == -1
+                got += y_loc[c0 + s1 // 4, s1 % 4]
+            elif recv[i] >= 0:
+                got += send[recv[i]]
+            assert np.abs(got - want[t]).max() <= 1e-14 * np.abs(want).max()
+        assert (celllt[c0:c1] < lt0[p + 1] - lt0[p]).all()
+    assert (owners == 1).all()
+    assert nslots == 2 * (recv >= 0).sum() // 2 and (recv >= 0).sum() == nslots
+    assert max_shared <= max_lt
+
+
+def test_subdomain_spectrum_and_iteration_count(harness, tmp_path):
+    """Preconditioned Lanczos bounds of P M1 against its dense eigenvalues
+    (refinement 2), and the Chebyshev iteration count against the polynomial's
+    closed-form error bound 2 / (c^k + c^-k)."""
+    E, F = map(int, run(harness, "solver", 2, repr(R), tmp_path / "s")[0].split())
+    lo, hi = map(float, run(harness, "spectrum", 2, repr(R), 40)[0].split())
+    tri = _read(tmp_path / "s.tri", np.int32).reshape(F, 4) & 0x7fffffff
+    m1 = _read(tmp_path / "s.m1", np.float64).reshape(78, F)
+    pinv = _read(tmp_path / "s.pinv", np.float32).reshape(E + F, 8).astype(np.float64)
+    n = 3 * (E + F)
+    iu = np.triu_indices(12)
+    A = np.zeros((F, 12, 12))
+    A[:, iu[0], iu[1]] = m1.T
+    A = A + np.transpose(A, (0, 2, 1)) - A * np.eye(12)[None]
+    dofs = (3 * tri[:, :, None] + np.arange(3)).reshape(F, 12)
+    M = np.zeros((n, n))
+    np.add.at(M, (np.repeat(dofs, 12, axis=1).ravel(), np.tile(dofs, (1, 12)).ravel()), A.reshape(F, -1).ravel())
+    Pm = np.zeros((n, n))
+    idx = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    for t in range(E + F):
+        for k, (a, b) in enumerate(idx):
+            Pm[3 * t + a, 3 * t + b] = Pm[3 * t + b, 3 * t + a] = pinv[t, k]
+    ev = np.sort(np.linalg.eigvals(Pm @ M).real)
+    assert ev[0] <= lo <= ev[0] * 1.01 and ev[-1] * 0.99 <= hi <= ev[-1], (lo, hi, ev[0], ev[-1])
+    a, b = 0.95 * lo, 1.05 * hi
+    k = int(run(harness, "chebits", a, b, 1e-5)[0])
+    c = (np.sqrt(b / a) + 1) / (np.sqrt(b / a) - 1)
+    bound = lambda j: 2 / (c ** j + c ** -j)  # noqa: E731
+    assert bound(k) <= 1e-5 < bound(k - 1)
