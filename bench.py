@@ -49,8 +49,10 @@ ALU_PEAKS = {}
 # The mass-solve kernel the default context runs, and the DRAM bytes (read +
 # write) of one of its launches from an ncu capture of the current kernel
 # (profiles/), per refinement; absent when the kernel changed since.
-SOLVER_KERNEL = "k_cg_ir (persistent mixed-precision M1 solve: FP32 CG + FP64 residual sweeps)"
-SOLVER_DRAM_BYTES = {(SOLVER_KERNEL, 6): (206.434304 + 80.506624) * 1e6}
+SOLVER_KERNELS = {0: "k_cg_ir (persistent mixed-precision M1 solve: FP32 CG + FP64 residual sweeps)",
+                  1: "k_cg (persistent FP64 Jacobi CG)",
+                  2: "k_cheb_sd (subdomain M1 solve: FP32 Chebyshev per SM, neighbour exchange, FP64 sweeps)"}
+SOLVER_DRAM_BYTES = {(SOLVER_KERNELS[0], 6): (206.434304 + 80.506624) * 1e6}
 
 
 def _cg_flops(F, n_u, iters, sweeps):
@@ -453,6 +455,14 @@ def _shift_groups_leg(model, cfg, Ud, ms_full, full):
 ORACLE_GROUP = (28, 36)
 
 
+def _single_threaded_blas():
+    """Set before numpy loads in an oracle process: its workers are forked
+    from it, and a BLAS thread pool does not survive a fork; one thread per
+    process is also the right size when every core runs a worker."""
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+
+
 def _oracle_term(args):
     """Forked worker: one complete term of the literal sum, and its wall time."""
     import oracle.parallel as op
@@ -466,6 +476,7 @@ def _oracle_term(args):
 def _oracle_master(q_out, q_in, cfg, parity):
     """Spawned process (no CUDA state): builds the oracle once, then forks its
     workers from itself so that they share the set-up."""
+    _single_threaded_blas()
     try:
         import numpy as np
 
@@ -612,6 +623,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    _single_threaded_blas()
     import numpy as np  # noqa: F401
 
     import oracle.parallel as op
@@ -801,8 +813,8 @@ def run_pavg(args):
         hbm = peaks.get("hbm_gbs", 6800.0)
         achieved = alg / dur_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": SOLVER_DRAM_BYTES.get((SOLVER_KERNEL, cfg["refinement"])),
-                "kernel": SOLVER_KERNEL, "algorithmic_bytes_per_launch": alg,
+                "traffic": SOLVER_DRAM_BYTES.get((SOLVER_KERNELS[st["solver_in_use"]], cfg["refinement"])),
+                "kernel": SOLVER_KERNELS[st["solver_in_use"]], "algorithmic_bytes_per_launch": alg,
                 "bytes_rule": "per FP32 iteration the packed FP32 element matrices (78 x 4 B per cell) and five "
                               "FP32 vector passes (5 x 4 B per velocity DOF); per FP64 refinement sweep the packed "
                               "FP64 matrices (78 x 8 B per cell) and five FP64 vector passes; no cache reuse",
@@ -816,7 +828,8 @@ def run_pavg(args):
                                        "(pavg_measure_fma_peak), best of five"},
                 "launch_ms": cg_ms / cg_n, "launches_per_step": cg_n, "iters_per_launch": iters,
                 "sweeps_per_launch": sweeps, "share_of_step": cg_ms / (ms / args.steps),
-                "note": "latency-bound: one synchronised phase per inner iteration"}
+                "note": "latency-bound: one synchronised phase per inner iteration (grid-wide for k_cg_ir, "
+                        "neighbour-only for k_cheb_sd)"}
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",

@@ -216,6 +216,8 @@ typedef struct {
   int error_flags;        /* bit 0 NOCONV, bit 1 TIMEOUT, bit 2 NONFINITE */
   int kernel_launches;    /* kernels enqueued by the last API call (graph replays: kernels in the graph) */
   double cg_sweeps_mean;  /* FP64 refinement sweeps per solve (mixed solver; 0 for FP64 CG) */
+  int solver_in_use;      /* PAVG_SOLVER_* of the context's M1 solves (SUBDOMAIN falls back to MIXED
+                             where its parts do not fit in shared memory) */
 } pavg_stats;
 
 /* Synchronises the device, then fills *out. */

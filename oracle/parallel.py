@@ -52,8 +52,19 @@ class OraclePool:
         self.params = params
         self.workers = workers or max(1, os.cpu_count() or 1)
         ctx = mp.get_context("spawn")
-        self.pool = ctx.Pool(self.workers, initializer=_init,
-                             initargs=(dataclasses.asdict(params), nice))
+        # one BLAS thread per worker: the children read these when numpy loads
+        keys = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+        saved = {k: os.environ.get(k) for k in keys}
+        os.environ.update({k: "1" for k in keys})
+        try:
+            self.pool = ctx.Pool(self.workers, initializer=_init,
+                                 initargs=(dataclasses.asdict(params), nice))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
 
     def degree(self, t):
         from . import expo

@@ -847,6 +847,8 @@ int pavg_get_stats(pavg_ctx* ctx, pavg_stats* out) {
   out->cg_sweeps_mean = st[0] ? (double)st[3] / (double)st[0] : 0.0;
   out->error_flags = f;
   out->kernel_launches = ctx->last_launches;
+  out->solver_in_use = ctx->use_sd ? PAVG_SOLVER_SUBDOMAIN
+                                   : (ctx->p.solver == PAVG_SOLVER_FP64 ? PAVG_SOLVER_FP64 : PAVG_SOLVER_MIXED);
   return PAVG_OK;
 }
 

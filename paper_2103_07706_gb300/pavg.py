@@ -75,6 +75,7 @@ class Stats(ctypes.Structure):
         ("error_flags", ctypes.c_int),
         ("kernel_launches", ctypes.c_int),
         ("cg_sweeps_mean", ctypes.c_double),
+        ("solver_in_use", ctypes.c_int),
     ]
 
 
