@@ -10,7 +10,7 @@ computes L U correctly again."""
 import numpy as np
 import pytest
 
-from tests.test_gpu_parity import LAM, assert_close, dev, orc, state
+from tests.test_gpu_parity import LAM, assert_close, dev, orc
 
 pytestmark = pytest.mark.gpu
 
@@ -24,7 +24,9 @@ def _model(r, **kw):
 @pytest.mark.parametrize("r", [1, 2, 3, 4])
 def test_linear_parity_against_oracle(r):
     g, o = _model(r), orc(r)
-    U = state(o, eta_noise=3.0)
+    # a random state: the harmonic states are divergence-free, so the eta
+    # part of their L U is round-off and has no meaningful relative error
+    U = np.random.default_rng(r).standard_normal(o.n) * 10.0
     assert_close(o, g.linear(dev(U)).cpu().numpy(), o.L(U), tol=1e-13)
     g.sync()
     st = g.stats()
@@ -81,7 +83,7 @@ def test_bounded_waits_run_out_and_the_context_recovers(mode):
     reported by pavg_sync, and after pavg_reset_stats the context is usable."""
     from paper_2103_07706_gb300 import pavg
     g, o = _model(4), orc(4)
-    U = state(o)
+    U = np.random.default_rng(44).standard_normal(o.n) * 10.0
     Ud = dev(U)
     g.linear(Ud)
     g.sync()
