@@ -446,6 +446,69 @@ def _shift_groups_leg(model, cfg, Ud, ms_full, full):
     return res
 
 
+def _tc5_leg(pavg, days=1.0):
+    """Williamson's test case 5 (Sec. 3) at refinement 5: the error of the
+    averaged model at `days` against the unaveraged (T = 0) Lawson RK4 at
+    dt = 22.5 s, for a sweep of windows T at dt = 450, 900 and 1350 s, in the
+    paper's normalised norms (H(div) of u, L2 of eta).  M follows the paper's
+    four points per fastest period, M >= 2 lambda_max T / pi (even, at least 8).
+    A run whose state stops being finite, or whose errors exceed 1, counts as
+    blown up (the paper's T_min is the smallest window that survives a day)."""
+    import torch
+
+    from paper_2103_07706_gb300.inputs import tc5_state
+    g_, H_ = 9.8, 5960.0
+    m = pavg.Model(5, g=g_, H=H_, omega=7.292e-5, radius=6.37122e6, lambda_max=0.0)
+    lam = m.lambda_max
+    verts, cells = m.mesh()
+    U0, b = tc5_state(verts, cells, g=g_, H=H_)
+    m.set_topography(torch.from_numpy(b).cuda())
+    t0 = time.time()
+    Ur = torch.from_numpy(U0).cuda()
+    n_ref = int(round(days * 86400.0 / 22.5))
+    for k in range(0, n_ref, 480):  # enqueue in chunks
+        m.timestep(22.5, 0.0, 1, Ur, min(480, n_ref - k))
+    m.sync()
+    ref_s = time.time() - t0
+    nref = m.norms(Ur)
+    res = {"setup": f"refinement 5 (20480 cells, flat facets), g = {g_}, H = {H_} m, u0 = 20 m/s, mountain "
+                    f"b0 = 2000 m at (30N, 90W); lambda_max = {lam:.5f} s^-1 (library estimate); reference: "
+                    f"Lawson RK4 without averaging (T = 0) at dt = 22.5 s ({n_ref} steps, {ref_s:.0f} s)",
+           "days": days, "runs": []}
+    sweeps = {900.0: [0.25, 0.3, 0.35, 0.4, 0.45, 0.5, 0.6, 0.8, 1.0, 2.0, 4.0],
+              450.0: [0.05, 0.1, 0.15, 0.25, 0.35, 0.5, 1.0],
+              1350.0: [0.25, 0.3, 0.375, 0.45, 0.6, 1.0]}
+    for dt, Ts in sweeps.items():
+        for Th in Ts:
+            T = Th * 3600.0
+            M = max(8, 2 * math.ceil(lam * T / math.pi))
+            U = torch.from_numpy(U0).cuda()
+            steps = int(round(days * 86400.0 / dt))
+            t1 = time.time()
+            eu = ee = float("inf")
+            try:
+                m.timestep(dt, T, M, U, steps)
+                m.sync()
+                if bool(torch.isfinite(U).all()):
+                    d = m.norms(U - Ur)
+                    eu, ee = d[1] / nref[1], d[2] / nref[2]
+            except pavg.PavgError:
+                m.reset_stats()
+            blown = not (eu <= 1.0 and ee <= 1.0)
+            res["runs"].append({"dt": dt, "T_h": Th, "M": M, "err_u_hdiv": eu, "err_eta_l2": ee,
+                                "blown_up": blown, "wall_s": time.time() - t1})
+    for dt in sweeps:
+        ok = [r for r in res["runs"] if r["dt"] == dt and not r["blown_up"]]
+        if ok:
+            res[f"dt{int(dt)}"] = {"T_min_h": min(r["T_h"] for r in ok),
+                                   "T_opt_u_h": min(ok, key=lambda r: r["err_u_hdiv"])["T_h"],
+                                   "T_opt_eta_h": min(ok, key=lambda r: r["err_eta_l2"])["T_h"],
+                                   "min_err_u": min(r["err_u_hdiv"] for r in ok),
+                                   "min_err_eta": min(r["err_eta_l2"] for r in ok)}
+    m.close()
+    return res
+
+
 # ----------------------------------------------------------------------------- CPU oracle leg
 # The oracle's sample at the benchmark configuration: the complete literal
 # terms w_m e^{-s_m L} N(e^{s_m L} U) of the ORACLE_GROUP central shifts
@@ -765,6 +828,7 @@ def run_pavg(args):
     day_r5 = _day_r5(pavg) if "day_r5" in legs else None
     surrogate = _surrogate_leg(pavg, sur_states) if "surrogate" in legs else None
     groups = _shift_groups_leg(model, cfg, Ud, ms / args.steps, out) if "groups" in legs else None
+    tc5 = _tc5_leg(pavg, args.days) if "tc5" in legs else None
 
     # parity against the oracle (computed by the spawned leg): the small
     # configuration in full, and the central shift group at the benchmark size
@@ -841,7 +905,7 @@ def run_pavg(args):
                     "d2h_bytes_per_step": 8 * model.n},
             "gpu_launches": st["kernel_launches"] * args.steps,
             "roofline": roof, "cpu_baseline": cpu, "parity": parity, "precision_mixed": mixed, "literal": literal, "precision_days": days, "day_r5": day_r5, "batch": batch, "surrogate": surrogate,
-            "shift_groups": groups,
+            "shift_groups": groups, "tc5": tc5,
             "clocks": clk,
             "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
             "alu_peaks_measured_tflops": ALU_PEAKS,
@@ -864,8 +928,8 @@ def main():
     ap.add_argument("--batch-max-r", type=int, default=None, help="largest refinement of the batched leg (profiling only)")
     ap.add_argument("--legs", default="fp64,mixed,literal,batch,surrogate,groups",
                     help="comma list: fp64 (always), mixed, literal, batch, surrogate, groups, precision_days, "
-                         "day_r5 (single GPU only)")
-    ap.add_argument("--days", type=float, default=1.0, help="simulated days of the precision_days leg")
+                         "day_r5, tc5 (single GPU only)")
+    ap.add_argument("--days", type=float, default=1.0, help="simulated days of the precision_days and tc5 legs")
     ap.add_argument("--refinement", type=int, default=None, help="smaller case (profiling only)")
     ap.add_argument("--M", type=int, default=None, help="number of shifts (profiling only)")
     args = ap.parse_args()

@@ -204,6 +204,13 @@ int pavg_timestep(pavg_ctx* ctx, double dt, double T, int M, double* U_inout, in
  * by the next pavg_sync: LU is valid only once pavg_sync returns PAVG_OK. */
 int pavg_linear_noalloc(pavg_ctx* ctx, const double* U, double* LU, void* stream);
 
+/* The paper's error norms of a state U (device, n doubles; Sec. 3):
+ * out[0] = ||u||_{L2} = sqrt(u^T M1 u), out[1] = ||u||_{H(div)} =
+ * sqrt(||u||^2 + ||div u||^2) with div u the DG1 field M2^{-1} D u, and
+ * out[2] = ||eta||_{L2} = sqrt(eta^T M2 eta) (host array of 3).  Runs on
+ * `stream` and synchronises it. */
+int pavg_norms(pavg_ctx* ctx, const double* U, double* out, void* stream);
+
 /* Wait for the context's work on `stream` and report latched device errors. */
 int pavg_sync(pavg_ctx* ctx, void* stream);
 
@@ -298,6 +305,9 @@ typedef struct {
 } pavg_batch_config;
 
 /* ctxs: host array of n distinct contexts on the current device, n >= 1.
+ * The persistent chains run their own mass solves (FP32 conjugate gradients
+ * refined by FP64 residuals, as PAVG_SOLVER_MIXED) whichever of the two
+ * mixed solvers the contexts use.
  * Errors: INVAL (null, n < 1, a repeated context, a context with the FP64
  * solver or on another device), NOMEM. */
 int pavg_batch_create(pavg_ctx* const* ctxs, int n, pavg_batch** out);

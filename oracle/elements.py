@@ -78,13 +78,82 @@ def _dof_functionals(fields):
     return np.array(rows)
 
 
+def _exact_vandermonde():
+    """V[k][l] = l_k(m_l) in exact rational arithmetic.
+
+    Along edge i, x = sx + tau dx and y = sy + tau dy with integer start and
+    direction, so a monomial is a polynomial in tau with integer coefficients
+    and int_0^1 tau^k dtau = 1/(k+1); over the triangle,
+    int x^a y^b = a! b! / (a + b + 2)!."""
+    from fractions import Fraction
+    from math import factorial
+
+    def mul(a, b):
+        r = [0] * (len(a) + len(b) - 1)
+        for i, x in enumerate(a):
+            for j, y in enumerate(b):
+                r[i + j] += x * y
+        return r
+
+    def power(p, n):
+        r = [1]
+        for _ in range(n):
+            r = mul(r, p)
+        return r
+
+    powers = [(0, 0), (1, 0), (0, 1), (2, 0), (1, 1), (0, 2)]      # the scalar monomials' (a, b)
+    legendre = [[1], [-1, 2], [1, -6, 6]]                           # p_j in powers of tau
+    V = [[Fraction(0)] * 12 for _ in range(12)]
+    for i in range(3):
+        sx, sy = (int(v) for v in EDGE_START[i])
+        dx, dy = (int(v) for v in EDGE_DIR[i])
+        for j in range(3):
+            for l in range(12):
+                a, b = powers[l % 6]
+                m = mul(power([sx, dx], a), power([sy, dy], b))
+                flux = [c * (dy if l < 6 else -dx) for c in m]  # cross2(m_l, d_i)
+                V[3 * i + j][l] = sum(Fraction(c, k + 1) for k, c in enumerate(mul(flux, legendre[j])))
+
+    def tri(a, b):
+        return Fraction(factorial(a) * factorial(b), factorial(a + b + 2))
+
+    for l in range(12):
+        a, b = powers[l % 6]
+        V[9][l] = tri(a, b) if l < 6 else Fraction(0)               # q_0 = (1, 0)
+        V[10][l] = tri(a, b) if l >= 6 else Fraction(0)             # q_1 = (0, 1)
+        V[11][l] = -tri(a, b + 1) if l < 6 else tri(a + 1, b)       # q_2 = (-y, x)
+    return V
+
+
+def _exact_inverse(V):
+    """Gauss-Jordan elimination in exact rational arithmetic."""
+    from fractions import Fraction
+    n = len(V)
+    A = [list(row) + [Fraction(int(i == k)) for k in range(n)] for i, row in enumerate(V)]
+    for col in range(n):
+        piv = next(r for r in range(col, n) if A[r][col] != 0)
+        A[col], A[piv] = A[piv], A[col]
+        pv = A[col][col]
+        A[col] = [x / pv for x in A[col]]
+        for r in range(n):
+            if r != col and A[r][col] != 0:
+                f = A[r][col]
+                A[r] = [x - f * y for x, y in zip(A[r], A[col])]
+    return [row[n:] for row in A]
+
+
 class BDM2:
-    """Reference BDM2 basis as coefficients over the vector monomials."""
+    """Reference BDM2 basis as coefficients over the vector monomials.
+
+    The basis is dual to the DOF functionals, l_k(psi_i) = delta_ki: the
+    coefficients are the inverse of V[k][l] = l_k(m_l), computed exactly in
+    rational arithmetic (it has integer entries) so that the basis carries no
+    rounding from an inversion of the moderately conditioned V (cond ~ 530)."""
 
     def __init__(self):
-        V = _dof_functionals(_vector_monomials)              # V[k, l] = l_k(m_l)
-        self.vandermonde = V
-        self.coeffs = np.linalg.inv(V)                       # psi_i = sum_l coeffs[l, i] m_l
+        Vq = _exact_vandermonde()
+        self.vandermonde = np.array([[float(x) for x in row] for row in Vq])
+        self.coeffs = np.array([[float(x) for x in row] for row in _exact_inverse(Vq)])  # psi_i = sum_l coeffs[l, i] m_l
 
     def values(self, xi):
         """psi_i(xi) -> (Q, 12, 2)."""

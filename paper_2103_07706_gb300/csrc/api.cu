@@ -826,6 +826,25 @@ int pavg_timestep(pavg_ctx* ctx, double dt, double T, int M, double* U, int nste
   return PAVG_OK;
 }
 
+int pavg_norms(pavg_ctx* ctx, const double* U, double* out, void* stream) {
+  if (!ctx || !U || !out) return PAVG_ERR_INVAL;
+  int nb = 0;
+  cudaStream_t st = S(stream);
+  KL(launch_norms(ctx->dm, U, ctx->dpart, &nb, st));
+  CK(cudaMemcpyAsync(ctx->host_part, ctx->dpart, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  double a = 0.0, d = 0.0, e = 0.0;
+  for (int i = 0; i < nb; ++i) {
+    a += ctx->host_part[3 * i];
+    d += ctx->host_part[3 * i + 1];
+    e += ctx->host_part[3 * i + 2];
+  }
+  out[0] = std::sqrt(a);
+  out[1] = std::sqrt(a + d);
+  out[2] = std::sqrt(e);
+  return PAVG_OK;
+}
+
 int pavg_sync(pavg_ctx* ctx, void* stream) {
   if (!ctx) return PAVG_ERR_INVAL;
   CK(cudaStreamSynchronize(S(stream)));

@@ -528,7 +528,7 @@ int pavg_batch_create(pavg_ctx* const* ctxs, int n, pavg_batch** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return PAVG_ERR_CUDA;
   for (int i = 0; i < n; ++i) {
-    if (!ctxs[i] || ctxs[i]->device != dev || ctxs[i]->p.solver != PAVG_SOLVER_MIXED) return PAVG_ERR_INVAL;
+    if (!ctxs[i] || ctxs[i]->device != dev || ctxs[i]->p.solver == PAVG_SOLVER_FP64) return PAVG_ERR_INVAL;
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == ctxs[i]) return PAVG_ERR_INVAL;
   }

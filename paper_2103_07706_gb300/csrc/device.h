@@ -271,6 +271,9 @@ cudaError_t launch_lincomb(double* out, double a, const double* x, double b, con
 cudaError_t launch_winner(const DeviceMesh& m, const double* U, const double* V, double g, double H,
                           double* part, int* nblocks, cudaStream_t st);
 
+// Per-block partial sums [nblocks][3] of u^T M1 u, ||div u||^2 and eta^T M2 eta.
+cudaError_t launch_norms(const DeviceMesh& m, const double* U, double* part, int* nblocks, cudaStream_t st);
+
 // Sets kFlagNonFinite when any entry of x is not finite.
 cudaError_t launch_check_finite(const double* x, int64_t len, int* flags, cudaStream_t st);
 

@@ -630,6 +630,47 @@ __global__ void __launch_bounds__(256) k_winner(DeviceMesh m, const double* __re
   if (threadIdx.x == 0) part[blockIdx.x] = s3[0];
 }
 
+// The paper's error norms (Sec. 3) per cell, summed over the block:
+// u^T M1 u, the L2 norm squared of div u (the DG1 field D u / M2, so
+// (D_K u)^T M2_K^{-1} (D_K u) on the cell) and eta^T M2 eta.
+__global__ void __launch_bounds__(256) k_norms(DeviceMesh m, const double* __restrict__ U, double* part) {
+  double a = 0.0, dv = 0.0, e = 0.0;
+  for (int64_t c = (int64_t)blockIdx.x * 256 + threadIdx.x; c < m.F; c += (int64_t)gridDim.x * 256) {
+    int dof[12];
+    double sg[12], u[12], w[12];
+    cell_dofs(m, c, dof, sg);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) u[k] = U[dof[k]];
+    spmv_cell(m.M1, m.F, c, u, w);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) a = fma(u[k], w[k], a);
+    const double det = m.det[c];
+    double d[3], h[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      double t = 0.0;
+#pragma unroll
+      for (int i = 0; i < 12; ++i) t = fma(c_tab.D[k][i] * sg[i], u[i], t);
+      d[k] = t;
+      h[k] = U[m.n_u + 3 * c + k];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        dv = fma(d[k] * c_tab.M2inv_ref[k][l] / det, d[l], dv);
+        e = fma(h[k] * c_tab.M2_ref[k][l] * det, h[l], e);
+      }
+  }
+  double s3[3];
+  block_sum3<256>(a, dv, e, s3);
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x] = s3[0];
+    part[3 * blockIdx.x + 1] = s3[1];
+    part[3 * blockIdx.x + 2] = s3[2];
+  }
+}
+
 __global__ void k_check_finite(const double* __restrict__ x, int64_t len, int* flags) {
   bool bad = false;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < len; j += (int64_t)gridDim.x * blockDim.x)
@@ -747,6 +788,13 @@ cudaError_t launch_winner(const DeviceMesh& m, const double* U, const double* V,
                           double* part, int* nblocks, cudaStream_t st) {
   int nb = grid_for(m.F, 256, 304);
   k_winner<<<nb, 256, 0, st>>>(m, U, V, g, H, part);
+  *nblocks = nb;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norms(const DeviceMesh& m, const double* U, double* part, int* nblocks, cudaStream_t st) {
+  int nb = grid_for(m.F, 256, 304);
+  k_norms<<<nb, 256, 0, st>>>(m, U, part);
   *nblocks = nb;
   return cudaGetLastError();
 }

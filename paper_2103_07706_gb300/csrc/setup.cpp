@@ -3,6 +3,7 @@
 // Riemann-sum weights.  Compiled with -ffp-contract=off so that vertex
 // coordinates are rounded identically on every host.
 #include <algorithm>
+#include <numeric>
 #include <array>
 #include <cmath>
 #include <complex>
@@ -229,11 +230,6 @@ void vmono(double x, double y, double v[12][2]) {
     v[l][1] = l < 6 ? 0.0 : m[l - 6];
   }
 }
-double legendre01(int j, double t) {
-  if (j == 0) return 1.0;
-  if (j == 1) return 2.0 * t - 1.0;
-  return 6.0 * t * t - 6.0 * t + 1.0;
-}
 
 bool invert(int n, const double* A, double* out) {
   std::vector<double> a(A, A + n * n), inv(n * n, 0.0);
@@ -267,42 +263,80 @@ bool invert(int n, const double* A, double* out) {
 // Degrees of freedom of BDM2 (paper Sec. 2.5: V1 = BDM2): Legendre moments of
 // the outward flux on each edge (counter-clockwise parameter), and interior
 // moments against (1,0), (0,1), (-y,x).  The basis is dual to them.
+// Exact rational numbers with small numerators and denominators: the BDM2
+// Vandermonde matrix and its inverse have entries of at most a few hundred.
+struct Rat {
+  int64_t n = 0, d = 1;
+  Rat() = default;
+  Rat(int64_t num, int64_t den = 1) : n(num), d(den) {
+    if (d < 0) { n = -n; d = -d; }
+    int64_t g = std::gcd(n < 0 ? -n : n, d);
+    if (g > 1) { n /= g; d /= g; }
+  }
+};
+Rat operator+(Rat a, Rat b) { return Rat(a.n * b.d + b.n * a.d, a.d * b.d); }
+Rat operator-(Rat a, Rat b) { return Rat(a.n * b.d - b.n * a.d, a.d * b.d); }
+Rat operator*(Rat a, Rat b) { return Rat(a.n * b.n, a.d * b.d); }
+Rat operator/(Rat a, Rat b) { return Rat(a.n * b.d, a.d * b.n); }
+
+// Product of two polynomials in one variable (integer coefficients, lowest first).
+std::vector<int64_t> pmul(const std::vector<int64_t>& a, const std::vector<int64_t>& b) {
+  std::vector<int64_t> r(a.size() + b.size() - 1, 0);
+  for (size_t i = 0; i < a.size(); ++i)
+    for (size_t j = 0; j < b.size(); ++j) r[i + j] += a[i] * b[j];
+  return r;
+}
+
+// The reference BDM2 basis is dual to the DOF functionals, l_k(psi_i) =
+// delta_ki: its coefficients over the vector monomials are the inverse of
+// V[k][l] = l_k(m_l).  Every entry of V is rational (along edge i,
+// x = sx + tau dx and y = sy + tau dy have integer start and direction, so a
+// monomial is an integer polynomial in tau and int_0^1 tau^k = 1/(k+1); over
+// the triangle int x^a y^b = a! b! / (a+b+2)!), and so is the inverse (its
+// entries are integers), so both are computed exactly and the basis carries
+// no rounding from inverting V (cond(V) is about 530).
 void build_reference_element(RefElement* el) {
-  double V[12][12];  // V[k][l] = dof_k(vector monomial l)
-  double gx[6], gw[6];
-  gauss_legendre01(6, gx, gw);
+  const int pa[6] = {0, 1, 0, 2, 1, 0}, pb[6] = {0, 0, 1, 0, 1, 2};  // monomial 1, x, y, xx, xy, yy
+  const std::vector<int64_t> leg[3] = {{1}, {-1, 2}, {1, -6, 6}};
+  const int64_t es[3][2] = {{1, 0}, {0, 1}, {0, 0}}, ed[3][2] = {{-1, 1}, {0, -1}, {1, 0}};
+  Rat V[12][24];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j)
       for (int l = 0; l < 12; ++l) {
-        double s = 0;
-        for (int q = 0; q < 6; ++q) {
-          double x = kEdgeStart[i][0] + gx[q] * kEdgeDir[i][0];
-          double y = kEdgeStart[i][1] + gx[q] * kEdgeDir[i][1];
-          double v[12][2];
-          vmono(x, y, v);
-          double flux = v[l][0] * kEdgeDir[i][1] - v[l][1] * kEdgeDir[i][0];
-          s += gw[q] * flux * legendre01(j, gx[q]);
-        }
+        std::vector<int64_t> m = {1};
+        for (int k = 0; k < pa[l % 6]; ++k) m = pmul(m, {es[i][0], ed[i][0]});
+        for (int k = 0; k < pb[l % 6]; ++k) m = pmul(m, {es[i][1], ed[i][1]});
+        const int64_t fx = l < 6 ? ed[i][1] : -ed[i][0];  // cross2(m_l, d_i)
+        std::vector<int64_t> p = pmul(m, leg[j]);
+        Rat s(0);
+        for (size_t k = 0; k < p.size(); ++k) s = s + Rat(p[k] * fx, (int64_t)k + 1);
         V[3 * i + j][l] = s;
       }
-  std::vector<double> tx, ty, tw;
-  triangle_gl(5, &tx, &ty, &tw);
-  for (int j = 0; j < 3; ++j)
-    for (int l = 0; l < 12; ++l) {
-      double s = 0;
-      for (size_t q = 0; q < tx.size(); ++q) {
-        double v[12][2];
-        vmono(tx[q], ty[q], v);
-        double qx = j == 0 ? 1.0 : (j == 1 ? 0.0 : -ty[q]);
-        double qy = j == 0 ? 0.0 : (j == 1 ? 1.0 : tx[q]);
-        s += tw[q] * (v[l][0] * qx + v[l][1] * qy);
-      }
-      V[9 + j][l] = s;
+  auto fact = [](int n) { int64_t f = 1; for (int k = 2; k <= n; ++k) f *= k; return f; };
+  auto tri = [&](int a, int b) { return Rat(fact(a) * fact(b), fact(a + b + 2)); };
+  for (int l = 0; l < 12; ++l) {
+    const int a = pa[l % 6], b = pb[l % 6];
+    V[9][l] = l < 6 ? tri(a, b) : Rat(0);                      // q_0 = (1, 0)
+    V[10][l] = l < 6 ? Rat(0) : tri(a, b);                     // q_1 = (0, 1)
+    V[11][l] = l < 6 ? Rat(0) - tri(a, b + 1) : tri(a + 1, b); // q_2 = (-y, x)
+  }
+  for (int r = 0; r < 12; ++r)
+    for (int c = 0; c < 12; ++c) V[r][12 + c] = Rat(r == c ? 1 : 0);
+  for (int col = 0; col < 12; ++col) {  // Gauss-Jordan, exact
+    int piv = col;
+    while (piv < 12 && V[piv][col].n == 0) ++piv;
+    if (piv == 12) throw std::runtime_error("BDM2 Vandermonde is singular");
+    for (int c = 0; c < 24; ++c) std::swap(V[col][c], V[piv][c]);
+    const Rat pv = V[col][col];
+    for (int c = 0; c < 24; ++c) V[col][c] = V[col][c] / pv;
+    for (int r = 0; r < 12; ++r) {
+      if (r == col || V[r][col].n == 0) continue;
+      const Rat f = V[r][col];
+      for (int c = 0; c < 24; ++c) V[r][c] = V[r][c] - f * V[col][c];
     }
-  double inv[144];
-  if (!invert(12, &V[0][0], inv)) throw std::runtime_error("BDM2 Vandermonde is singular");
+  }
   for (int l = 0; l < 12; ++l)
-    for (int i = 0; i < 12; ++i) el->coef[l][i] = inv[l * 12 + i];
+    for (int i = 0; i < 12; ++i) el->coef[l][i] = (double)V[l][12 + i].n / (double)V[l][12 + i].d;
 }
 
 void RefElement::eval(double x, double y, double val[12][2]) const {

@@ -88,29 +88,11 @@ def canonical_edges(cells):
     return np.unique(pairs, axis=0)
 
 
-def harmonic_state(verts, cells, seed, lmax, eta_rms=100.0, g=9.80616, omega=7.292e-5):
-    """Balanced seeded state U = [u (3E + 3F), eta (3F)] as float64.
-
-    Returns (U, info) with info = {"rossby": ..., "u_rms": ...}.
-    """
-    verts = np.asarray(verts, dtype=np.float64)
-    cells = np.asarray(cells, dtype=np.int64)
-    edges = canonical_edges(cells)
+def velocity_dofs_from_streamfunction(verts, cells, edges, psi):
+    """BDM2 degrees of freedom of u = k x grad psi (divergence free), from point
+    values of psi only (see the module docstring); psi maps points (..., 3)
+    to values (...)."""
     F, E = len(cells), len(edges)
-    rng = np.random.Generator(np.random.PCG64(seed))
-    coeffs = np.zeros((lmax + 1, 2 * lmax + 1))
-    for l in range(1, lmax + 1):
-        coeffs[l, lmax - l: lmax + l + 1] = rng.standard_normal(2 * l + 1) * l ** -1.5
-    # elevation at vertices, scaled to the requested rms over the DG1 DOFs
-    eta_v = real_sph_harm_sum(verts, coeffs, lmax)
-    eta = eta_v[cells].reshape(-1)
-    scale = eta_rms / math.sqrt(np.mean(eta * eta))
-    eta *= scale
-    f0 = 2.0 * omega * math.sin(math.pi / 4.0)
-
-    def psi(x):
-        return g * scale * real_sph_harm_sum(x, coeffs, lmax) / f0
-
     u = np.zeros(3 * E + 3 * F)
     # edge moments: -int_0^1 psi'(tau) p_j(tau) dtau by parts
     tau, wt = _gl01(6)
@@ -146,13 +128,69 @@ def harmonic_state(verts, cells, seed, lmax, eta_rms=100.0, g=9.80616, omega=7.2
     x = a[:, None, :] + xi[None, :, 0:1] * J0[:, None, :] + xi[None, :, 1:2] * J1[:, None, :]
     mom[:, 2] -= 2.0 * psi(x) @ wtri
     u[3 * E:] = mom.reshape(-1)
+    return u
+
+
+def harmonic_state(verts, cells, seed, lmax, eta_rms=100.0, g=9.80616, omega=7.292e-5):
+    """Balanced seeded state U = [u (3E + 3F), eta (3F)] as float64.
+
+    Returns (U, info) with info = {"rossby": ..., "u_rms": ...}.
+    """
+    verts = np.asarray(verts, dtype=np.float64)
+    cells = np.asarray(cells, dtype=np.int64)
+    edges = canonical_edges(cells)
+    F, E = len(cells), len(edges)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    coeffs = np.zeros((lmax + 1, 2 * lmax + 1))
+    for l in range(1, lmax + 1):
+        coeffs[l, lmax - l: lmax + l + 1] = rng.standard_normal(2 * l + 1) * l ** -1.5
+    # elevation at vertices, scaled to the requested rms over the DG1 DOFs
+    eta_v = real_sph_harm_sum(verts, coeffs, lmax)
+    eta = eta_v[cells].reshape(-1)
+    scale = eta_rms / math.sqrt(np.mean(eta * eta))
+    eta *= scale
+    f0 = 2.0 * omega * math.sin(math.pi / 4.0)
+
+    def psi(x):
+        return g * scale * real_sph_harm_sum(x, coeffs, lmax) / f0
+
+    u = velocity_dofs_from_streamfunction(verts, cells, edges, psi)
     # diagnostics: rms velocity from the edge flux densities, Rossby number
-    elen = np.linalg.norm(xhi - xlo, axis=1)
+    elen = np.linalg.norm(verts[edges[:, 1]] - verts[edges[:, 0]], axis=1)
     u_rms = math.sqrt(np.mean((u[0:3 * E:3] / elen) ** 2))
     radius = float(np.linalg.norm(verts[0]))
     l_eff = max(1.0, float(np.sqrt(np.sum(coeffs ** 2 * np.arange(lmax + 1)[:, None] ** 2) / np.sum(coeffs ** 2))))
     rossby = u_rms / (f0 * math.pi * radius / l_eff)
     return np.concatenate([u, eta]), {"rossby": rossby, "u_rms": u_rms, "edges": E, "cells": F}
+
+
+def tc5_state(verts, cells, u0=20.0, H=5960.0, g=9.8, omega=7.292e-5, b0=2000.0, lat_c=math.pi / 6.0,
+              lon_c=-math.pi / 2.0, r0=math.pi / 9.0):
+    """Williamson's test case 5 as Sec. 3 states it: zonal flow
+    u = (u0 / R)(-y, x, 0) in geostrophic balance with the layer depth
+    h = H - (R Omega u0 + u0^2 / 2) z^2 / (g R^2), over a cone-shaped mountain
+    b = b0 (1 - min(r0, d) / r0), d^2 = (lat - lat_c)^2 + (lon - lon_c)^2, the
+    longitude difference wrapped to [-pi, pi].  The paper's constants are the
+    defaults (Omega = 7.292e-5 s^-1 and u0 = 20 m/s, where the printed
+    exponent and unit are typographical slips).
+
+    Returns (U, b): U = [u, eta] with eta = h - H the elevation of the free
+    surface (the depth is H + eta - b), and b at the DG1 nodes (cell vertices).
+    u = k x grad psi with psi = -u0 z (divergence free); eta and b are nodal
+    values at the cell vertices."""
+    verts = np.asarray(verts, dtype=np.float64)
+    cells = np.asarray(cells, dtype=np.int64)
+    edges = canonical_edges(cells)
+    R = float(np.linalg.norm(verts[0]))
+    u = velocity_dofs_from_streamfunction(verts, cells, edges, lambda x: -u0 * x[..., 2])
+    z = verts[:, 2]
+    eta_v = -(R * omega * u0 + 0.5 * u0 * u0) * z * z / (g * R * R)
+    lat = np.arcsin(np.clip(z / R, -1.0, 1.0))
+    lon = np.arctan2(verts[:, 1], verts[:, 0])
+    dlon = (lon - lon_c + math.pi) % (2.0 * math.pi) - math.pi
+    d = np.sqrt((lat - lat_c) ** 2 + dlon ** 2)
+    b_v = b0 * (1.0 - np.minimum(r0, d) / r0)
+    return np.concatenate([u, eta_v[cells].reshape(-1)]), b_v[cells].reshape(-1)
 
 
 # lambda_max of L per refinement (R = 6.37122e6 m, Omega = 7.292e-5 s^-1,

@@ -34,7 +34,7 @@ ERRORS = {
 EXPORTED = [
     "pavg_default_params", "pavg_create", "pavg_destroy", "pavg_sizes", "pavg_mesh_export",
     "pavg_set_topography", "pavg_lambda_max", "pavg_linear", "pavg_nonlinear", "pavg_expL_apply",
-    "pavg_averaged_rhs", "pavg_averaged_rhs_group", "pavg_averaged_rhs_literal", "pavg_timestep", "pavg_sync", "pavg_get_stats",
+    "pavg_averaged_rhs", "pavg_averaged_rhs_group", "pavg_averaged_rhs_literal", "pavg_timestep", "pavg_sync", "pavg_norms", "pavg_get_stats",
     "pavg_reset_stats", "pavg_last_error", "pavg_kernel_timing", "pavg_kernel_time", "pavg_linear_noalloc", "pavg_measure_fma_peak", "pavg_test_stall",
     "pavg_batch_create", "pavg_batch_destroy", "pavg_batch_averaged_rhs", "pavg_batch_autotune",
     "pavg_batch_set_config", "pavg_batch_get_config", "pavg_batch_kernel_time", "pavg_batch_sync",
@@ -117,6 +117,7 @@ def load(path=LIB_PATH):
         "pavg_averaged_rhs_literal": (I, [P, D, I, P, P, V]),
         "pavg_timestep": (I, [P, D, D, I, P, I, V]),
         "pavg_sync": (I, [P, V]),
+        "pavg_norms": (I, [P, P, P, V]),
         "pavg_get_stats": (I, [P, ctypes.POINTER(Stats)]),
         "pavg_reset_stats": (I, [P]),
         "pavg_last_error": (ctypes.c_char_p, [P]),
@@ -273,6 +274,13 @@ class Model:
         """Test aid: make one block of the subdomain solver stall (pavg.h)."""
         self._check(self._lib.pavg_test_stall(self._h, int(mode), int(part), float(wait_us)))
 
+    def norms(self, U):
+        """(||u||_L2, ||u||_H(div), ||eta||_L2) of a state (the paper's error norms)."""
+        import numpy as np
+        out = np.zeros(3)
+        self._check(self._lib.pavg_norms(self._h, _ptr(U, self.n), out.ctypes.data_as(ctypes.c_void_p), _stream()))
+        return tuple(float(x) for x in out)
+
     def sync(self):
         self._check(self._lib.pavg_sync(self._h, _stream()))
 
@@ -413,6 +421,13 @@ class Batch:
         f, g = ctypes.c_double(), ctypes.c_double()
         self._check(self._lib.pavg_batch_kernel_time(self._h, ctypes.byref(f), ctypes.byref(g)))
         return f.value, g.value
+
+    def norms(self, U):
+        """(||u||_L2, ||u||_H(div), ||eta||_L2) of a state (the paper's error norms)."""
+        import numpy as np
+        out = np.zeros(3)
+        self._check(self._lib.pavg_norms(self._h, _ptr(U, self.n), out.ctypes.data_as(ctypes.c_void_p), _stream()))
+        return tuple(float(x) for x in out)
 
     def sync(self):
         self._check(self._lib.pavg_batch_sync(self._h, _stream()))

@@ -443,3 +443,14 @@ def test_empty_batches_are_no_ops():
         assert f(empty).numel() == 0
     assert g.expL(600.0, empty).numel() == 0
     g.sync()
+
+
+@pytest.mark.parametrize("r", [2, 4])
+def test_norms_match_oracle(r):
+    """pavg_norms: the L2 norm of u, its H(div) norm and the L2 norm of eta
+    (the error norms of Sec. 3) against the oracle's assembled matrices."""
+    g, o = gpu(r), orc(r)
+    U = np.random.default_rng(9).standard_normal(o.n)
+    got = g.norms(dev(U))
+    want = o.ops.norms(U)
+    assert np.allclose(got, want, rtol=1e-13, atol=0), (got, want)

@@ -143,3 +143,19 @@ def test_mass_matrix_spd_and_velocity_mass_closed_form():
         e = d @ (A.M1_e[c] * np.outer(A.sign[c], A.sign[c])) @ d
         want = uh @ A.G[c] @ uh / A.det[c] * 0.5
         assert abs(e / want - 1) < 1e-13
+
+
+def test_dual_basis_is_exact():
+    """The BDM2 basis is dual to the DOF functionals (l_k(psi_i) = delta_ki).
+    Its coefficients come from an exact rational inverse of V; they are
+    integers, V times them is the identity without rounding, the exact V
+    equals the functionals applied by quadrature, and a floating-point
+    inverse of the quadrature V agrees to its own rounding (cond(V) ~ 530)."""
+    from oracle.elements import BDM2, _dof_functionals, _vector_monomials
+    b = BDM2()
+    C = b.coeffs
+    assert np.array_equal(C, np.round(C)) and np.abs(C).max() == 120.0
+    assert np.abs(b.vandermonde @ C - np.eye(12)).max() <= 1e-13  # V rounded to doubles (1/3, 1/60, ...)
+    Vq = _dof_functionals(_vector_monomials)
+    assert np.abs(b.vandermonde - Vq).max() <= 1e-15
+    assert np.abs(np.linalg.inv(Vq) - C).max() <= 1e-11
