@@ -509,6 +509,39 @@ def _tc5_leg(pavg, days=1.0):
     return res
 
 
+def _marching_leg(model, Ud):
+    """Shift marching against the shared basis on the benchmark state:
+    wall time (CUDA events, after one warm-up each), mass solves per call and
+    the relative difference of the two results (the marching's extra
+    truncations at the tail threshold of Sec. 2.4)."""
+    import torch
+    res = []
+    nu = model.n_u
+    o1, o2 = torch.empty_like(Ud), torch.empty_like(Ud)
+    for Th, M in ((1.0, 64), (4.0, 8), (0.25, 16), (2.0, 4)):
+        T = Th * 3600.0
+        row = {"T_h": Th, "M": M}
+        for name, fn, o in (("shared", model.averaged_rhs, o1), ("marching", model.averaged_rhs_marching, o2)):
+            fn(T, M, Ud, o)
+            model.sync()
+            model.reset_stats()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn(T, M, Ud, o)
+            e1.record()
+            torch.cuda.synchronize()
+            model.sync()
+            row[f"{name}_ms"] = e0.elapsed_time(e1)
+            row[f"{name}_solves"] = model.stats()["cg_solves"]
+        row["rel_diff_u"] = float((o2[:nu] - o1[:nu]).norm() / o1[:nu].norm())
+        row["rel_diff_eta"] = float((o2[nu:] - o1[nu:]).norm() / o1[nu:].norm())
+        row["marching_over_shared"] = row["marching_ms"] / row["shared_ms"]
+        res.append(row)
+    return {"runs": res, "note": "shared basis: 2 K_max + 1 chain steps; marching: K(|s_0|) + (M - 1) K(ds) "
+                                 "each way plus M mass solves, and K(a + b) <= K(a) + K(b) + O(1), so the "
+                                 "shared basis needs fewer solves at every (T, M)"}
+
+
 # ----------------------------------------------------------------------------- CPU oracle leg
 # The oracle's sample at the benchmark configuration: the complete literal
 # terms w_m e^{-s_m L} N(e^{s_m L} U) of the ORACLE_GROUP central shifts
@@ -829,6 +862,7 @@ def run_pavg(args):
     surrogate = _surrogate_leg(pavg, sur_states) if "surrogate" in legs else None
     groups = _shift_groups_leg(model, cfg, Ud, ms / args.steps, out) if "groups" in legs else None
     tc5 = _tc5_leg(pavg, args.days) if "tc5" in legs else None
+    marching = _marching_leg(model, Ud) if "marching" in legs else None
 
     # parity against the oracle (computed by the spawned leg): the small
     # configuration in full, and the central shift group at the benchmark size
@@ -905,7 +939,7 @@ def run_pavg(args):
                     "d2h_bytes_per_step": 8 * model.n},
             "gpu_launches": st["kernel_launches"] * args.steps,
             "roofline": roof, "cpu_baseline": cpu, "parity": parity, "precision_mixed": mixed, "literal": literal, "precision_days": days, "day_r5": day_r5, "batch": batch, "surrogate": surrogate,
-            "shift_groups": groups, "tc5": tc5,
+            "shift_groups": groups, "tc5": tc5, "marching": marching,
             "clocks": clk,
             "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
             "alu_peaks_measured_tflops": ALU_PEAKS,
@@ -926,9 +960,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-n", type=int, default=None, help="instances of the batched leg (profiling only)")
     ap.add_argument("--batch-max-r", type=int, default=None, help="largest refinement of the batched leg (profiling only)")
-    ap.add_argument("--legs", default="fp64,mixed,literal,batch,surrogate,groups",
-                    help="comma list: fp64 (always), mixed, literal, batch, surrogate, groups, precision_days, "
-                         "day_r5, tc5 (single GPU only)")
+    ap.add_argument("--legs", default="fp64,mixed,literal,batch,surrogate,groups,marching",
+                    help="comma list: fp64 (always), mixed, literal, batch, surrogate, groups, marching, "
+                         "precision_days, day_r5, tc5 (single GPU only)")
     ap.add_argument("--days", type=float, default=1.0, help="simulated days of the precision_days and tc5 legs")
     ap.add_argument("--refinement", type=int, default=None, help="smaller case (profiling only)")
     ap.add_argument("--M", type=int, default=None, help="number of shifts (profiling only)")

@@ -167,6 +167,20 @@ int pavg_averaged_rhs_group(pavg_ctx* ctx, double T, int M, int m0, int m1, cons
 int pavg_averaged_rhs_literal(pavg_ctx* ctx, double T, int M, const double* U, double* out,
                               void* stream);
 
+/* The same average by shift marching: the shifts of both point rules are
+ * equally spaced (spacing ds), so the shifted states follow one another,
+ * V_0 = e^{s_0 L} U, V_{m+1} = e^{ds L} V_m, and the backward maps nest
+ * (Horner): H_{M-1} = w_{M-1} N(V_{M-1}), H_m = w_m N(V_m) + e^{-ds L} H_{m+1},
+ * out = e^{-s_0 L} H_0 (Sec. 2.2's sum with e^{s_{m+1} L} = e^{ds L} e^{s_m L}).
+ * It needs K(|s_0|) + (M-1) K(ds) chain steps each way (K(t) the degree of
+ * e^{tL}) against 2 K_max + 1 for the shared basis, and each short
+ * exponential is truncated by the tail rule of Sec. 2.4, so the result
+ * differs from pavg_averaged_rhs by those extra truncations (it equals the
+ * direct sum as cheb_tol -> 0).  Not graph-captured.  Same limits as
+ * pavg_averaged_rhs. */
+int pavg_averaged_rhs_marching(pavg_ctx* ctx, double T, int M, const double* U, double* out,
+                               void* stream);
+
 /* nsteps averaged Lawson RK4 steps of size dt (Sec. 2.3, Eqs. stage1_c to stage4),
  * in place on the device state U_inout (n doubles).  INVAL for a
  * non-finite dt or T, for lambda_max |dt| > PAVG_MAX_CHEB_ARG (each step

@@ -616,7 +616,8 @@ int pavg_create(const pavg_params* p, pavg_ctx** out) {
       SdParams& sp = ctx->sdp;
       sp.rtol = ctx->cgip.rtol;
       sp.max_sweeps = 8;
-      sp.iters = sd_iterations(a, bnd, mixed ? 1e-6 : 1e-5);
+      // cg_maxit caps the inner iterations of one refinement sweep, as for the mixed solver
+      sp.iters = std::min(sd_iterations(a, bnd, mixed ? 1e-6 : 1e-5), p->cg_maxit);
       sp.theta = 0.5 * (bnd + a);
       sp.delta = 0.5 * (bnd - a);
       sp.wait_cycles = kSdWaitCycles;
@@ -781,6 +782,61 @@ int pavg_averaged_rhs_literal(pavg_ctx* ctx, double T, int M, const double* U, d
   }
   CK(cudaMemcpyAsync(out, acc, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   return PAVG_OK;
+}
+
+// Shift marching (an alternative to the shared basis): the shifts of both
+// point rules are equally spaced, so V_0 = e^{s_0 L} U, V_{m+1} = e^{ds L} V_m,
+// and the backward sum nests (Horner): H_{M-1} = M^{-1} w_{M-1} r_{M-1},
+// H_m = M^{-1} w_m r_m + e^{-ds L} H_{m+1}, out = e^{-s_0 L} H_0, with r_m the
+// weak form of N(V_m).  Every short exponential is truncated by the tail rule
+// of Sec. 2.4, so the result differs from pavg_averaged_rhs by those extra
+// truncations.
+int pavg_averaged_rhs_marching(pavg_ctx* ctx, double T, int M, const double* U, double* out, void* stream) {
+  if (!ctx || !U || !out || M < 1 || !(T >= 0) || !std::isfinite(T)) return PAVG_ERR_INVAL;
+  if (out == U) return set_err(ctx, PAVG_ERR_INVAL, "pavg_averaged_rhs_marching: the output aliases the input");
+  CallScope scope_(ctx);
+  cudaStream_t st = S(stream);
+  const DeviceMesh& m = ctx->dm;
+  const int64_t n = m.n;
+  if (T == 0.0) return enq_nonlinear(ctx, U, out, ctx->vec[5], st);
+  std::vector<double> s, w;
+  int rc = shifts_weights(T, M, ctx->p.quad_rule, &s, &w);
+  if (rc) return set_err(ctx, rc, "invalid T / M / quadrature rule");
+  for (int k = 0; k < M; ++k)
+    if (cheb_coefficients(ctx->lam * std::fabs(s[k]), ctx->p.cheb_tol).empty())
+      return set_err(ctx, PAVG_ERR_INVAL, cheb_limit_msg(ctx->lam * std::fabs(s[k])));
+  rc = ensure_avg_workspace(ctx, std::max(ctx->Kcap, 0), M);
+  if (rc) return rc;
+  double* V = ctx->Um;  // [M][n] shifted states
+  double* R = ctx->Rm;  // [M][n] weak forms of N
+  if ((rc = enq_expL(ctx, s[0], U, V, st))) return rc;
+  for (int k = 1; k < M; ++k)
+    if ((rc = enq_expL(ctx, s[k] - s[k - 1], V + (int64_t)(k - 1) * n, V + (int64_t)k * n, st))) return rc;
+  const bool fp32 = ctx->p.precision == PAVG_PRECISION_MIXED;
+  CK(cudaMemset2DAsync(R, sizeof(double) * n, 0, sizeof(double) * 3 * m.E, M, st));
+  KL(launch_nonlinear_rhs(m, V, R, M, ctx->p.upwind_convention, st, fp32, ctx->facets, ctx->facet_chunk));
+  double* H = ctx->io_out;
+  double* wr = ctx->io_in;
+  double* tn = ctx->vec[4];
+  double* te = ctx->vec[5];
+  bool started = false;
+  for (int k = M - 1; k >= 0; --k) {
+    if (started) {
+      if ((rc = enq_expL(ctx, -(s[k + 1] - s[k]), H, te, st))) return rc;
+    }
+    if (w[k] != 0.0) {
+      KL(launch_lincomb(wr, w[k], R + (int64_t)k * n, 0.0, nullptr, 0.0, nullptr, n, st));
+      if ((rc = enq_mass_solve(ctx, wr, tn, st))) return rc;
+      if (started) KL(launch_lincomb(H, 1.0, tn, 1.0, te, 0.0, nullptr, n, st));
+      else CK(cudaMemcpyAsync(H, tn, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    } else if (started) {
+      CK(cudaMemcpyAsync(H, te, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    } else {
+      CK(cudaMemsetAsync(H, 0, sizeof(double) * n, st));
+    }
+    started = true;
+  }
+  return enq_expL(ctx, -s[0], H, out, st);
 }
 
 // Sec. 2.3 (Eqs. stage1_c to stage4), with E(t) = e^{tL} and N-bar the average:

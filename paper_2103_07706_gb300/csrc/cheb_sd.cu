@@ -492,7 +492,11 @@ cudaError_t sd_configure(int64_t F, int64_t E, const std::vector<int32_t>& tri, 
   if (e != cudaSuccess) return e;
   const size_t smem = sd_smem_bytes(part.max_cells, part.max_lt);
   if (part.max_lt > kSdRounds * kSdThreads || smem + fa.sharedSizeBytes > (size_t)optin) return cudaSuccess;
-  e = cudaFuncSetAttribute(k_cheb_sd<kSdThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the attribute belongs to the kernel (per device), not to this mesh: allow
+  // the largest block any mesh may need, so that configuring a small mesh
+  // after a large one does not make the large one's launches invalid
+  e = cudaFuncSetAttribute(k_cheb_sd<kSdThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin - (int)fa.sharedSizeBytes);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb_sd<kSdThreads>, kSdThreads, smem);

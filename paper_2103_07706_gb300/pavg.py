@@ -34,7 +34,7 @@ ERRORS = {
 EXPORTED = [
     "pavg_default_params", "pavg_create", "pavg_destroy", "pavg_sizes", "pavg_mesh_export",
     "pavg_set_topography", "pavg_lambda_max", "pavg_linear", "pavg_nonlinear", "pavg_expL_apply",
-    "pavg_averaged_rhs", "pavg_averaged_rhs_group", "pavg_averaged_rhs_literal", "pavg_timestep", "pavg_sync", "pavg_norms", "pavg_get_stats",
+    "pavg_averaged_rhs", "pavg_averaged_rhs_group", "pavg_averaged_rhs_literal", "pavg_averaged_rhs_marching", "pavg_timestep", "pavg_sync", "pavg_norms", "pavg_get_stats",
     "pavg_reset_stats", "pavg_last_error", "pavg_kernel_timing", "pavg_kernel_time", "pavg_linear_noalloc", "pavg_measure_fma_peak", "pavg_test_stall",
     "pavg_batch_create", "pavg_batch_destroy", "pavg_batch_averaged_rhs", "pavg_batch_autotune",
     "pavg_batch_set_config", "pavg_batch_get_config", "pavg_batch_kernel_time", "pavg_batch_sync",
@@ -115,6 +115,7 @@ def load(path=LIB_PATH):
         "pavg_averaged_rhs": (I, [P, D, I, P, P, V]),
         "pavg_averaged_rhs_group": (I, [P, D, I, I, I, P, P, V]),
         "pavg_averaged_rhs_literal": (I, [P, D, I, P, P, V]),
+        "pavg_averaged_rhs_marching": (I, [P, D, I, P, P, V]),
         "pavg_timestep": (I, [P, D, D, I, P, I, V]),
         "pavg_sync": (I, [P, V]),
         "pavg_norms": (I, [P, P, P, V]),
@@ -333,6 +334,13 @@ class Model:
         out = self._out(U, out)
         self._check(self._lib.pavg_averaged_rhs_group(self._h, float(T), int(M), int(m0), int(m1), _ptr(U, self.n),
                                                       _ptr(out, self.n), _stream()))
+        return out
+
+    def averaged_rhs_marching(self, T, M, U, out=None):
+        """The average by shift marching (pavg.h)."""
+        out = self._out(U, out)
+        self._check(self._lib.pavg_averaged_rhs_marching(self._h, float(T), int(M), _ptr(U, self.n),
+                                                         _ptr(out, self.n), _stream()))
         return out
 
     def averaged_rhs_literal(self, T, M, U, out=None):

@@ -454,3 +454,15 @@ def test_norms_match_oracle(r):
     got = g.norms(dev(U))
     want = o.ops.norms(U)
     assert np.allclose(got, want, rtol=1e-13, atol=0), (got, want)
+
+
+@pytest.mark.parametrize("r,T,M,rule", [(2, 3600.0, 8, 0), (3, 7200.0, 16, 0), (2, 3600.0, 7, 1)])
+def test_shift_marching_parity(r, T, M, rule):
+    """Shift marching (V_{m+1} = e^{ds L} V_m, Horner backward) on the GPU
+    against the oracle's marching at the same tail threshold (1e-6)."""
+    from oracle import averaging
+    g, o = gpu(r, quad_rule=rule), orc(r, quad_rule=rule)
+    U = state(o, eta_noise=5.0)
+    want = averaging.averaged_rhs_marching(o, T, M, U, rule)
+    assert_close(o, g.averaged_rhs_marching(T, M, dev(U)).cpu().numpy(), want)
+    g.sync()

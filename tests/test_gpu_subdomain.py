@@ -112,3 +112,18 @@ def test_stall_hook_arguments():
     with pytest.raises(pavg.PavgError):
         h.test_stall(1, 0, 100.0)
     h.close()
+
+
+def test_large_mesh_after_small_mesh():
+    """The kernel's dynamic shared-memory limit is one setting per device:
+    configuring a small mesh after a large one must not make the large one's
+    launches invalid (it did once, in the batched benchmark)."""
+    import torch
+    big = _model(6)
+    small = _model(3)
+    U = torch.from_numpy(np.random.default_rng(5).standard_normal(big.n)).cuda()
+    big.linear(U)
+    big.sync()
+    assert big.stats()["solver_in_use"] == 2 and small.stats()["solver_in_use"] == 2
+    small.close()
+    big.close()
