@@ -617,7 +617,7 @@ int pavg_create(const pavg_params* p, pavg_ctx** out) {
       sp.rtol = ctx->cgip.rtol;
       sp.max_sweeps = 8;
       // cg_maxit caps the inner iterations of one refinement sweep, as for the mixed solver
-      sp.iters = std::min(sd_iterations(a, bnd, mixed ? 1e-6 : 1e-5), p->cg_maxit);
+      sp.iters = std::min(std::min(sd_iterations(a, bnd, mixed ? 1e-6 : 1e-5), p->cg_maxit), 256);
       sp.theta = 0.5 * (bnd + a);
       sp.delta = 0.5 * (bnd - a);
       sp.wait_cycles = kSdWaitCycles;

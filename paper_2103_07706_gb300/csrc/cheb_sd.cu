@@ -47,6 +47,7 @@ namespace {
 constexpr int kSdThreads = 768;   // one thread per local cell (up to 768) and two triples each
 constexpr int kSdRounds = 2;      // local triples per thread at most
 constexpr int kSdMatStride = 79;  // floats per cell's packed matrix (78, padded: conflict-free columns)
+constexpr int kSdMaxIters = 256;  // Chebyshev iterations per sweep at most (the set-up caps it)
 
 __device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
   unsigned long long v;
@@ -193,6 +194,8 @@ __global__ void __launch_bounds__(NT, 1)
   float4* s_slot = s_d + sd.max_lt;
   double* s_x64 = reinterpret_cast<double*>(s_d);
   __shared__ unsigned long long s_base;
+  // the recurrence's scalars, the same in every sweep: d_{k+1} = c1[k] d_k + c2[k] P r_{k+1}
+  __shared__ float s_c1[kSdMaxIters], s_c2[kSdMaxIters];
 
   const int nb = gridDim.x, bid = blockIdx.x, tid = threadIdx.x;
   if (sp.stall_mode == 1 && bid == sp.stall_part) return;  // test hook: never arrives
@@ -207,7 +210,17 @@ __global__ void __launch_bounds__(NT, 1)
     const int idx = t / nc, k = t - idx * nc;
     s_mat[k * kSdMatStride + idx] = __ldg(&m.M1p[(int64_t)idx * F + c0 + k]);
   }
-  if (tid == 0) s_base = ld_relaxed64(&w.sync[2]);
+  if (tid == 0) {
+    s_base = ld_relaxed64(&w.sync[2]);
+    const double sigma = sp.theta / sp.delta;
+    double rho = 1.0 / sigma;
+    for (int k = 0; k < sp.iters && k < kSdMaxIters; ++k) {
+      const double rho_n = 1.0 / (2.0 * sigma - rho);
+      s_c1[k] = (float)(rho_n * rho);
+      s_c2[k] = (float)(2.0 * rho_n / sp.delta);
+      rho = rho_n;
+    }
+  }
   // ---- per-triple registers
   // d lives in shared memory only (s_d[lt], written and read by the thread that owns lt)
   float P[kSdRounds][6], r[kSdRounds][3], x[kSdRounds][3];
@@ -247,7 +260,7 @@ __global__ void __launch_bounds__(NT, 1)
   const double tol2 = sp.rtol * sp.rtol * bb;
   double rr = bb;
   int sweeps = 0;
-  const double sigma = sp.theta / sp.delta;
+  const float inv_theta = (float)(1.0 / sp.theta);
 
   while (alive && !bad && !conv && sweeps < sp.max_sweeps) {
     // ---- sweep start: r_0 = r / ||r|| in FP32, x_0 = 0, d_0 = P r_0 / theta
@@ -262,12 +275,10 @@ __global__ void __launch_bounds__(NT, 1)
         for (int k = 0; k < 3; ++k) r[j][k] = (float)(__ldcg(&w.r64[3 * (int64_t)(l0 + lt) + k]) * scale);
         float u[3];
         apply_p(P[j], r[j], u);
-        const float it = (float)(1.0 / sp.theta);
-        s_d[lt] = make_float4(u[0] * it, u[1] * it, u[2] * it, 0.f);
+        s_d[lt] = make_float4(u[0] * inv_theta, u[1] * inv_theta, u[2] * inv_theta, 0.f);
       }
     }
     __syncthreads();
-    double rho = 1.0 / sigma;
     for (int it = 0; it < sp.iters; ++it) {
       ++ep;
       const unsigned tag = (unsigned)(base + ep);
@@ -301,9 +312,7 @@ __global__ void __launch_bounds__(NT, 1)
       }
       __syncthreads();
       // ---- triple phase: M1 d on every local triple, then the recurrence
-      const double rho_n = 1.0 / (2.0 * sigma - rho);
-      const float c1 = (float)(rho_n * rho), c2 = (float)(2.0 * rho_n / sp.delta);
-      rho = rho_n;
+      const float c1 = s_c1[it], c2 = s_c2[it];
       const bool more = it + 1 < sp.iters;
       bool fail = false;
 #pragma unroll
