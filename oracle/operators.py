@@ -35,13 +35,18 @@ UPWIND_STANDARD = 0
 UPWIND_AS_PRINTED = 1
 
 
+ELEVATION_WEAK = 0
+ELEVATION_STRONG = 1
+
+
 class Operators:
-    def __init__(self, mesh, g, H, omega, radius, upwind=UPWIND_STANDARD):
+    def __init__(self, mesh, g, H, omega, radius, upwind=UPWIND_STANDARD, elevation_form=ELEVATION_WEAK):
         self.mesh = mesh
         self.asm = Assembly(mesh, omega, radius)
         self.g = float(g)
         self.H = float(H)
         self.upwind = upwind
+        self.elevation_form = elevation_form
         self.n_u = self.asm.n_u
         self.n_eta = self.asm.n_eta
         self.n = self.n_u + self.n_eta
@@ -106,7 +111,15 @@ class Operators:
         ke = 0.5 * np.einsum("fqa,fqa->fq", uh, Guh)             # det^2 |u|^2 / 2
         kin = np.einsum("q,qi,fq->fi", wq, divpsi, ke) / det[:, None] ** 2
         ru = vort + kin
-        re = np.einsum("q,ia,fqa,fq->fi", wq, DG1_GRADS, uh, hh)
+        strong = self.elevation_form == ELEVATION_STRONG
+        if strong:
+            # -int phi_i div(u h) = -int_ref phi_i (h div_hat u_hat + u_hat . grad_hat h)
+            divu = np.einsum("fj,qj->fq", c, divpsi)
+            gradh = np.einsum("fk,ka->fa", h, DG1_GRADS)               # DG1: constant per cell
+            g_ = hh * divu + np.einsum("fqa,fa->fq", uh, gradh)
+            re = -np.einsum("q,qi,fq->fi", wq, phi, g_)
+        else:
+            re = np.einsum("q,ia,fqa,fq->fi", wq, DG1_GRADS, uh, hh)
         # ---- facet integrals
         tau, wt = gauss_legendre_01(FACET_POINTS)
         cp, cm = self.mesh.edge_cells[:, 0], self.mesh.edge_cells[:, 1]
@@ -135,8 +148,12 @@ class Operators:
         qm = cross2(um[:, :, None, :], psim) / det[cm][:, None, None]
         fp = -np.einsum("p,epi,ep->ei", wt, qp, tan)
         fm = np.einsum("p,epi,ep->ei", wt, qm, tan)
-        gp = -np.einsum("p,epi,ep->ei", wt, phip, flux * h_up)
-        gm = np.einsum("p,epi,ep->ei", wt, phim, flux * h_up)
+        if strong:   # int_dK phi (h_own - h~) u . n_out, u . n_out = +flux (plus cell), -flux (minus cell)
+            gp = np.einsum("p,epi,ep->ei", wt, phip, flux * (hp - h_up))
+            gm = np.einsum("p,epi,ep->ei", wt, phim, flux * (h_up - hm))
+        else:
+            gp = -np.einsum("p,epi,ep->ei", wt, phip, flux * h_up)
+            gm = np.einsum("p,epi,ep->ei", wt, phim, flux * h_up)
         np.add.at(ru, cp, fp)
         np.add.at(ru, cm, fm)
         np.add.at(re, cp, gp)

@@ -315,8 +315,10 @@ __global__ void __launch_bounds__(NT, 1)
       const float c1 = s_c1[it], c2 = s_c2[it];
       const bool more = it + 1 < sp.iters;
       bool fail = false;
+      // the partition numbers shared triples first: the second round (no
+      // partner) before the first, which may wait for one
 #pragma unroll
-      for (int j = 0; j < kSdRounds; ++j) {
+      for (int j = kSdRounds - 1; j >= 0; --j) {
         const int lt = tid + j * NT;
         if (lt >= nl) continue;
         const unsigned s0 = slot[j] & 0xffffu, s1 = slot[j] >> 16;
@@ -409,7 +411,7 @@ __global__ void __launch_bounds__(NT, 1)
     rr_loc = 0.0;
     bool fail = false;
 #pragma unroll
-    for (int j = 0; j < kSdRounds; ++j) {
+    for (int j = kSdRounds - 1; j >= 0; --j) {  // as in the FP32 phase: the round that may wait last
       const int lt = tid + j * NT;
       if (lt >= nl) continue;
       const unsigned s0 = slot[j] & 0xffffu, s1 = slot[j] >> 16;

@@ -56,11 +56,19 @@ void build_sd_partition(int64_t F, int64_t E, const std::vector<int32_t>& tri, i
         const int64_t t = tri[4 * c + q] & 0x7fffffff;
         if (seen_by[t] != p) {
           seen_by[t] = p;
-          local[t] = nl++;
           order.push_back(t);
         }
-        sp.cell_lt[4 * c + q] = local[t];
       }
+    // triples shared with another part first: the kernel's thread i serves
+    // local triples i and i + NT and handles the second before the first, so
+    // a shared triple's partner contribution has the longest time to arrive
+    auto shared = [&](int64_t t) {
+      return tcell[2 * t + 1] >= 0 && (part_of_cell[tcell[2 * t]] != p || part_of_cell[tcell[2 * t + 1]] != p);
+    };
+    std::stable_partition(order.begin(), order.end(), shared);
+    for (int64_t t : order) local[t] = nl++;
+    for (int32_t c = c0; c < c1; ++c)
+      for (int q = 0; q < 4; ++q) sp.cell_lt[4 * c + q] = local[tri[4 * c + q] & 0x7fffffff];
     if (nl > 0xfffe || c1 - c0 > 0x3fff) throw std::runtime_error("subdomain too large for 16-bit local indices");
     sp.lt0[p + 1] = sp.lt0[p] + nl;
     sp.max_cells = std::max<int32_t>(sp.max_cells, c1 - c0);
