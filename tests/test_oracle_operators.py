@@ -184,3 +184,26 @@ def test_geostrophic_balance_is_steady(om):
     e = [_geostrophic_residual(om(r)) for r in (2, 3, 4)]
     assert e[0] < 0.04 and e[2] < 0.006, e
     assert e[0] / e[1] > 1.8 and e[1] / e[2] > 1.8, e
+
+
+def test_strong_form_of_the_elevation_terms_is_the_same_quantity():
+    """The elevation equation's weak form of Sec. 2.5 (int grad phi . u (eta-b)
+    minus the upwinded facet flux) integrated by parts on each cell is
+    -int phi div(u (eta-b)) + int_dK phi (u.n)((eta-b)_own - (eta-b)~): the
+    same numbers for these polynomial integrands under exact quadrature.
+    The library evaluates the strong form (no cancellation between cell and
+    facet terms, which both grow like 1/h); the oracle's option gives the
+    same values to rounding, and the velocity part is untouched."""
+    from oracle.operators import ELEVATION_STRONG, ELEVATION_WEAK
+    from tests.conftest import oracle_model
+    for r in (2, 3):
+        m = oracle_model(r)
+        U = _state(m)
+        U[m.n_u:] += np.random.default_rng(r).standard_normal(m.n_eta) * 20.0
+        a = m.ops.nonlinear_rhs(U)
+        m.ops.elevation_form = ELEVATION_STRONG
+        b = m.ops.nonlinear_rhs(U)
+        m.ops.elevation_form = ELEVATION_WEAK
+        assert np.array_equal(a[: m.n_u], b[: m.n_u])
+        assert np.abs(a[m.n_u:] - b[m.n_u:]).max() <= 1e-14 * np.abs(a[m.n_u:]).max()
+        assert abs(b[m.n_u:].sum()) <= 1e-15 * np.abs(b[m.n_u:]).sum()   # mass conserved in both forms
