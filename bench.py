@@ -252,22 +252,25 @@ def _surrogate_jobs():
 
 def _batch_leg(pavg, states):
     """64 independent instances (refinements 4-6, T in [0.25, 4] h, M in
-    {16, 32, 64, 128}): one batched evaluation (persistent recurrences,
-    autotuned grid) against the same instances one after another."""
+    {16, 32, 64, 128}): one batched evaluation against the same instances one
+    after another.  The batch's contexts ask for subdomain parts of at least
+    512 cells (a refinement-4 solve on 10 SMs, refinement 5 on 40,
+    refinement 6 on all 152), and the batch's first call picks the faster of
+    its two strategies (persistent chain launches, or one graph branch per
+    instance running side by side).  The one-after-another baseline uses
+    default contexts (every solve spread over all SMs)."""
     import torch
     from paper_2103_07706_gb300.inputs import lambda_max_for
     work = _batch_work()
-    ms = [pavg.Model(w["refinement"], lambda_max=lambda_max_for(w["refinement"])) for w in work]
     U = [torch.from_numpy(x).cuda() for x in states]
     T = [w["T"] for w in work]
     M = [w["M"] for w in work]
+    ms = [pavg.Model(w["refinement"], lambda_max=lambda_max_for(w["refinement"]), sd_part_cells=512) for w in work]
     b = pavg.Batch(ms)
     t0 = time.time()
-    out = b.averaged_rhs(T, M, U)  # autotune + capture
+    out = b.averaged_rhs(T, M, U)  # autotune, strategy choice, capture
     b.sync()
     first_s = time.time() - t0
-    for m in ms:
-        m.reset_stats()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record()
@@ -275,40 +278,35 @@ def _batch_leg(pavg, states):
     e1.record()
     torch.cuda.synchronize()
     t_batch = e0.elapsed_time(e1)
-    fwd, bwd = b.kernel_time()
     b.sync()
-    f32 = f64 = 0.0
+    cfg = b.config()
+    b.close()
     for m in ms:
-        st = m.stats()
-        a, c = _cg_flops(m.n_cells, m.n_u, st["cg_iters_mean"], st["cg_sweeps_mean"])
-        f32 += st["cg_solves"] * a
-        f64 += st["cg_solves"] * c
+        m.close()
+    del ms
+    seq_models = [pavg.Model(w["refinement"], lambda_max=lambda_max_for(w["refinement"])) for w in work]
     seq = [torch.empty_like(u) for u in U]
-    for i, m in enumerate(ms):  # capture each instance's graph
+    for i, m in enumerate(seq_models):  # capture each instance's graph
         m.averaged_rhs(T[i], M[i], U[i], seq[i])
     torch.cuda.synchronize()
     e0.record()
-    for i, m in enumerate(ms):
+    for i, m in enumerate(seq_models):
         m.averaged_rhs(T[i], M[i], U[i], seq[i])
     e1.record()
     torch.cuda.synchronize()
     t_seq = e0.elapsed_time(e1)
-    diff = max(float(((o - q).norm() / q.norm()).item()) for o, q in zip(out, seq))
-    chain_s = (fwd + bwd) / 1e3
-    res = {"workload": f"{len(ms)} instances, refinements 4-{BATCH['max_refinement']}, T ~ U[0.25, 4] h, "
-                       "M in {16, 32, 64, 128}, harmonic l<=16",
-           "value": len(ms) / (t_batch / 1e3), "unit": "instance-evals/s", "ms_per_batch": t_batch,
-           "sequential_ms": t_seq, "speedup_vs_sequential": t_seq / t_batch,
-           "max_rel_l2_vs_single_instance": diff, "first_call_s": first_s, "config": b.config(),
-           "forward_chain_ms": fwd, "clenshaw_ms": bwd,
-           "roofline": {"bound": "alu", "kernel": "k_chain (persistent recurrences, all instances)",
-                        "achieved": f32 / chain_s / 1e12, "peak": ALU_PEAKS.get("fp32", FP32_PEAK_TFLOPS),
-                        "unit": "TFLOP/s", "frac": f32 / chain_s / 1e12 / ALU_PEAKS.get("fp32", FP32_PEAK_TFLOPS), "fp64_achieved": f64 / chain_s / 1e12,
-                        "note": "FP32 CG flops of every solve in both launches over their summed duration"},
-           "K_max": max(m.stats()["last_degree"] for m in ms)}
-    b.close()
-    for m in ms:
+    K_max = max(m.stats()["last_degree"] for m in seq_models)
+    for m in seq_models:
+        m.sync()
         m.close()
+    diff = max(float(((o - q).norm() / q.norm()).item()) for o, q in zip(out, seq))
+    res = {"workload": f"{len(work)} instances, refinements 4-{BATCH['max_refinement']}, T ~ U[0.25, 4] h, "
+                       "M in {16, 32, 64, 128}, harmonic l<=16",
+           "value": len(work) / (t_batch / 1e3), "unit": "instance-evals/s", "ms_per_batch": t_batch,
+           "sequential_ms": t_seq, "speedup_vs_sequential": t_seq / t_batch,
+           "max_rel_l2_vs_single_instance": diff, "first_call_s": first_s, "config": cfg,
+           "strategy": ["persistent chain launches (k_chain)", "one graph branch per instance"][cfg["strategy"]],
+           "K_max": K_max}
     return res
 
 

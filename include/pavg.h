@@ -96,6 +96,10 @@ typedef struct {
                              subdomain solver runs a fixed number of Chebyshev iterations per
                              sweep (at most 8 sweeps) */
   int precision;          /* PAVG_PRECISION_FP64 (default) or PAVG_PRECISION_MIXED */
+  int sd_part_cells;      /* subdomain solver: 0 (default) splits the mesh over every SM (parts of
+                             F / SMs cells, at least 32); > 0 asks for parts of at least this many
+                             cells, so a small mesh's solve occupies fewer SMs and solves of other
+                             contexts can run beside it (batches, concurrent streams) */
 } pavg_params;
 
 /* Fill `p` with the defaults: r = 3, R = 6.37122e6, Omega = 7.292e-5,
@@ -315,7 +319,10 @@ typedef struct {
   int blocks_per_sm;  /* co-resident blocks of the persistent launch per SM */
   int resident;       /* 1: FP32 element matrices in shared memory; 0: streamed from L2 */
   int weighting;      /* blocks per instance proportional to 0: cells x chain steps, 1: cells */
-  double predicted_ms;/* autotuner's predicted forward-chain launch time (0 when set by hand) */
+  double predicted_ms;/* autotuner's measured time of one evaluation of the batch (0 when set by hand) */
+  int strategy;       /* 0: every instance's chains in persistent launches (the fields above);
+                         1: one graph branch per instance, each evaluated with its own context's
+                         solver, the branches running concurrently where the GPU has room */
 } pavg_batch_config;
 
 /* ctxs: host array of n distinct contexts on the current device, n >= 1.

@@ -286,7 +286,7 @@ int enq_avg(pavg_ctx* ctx, const AvgPlan& pl, const double* U, double* out, cuda
     return PAVG_OK;
   }
   double* Q = ctx->Q;
-  CK(cudaMemcpyAsync(Q, U, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  if (U != Q) CK(cudaMemcpyAsync(Q, U, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   for (int k = 0; k < K; ++k) {
     int rc = enq_step(ctx, Q + (int64_t)k * n, (k == 0 ? 1.0 : 2.0) / ctx->lam, nullptr,
                       k == 0 ? nullptr : Q + (int64_t)(k - 1) * n, Q + (int64_t)(k + 1) * n, st);
@@ -443,13 +443,30 @@ int build_shared_mesh(const pavg_params* p, SharedMesh* sh, std::string* why) {
     *why = "device upload failed";
     return PAVG_ERR_NOMEM;
   }
-  // the subdomain solver's partition and Chebyshev interval (P = 0 when its
-  // parts do not fit in shared memory: contexts then use the global solver)
-  if (sd_configure(m.F, m.E, hc.tri, hc.M1, hc.Pinv, &sh->sd) != cudaSuccess) {
-    free_device_mesh(m);
-    *why = "subdomain solver set-up failed";
-    return PAVG_ERR_CUDA;
+  // the subdomain solver's Chebyshev interval (the partitions are built per
+  // part count when a context asks for one)
+  try {
+    sd_spectrum(m.F, m.E, hc.M1, hc.tri, hc.Pinv, 40, &sh->sd_lmin, &sh->sd_lmax);
+  } catch (const std::exception&) {
+    sh->sd_lmin = sh->sd_lmax = 0.0;
   }
+  sh->tri = hc.tri;
+  return PAVG_OK;
+}
+
+// The subdomain partition of a shared mesh into P parts (built on first use;
+// P = 0 in the result when it does not fit).  Called under g_mesh_mu.
+int sd_partition_for(SharedMesh* sh, int P, SdMesh* out, std::string* why) {
+  auto it = sh->sds.find(P);
+  if (it == sh->sds.end()) {
+    SdMesh sd;
+    if (sd_configure(sh->dm.F, sh->dm.E, sh->tri, sh->sd_lmin, sh->sd_lmax, P, &sd) != cudaSuccess) {
+      *why = "subdomain solver set-up failed";
+      return PAVG_ERR_CUDA;
+    }
+    it = sh->sds.emplace(P, sd).first;
+  }
+  *out = it->second;
   return PAVG_OK;
 }
 
@@ -478,7 +495,7 @@ void release_mesh(SharedMesh* sh) {
   if (--sh->refs > 0) return;
   g_meshes.erase(sh->key);
   free_device_mesh(sh->dm);
-  sd_free(&sh->sd);
+  for (auto& kv : sh->sds) sd_free(&kv.second);
   delete sh;
 }
 
@@ -521,7 +538,7 @@ bool valid_params(const pavg_params* p) {
          (p->quad_rule == PAVG_QUAD_MIDPOINT || p->quad_rule == PAVG_QUAD_CLOSED) &&
          (p->upwind_convention == PAVG_UPWIND_STANDARD || p->upwind_convention == PAVG_UPWIND_AS_PRINTED) &&
          (p->solver == PAVG_SOLVER_MIXED || p->solver == PAVG_SOLVER_FP64 || p->solver == PAVG_SOLVER_SUBDOMAIN) &&
-         (p->precision == PAVG_PRECISION_FP64 || p->precision == PAVG_PRECISION_MIXED);
+         (p->precision == PAVG_PRECISION_FP64 || p->precision == PAVG_PRECISION_MIXED) && p->sd_part_cells >= 0;
 }
 
 }  // namespace pavg_api
@@ -545,6 +562,7 @@ int pavg_default_params(pavg_params* p) {
   p->upwind_convention = PAVG_UPWIND_STANDARD;
   p->solver = PAVG_SOLVER_SUBDOMAIN;
   p->precision = PAVG_PRECISION_FP64;
+  p->sd_part_cells = 0;
   return PAVG_OK;
 }
 
@@ -573,7 +591,15 @@ int pavg_create(const pavg_params* p, pavg_ctx** out) {
     ctx->shared = sh;
     ctx->mesh = sh->mesh;
     ctx->dm = sh->dm;
-    ctx->sd = sh->sd;
+    if (p->solver == PAVG_SOLVER_SUBDOMAIN) {
+      int sms = 0;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+      const int64_t F = sh->dm.F;
+      const int64_t want = p->sd_part_cells > 0 ? (F + p->sd_part_cells - 1) / p->sd_part_cells : F / 32;
+      const int P = (int)std::max<int64_t>(1, std::min<int64_t>(sms, want));
+      std::lock_guard<std::mutex> lock(g_mesh_mu);
+      if ((rc = sd_partition_for(sh, P, &ctx->sd, &why))) { set_err(ctx, rc, why); throw 0; }
+    }
     DeviceMesh& m = ctx->dm;
     bool ok = dalloc(&m.topo, m.n_eta) == cudaSuccess;
     if (!ok) { rc = set_err(ctx, PAVG_ERR_NOMEM, "device upload failed"); throw 0; }

@@ -57,6 +57,8 @@ int get_plan(pavg_ctx* ctx, double T, int M, AvgPlan** out, int m0 = 0, int m1 =
 // Middle of the shared-basis average: U_m = sum_k A[m][k] Q_k, r_m = N(U_m)
 // (weak form), y_k = sum_m B[k][m] r_m written over Q_k.
 int enq_avg_shifts(pavg_ctx* ctx, const AvgPlan& pl, cudaStream_t st);
+// The whole shared-basis average on `st` (no graph): U -> out.
+int enq_avg(pavg_ctx* ctx, const AvgPlan& pl, const double* U, double* out, cudaStream_t st);
 // Energy inner product <U, V>_W = H u^T M1 v + g eta^T M2 zeta (synchronous, legacy stream).
 double host_winner(pavg_ctx* ctx, const double* U, const double* V);
 // The shared-basis average through the context's cached graph.

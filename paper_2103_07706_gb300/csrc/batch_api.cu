@@ -29,10 +29,11 @@ constexpr int kTuneSteps = 4;  // chain steps per autotuning candidate
 struct Config {
   int nt = 256, bps = 3, res = 0, weighting = 0;
   double predicted_ms = 0.0;
+  int strategy = 0;  // 0 persistent chain launches, 1 one graph branch per instance
 };
 
 bool same(const Config& a, const Config& c) {
-  return a.nt == c.nt && a.bps == c.bps && a.res == c.res && a.weighting == c.weighting;
+  return a.nt == c.nt && a.bps == c.bps && a.res == c.res && a.weighting == c.weighting && a.strategy == c.strategy;
 }
 
 // One launch of k_chain: its problems (uploaded) and its grid.
@@ -80,6 +81,7 @@ struct pavg_batch {
   };
   std::map<std::vector<double>, ExpPlan> exps;
   std::vector<std::vector<double*>> stage;  // per instance: k1, k2, k3, k4, EhU, tmp, tmp2
+  std::vector<cudaEvent_t> branch_ev;       // [n + 1]: fork, then one join per instance (strategy 1)
   std::string err;
 };
 
@@ -353,6 +355,90 @@ int capture(pavg_batch* b, BatchPlan* bp) {
   return PAVG_OK;
 }
 
+// Strategy 1: one branch per instance in the captured graph (forked from and
+// joined to the batch's stream through events), each instance's evaluation
+// enqueued on its own context's stream with its own solver, inputs in its Q,
+// result in its io_out.  The graph's branches are independent, so the GPU
+// runs them side by side where their launches fit.
+int capture_branches(pavg_batch* b, BatchPlan* bp) {
+  drop_exec(bp);
+  const int n = (int)b->ctx.size();
+  if ((int)b->branch_ev.size() < n + 1) {
+    for (int k = (int)b->branch_ev.size(); k < n + 1; ++k) {
+      cudaEvent_t e = nullptr;
+      BCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      b->branch_ev.push_back(e);
+    }
+  }
+  cudaStream_t cs = b->cap_stream;
+  std::vector<bool> timing;
+  for (auto* c : b->ctx) { timing.push_back(c->timing); c->timing = false; }
+  struct Restore {
+    pavg_batch* b;
+    std::vector<bool>& t;
+    ~Restore() { for (size_t i = 0; i < b->ctx.size(); ++i) b->ctx[i]->timing = t[i]; }
+  } restore{b, timing};
+  BCK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  int launches = 0;
+  auto body = [&]() -> int {
+    int r = record(b, 0, cs);
+    if (r) return r;
+    BCK(cudaEventRecord(b->branch_ev[0], cs));
+    for (int i = 0; i < n; ++i) {
+      pavg_ctx* c = b->ctx[i];
+      cudaStream_t si = c->cap_stream;
+      BCK(cudaStreamWaitEvent(si, b->branch_ev[0], 0));
+      c->launches = 0;
+      r = bp->K[i] < 0 ? enq_nonlinear(c, c->Q, c->io_out, c->Rm, si) : enq_avg(c, *bp->pl[i], c->Q, c->io_out, si);
+      launches += c->launches;
+      if (r) return bset_err(b, r, "instance " + std::to_string(i) + ": " + c->err);
+      BCK(cudaEventRecord(b->branch_ev[i + 1], si));
+      BCK(cudaStreamWaitEvent(cs, b->branch_ev[i + 1], 0));
+    }
+    // the whole evaluation counts as the "forward" interval of pavg_batch_kernel_time
+    if ((r = record(b, 1, cs))) return r;
+    if ((r = record(b, 2, cs))) return r;
+    return record(b, 3, cs);
+  };
+  int rc = body();
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &graph);
+  if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+  if (e != cudaSuccess) return bset_err(b, PAVG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&bp->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    bp->exec = nullptr;
+    return bset_err(b, PAVG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  bp->cfg = b->cfg;
+  bp->launches = launches;
+  bp->ws = workspaces(b);
+  return PAVG_OK;
+}
+
+int capture_for(pavg_batch* b, BatchPlan* bp) {
+  return b->cfg.strategy == 1 ? capture_branches(b, bp) : capture(b, bp);
+}
+
+// Time of one replay of the plan's graph (inputs already loaded), ms.
+int time_replay(pavg_batch* b, BatchPlan* bp, cudaStream_t st, double* ms) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  BCK(cudaEventCreate(&e0));
+  BCK(cudaEventCreate(&e1));
+  cudaEventRecord(e0, st);
+  cudaError_t e = cudaGraphLaunch(bp->exec, st);
+  cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float f = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&f, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return bset_err(b, PAVG_ERR_CUDA, std::string("timing a batch graph: ") + cudaGetErrorString(e));
+  *ms = f;
+  return PAVG_OK;
+}
+
 int load_inputs(pavg_batch* b, const double* const* U, cudaStream_t st) {
   for (size_t i = 0; i < b->ctx.size(); ++i) {
     pavg_ctx* c = b->ctx[i];
@@ -431,6 +517,28 @@ int autotune(pavg_batch* b, BatchPlan* bp, cudaStream_t st, Config* best) {
   return PAVG_OK;
 }
 
+// Chooses between the persistent chain launches (grid `c` from autotune) and
+// one graph branch per instance by timing one replay of each on the loaded
+// inputs; c gets the faster strategy and its measured time.  Each replay
+// overwrites the instances' workspaces, so the inputs are loaded again.
+int choose_strategy(pavg_batch* b, BatchPlan* bp, const double* const* U, cudaStream_t st, Config* c) {
+  double t[2] = {0.0, 0.0};
+  for (int k = 0; k < 2; ++k) {
+    Config ck = *c;
+    ck.strategy = k;
+    b->cfg = ck;
+    int rc = load_inputs(b, U, st);
+    if (!rc) rc = capture_for(b, bp);
+    if (!rc) rc = time_replay(b, bp, st, &t[k]);
+    if (rc) return rc;
+  }
+  c->strategy = t[1] < t[0] ? 1 : 0;
+  c->predicted_ms = t[c->strategy];
+  b->cfg = *c;
+  drop_exec(bp);
+  return load_inputs(b, U, st);
+}
+
 void free_batch(pavg_batch* b) {
   if (!b) return;
   for (auto& kv : b->exps) {
@@ -449,6 +557,7 @@ void free_batch(pavg_batch* b) {
   for (auto* p : b->scal) cudaFree(p);
   cudaFree(b->sync);
   cudaFree(b->timer);
+  for (auto e : b->branch_ev) cudaEventDestroy(e);
   for (auto e : b->ev)
     if (e) cudaEventDestroy(e);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
@@ -573,22 +682,24 @@ int pavg_batch_autotune(pavg_batch* b, const double* T, const int* M, const doub
   if (!rc) rc = load_inputs(b, U, st);
   Config c;
   if (!rc) rc = autotune(b, bp, st, &c);
+  if (!rc) rc = choose_strategy(b, bp, U, st, &c);
   if (rc) return rc;
-  if (!b->have_cfg || !same(c, b->cfg))
-    for (auto& kv : b->plans) drop_exec(&kv.second);
+  for (auto& kv : b->plans) drop_exec(&kv.second);
   b->cfg = c;
   b->have_cfg = true;
-  if (best) *best = {c.nt, c.bps, c.res, c.weighting, c.predicted_ms};
+  if (best) *best = {c.nt, c.bps, c.res, c.weighting, c.predicted_ms, c.strategy};
   return PAVG_OK;
 }
 
 int pavg_batch_set_config(pavg_batch* b, const pavg_batch_config* cfg) {
   if (!b || !cfg) return PAVG_ERR_INVAL;
   if ((cfg->threads != 128 && cfg->threads != 256) || cfg->blocks_per_sm < 1 || cfg->blocks_per_sm > 8 ||
-      (cfg->resident != 0 && cfg->resident != 1) || (cfg->weighting != 0 && cfg->weighting != 1))
+      (cfg->resident != 0 && cfg->resident != 1) || (cfg->weighting != 0 && cfg->weighting != 1) ||
+      (cfg->strategy != 0 && cfg->strategy != 1))
     return bset_err(b, PAVG_ERR_INVAL, "invalid configuration");
   Config c;
   c.nt = cfg->threads; c.bps = cfg->blocks_per_sm; c.res = cfg->resident; c.weighting = cfg->weighting;
+  c.strategy = cfg->strategy;
   if (!b->have_cfg || !same(c, b->cfg))
     for (auto& kv : b->plans) drop_exec(&kv.second);
   b->cfg = c;
@@ -599,7 +710,7 @@ int pavg_batch_set_config(pavg_batch* b, const pavg_batch_config* cfg) {
 int pavg_batch_get_config(const pavg_batch* b, pavg_batch_config* cfg) {
   if (!b || !cfg) return PAVG_ERR_INVAL;
   if (!b->have_cfg) return PAVG_ERR_INVAL;
-  *cfg = {b->cfg.nt, b->cfg.bps, b->cfg.res, b->cfg.weighting, b->cfg.predicted_ms};
+  *cfg = {b->cfg.nt, b->cfg.bps, b->cfg.res, b->cfg.weighting, b->cfg.predicted_ms, b->cfg.strategy};
   return PAVG_OK;
 }
 
@@ -620,11 +731,12 @@ int pavg_batch_averaged_rhs(pavg_batch* b, const double* T, const int* M, const 
   if (!b->have_cfg) {
     Config c;
     if ((rc = autotune(b, bp, st, &c))) return rc;
+    if ((rc = choose_strategy(b, bp, U, st, &c))) return rc;
     b->cfg = c;
     b->have_cfg = true;
   }
   if (!bp->exec || !same(bp->cfg, b->cfg))
-    if ((rc = capture(b, bp))) return rc;
+    if ((rc = capture_for(b, bp))) return rc;
   BCK(cudaGraphLaunch(bp->exec, st));
   b->ev_recorded = true;
   for (size_t i = 0; i < b->ctx.size(); ++i) {

@@ -483,15 +483,15 @@ static cudaError_t upload_vec(T** dst, const std::vector<T>& v) {
   return v.empty() ? cudaSuccess : cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
 }
 
-cudaError_t sd_configure(int64_t F, int64_t E, const std::vector<int32_t>& tri, const std::vector<double>& M1,
-                         const std::vector<float>& Pinv, SdMesh* sd) {
+cudaError_t sd_configure(int64_t F, int64_t E, const std::vector<int32_t>& tri, double lmin, double lmax, int P,
+                         SdMesh* sd) {
   *sd = SdMesh();
   int dev = 0, sms = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  const int P = (int)std::max<int64_t>(1, std::min<int64_t>(sms, F / 32));
+  if (P < 1 || P > sms || P > F || !(lmin > 0.0) || !(lmax > lmin)) return cudaSuccess;
   SdPartition part;
   try {
     build_sd_partition(F, E, tri, P, &part);
@@ -513,13 +513,6 @@ cudaError_t sd_configure(int64_t F, int64_t E, const std::vector<int32_t>& tri, 
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb_sd<kSdThreads>, kSdThreads, smem);
   if (e != cudaSuccess) return e;
   if ((int64_t)per_sm * sms < P) return cudaSuccess;
-  double lmin = 0, lmax = 0;
-  try {
-    sd_spectrum(F, E, M1, tri, Pinv, 40, &lmin, &lmax);
-  } catch (const std::exception&) {
-    return cudaSuccess;
-  }
-  if (!(lmin > 0.0) || !(lmax > lmin)) return cudaSuccess;
   std::vector<ushort4> cl(F);
   std::vector<int4> cs(F);
   for (int64_t c = 0; c < F; ++c) {

@@ -40,7 +40,11 @@ struct SharedMesh {
   pavg_detail::SharedMesh* shared = nullptr;
   pavg::Mesh mesh;
   pavg::DeviceMesh dm;  // topo stays per context
-  pavg::SdMesh sd;      // partition of the subdomain solver (P = 0: not available)
+  // subdomain solver: the spectrum estimate (per mesh) and the partitions
+  // built so far, by number of parts (P = 0 in a descriptor: not available)
+  double sd_lmin = 0, sd_lmax = 0;
+  std::vector<int32_t> tri;            // [F][4] DOF triples (host copy, for later partitions)
+  std::map<int, pavg::SdMesh> sds;
 };
 
 }  // namespace pavg_detail

@@ -137,10 +137,11 @@ struct SdParams {
   int stall_part;       //            2: block stall_part never publishes its shared contributions
 };
 
-// Builds the partition for F cells on the current device (P = min(SMs, F/32)
-// parts) when its blocks fit in shared memory; sd->P = 0 otherwise.
-cudaError_t sd_configure(int64_t F, int64_t E, const std::vector<int32_t>& tri, const std::vector<double>& M1,
-                         const std::vector<float>& Pinv, SdMesh* sd);
+// Builds the partition of F cells into P parts on the current device when its
+// blocks fit in shared memory and are co-resident; sd->P = 0 otherwise.
+// [lmin, lmax]: the spectrum estimate of the preconditioned M1 (sd_spectrum).
+cudaError_t sd_configure(int64_t F, int64_t E, const std::vector<int32_t>& tri, double lmin, double lmax, int P,
+                         SdMesh* sd);
 void sd_free(SdMesh* sd);
 cudaError_t sd_alloc_work(const SdMesh& sd, int64_t F, SdWork* w);
 void sd_free_work(SdWork* w);

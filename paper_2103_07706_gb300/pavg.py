@@ -62,6 +62,7 @@ class Params(ctypes.Structure):
         ("upwind_convention", ctypes.c_int),
         ("solver", ctypes.c_int),
         ("precision", ctypes.c_int),
+        ("sd_part_cells", ctypes.c_int),
     ]
 
 
@@ -86,6 +87,7 @@ class BatchConfig(ctypes.Structure):
         ("resident", ctypes.c_int),
         ("weighting", ctypes.c_int),
         ("predicted_ms", ctypes.c_double),
+        ("strategy", ctypes.c_int),
     ]
 
 
@@ -415,8 +417,8 @@ class Batch:
         self._check(self._lib.pavg_batch_autotune(self._h, Ta, Ma, Ua, _stream(), ctypes.byref(c)))
         return {k: getattr(c, k) for k, _ in BatchConfig._fields_}
 
-    def set_config(self, threads, blocks_per_sm, resident=0, weighting=0):
-        c = BatchConfig(threads, blocks_per_sm, resident, weighting, 0.0)
+    def set_config(self, threads, blocks_per_sm, resident=0, weighting=0, strategy=0):
+        c = BatchConfig(threads, blocks_per_sm, resident, weighting, 0.0, strategy)
         self._check(self._lib.pavg_batch_set_config(self._h, ctypes.byref(c)))
 
     def config(self):

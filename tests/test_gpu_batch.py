@@ -64,7 +64,8 @@ def test_batch_matches_single_instance_and_is_reproducible(batch_case):
         single = ms[i].averaged_rhs(t, m, U[i]).cpu().numpy()
         assert_close(orc(r), a[i], single)
     fwd, bwd = b.kernel_time()
-    assert fwd > 0.0 and bwd > 0.0
+    # one graph branch per instance times the whole evaluation as "forward"
+    assert fwd > 0.0 and (bwd > 0.0 if b.config()["strategy"] == 0 else bwd >= 0.0)
 
 
 @pytest.mark.parametrize("threads,bps,res,wt", [(128, 1, 0, 0), (256, 2, 1, 1), (128, 4, 1, 0), (256, 3, 0, 1)])
@@ -79,9 +80,49 @@ def test_batch_configurations_agree(batch_case, threads, bps, res, wt):
         got = [x.cpu().numpy() for x in b.averaged_rhs(T, M, U)]
         b.sync()
     finally:
-        b.set_config(keep["threads"], keep["blocks_per_sm"], keep["resident"], keep["weighting"])
+        b.set_config(keep["threads"], keep["blocks_per_sm"], keep["resident"], keep["weighting"], keep["strategy"])
     for i, (r, _, _) in enumerate(SPEC):
         assert_close(orc(r), got[i], ref[i])
+
+
+@pytest.mark.parametrize("part_cells", [0, 512])
+def test_batch_strategies_agree(part_cells):
+    """Persistent chain launches (strategy 0) and one graph branch per
+    instance running its own solver (strategy 1), with the subdomain solver
+    on all SMs or on parts of at least 512 cells: both match the
+    single-instance path and the oracle; strategy 1 is bit-identical to the
+    same contexts evaluated one at a time."""
+    from paper_2103_07706_gb300 import pavg
+    ms = _models(SPEC, sd_part_cells=part_cells)
+    U = _states(SPEC)
+    T = [t for _, t, _ in SPEC]
+    M = [m for _, _, m in SPEC]
+    b = pavg.Batch(ms)
+    try:
+        b.averaged_rhs(T, M, U)  # autotune and strategy choice
+        keep = b.config()
+        assert keep["strategy"] in (0, 1) and keep["predicted_ms"] > 0.0
+        got = {}
+        for k in (0, 1):
+            b.set_config(keep["threads"], keep["blocks_per_sm"], keep["resident"], keep["weighting"], k)
+            assert b.config()["strategy"] == k
+            got[k] = [x.cpu().numpy() for x in b.averaged_rhs(T, M, U)]
+            b.sync()
+        with pytest.raises(pavg.PavgError):
+            b.set_config(keep["threads"], keep["blocks_per_sm"], keep["resident"], keep["weighting"], 2)
+        single = [m.averaged_rhs(t, mm, u).cpu().numpy() for m, t, mm, u in zip(ms, T, M, U)]
+        for m in ms:
+            m.sync()
+        for i, (r, t, m) in enumerate(SPEC):
+            assert np.array_equal(got[1][i], single[i])
+            assert_close(orc(r), got[0][i], got[1][i])
+            if i < 3:
+                o = orc(r)
+                assert_close(o, got[1][i], o.averaged_rhs(t, m, U[i].cpu().numpy()))
+    finally:
+        b.close()
+        for m in ms:
+            m.close()
 
 
 def test_batch_survives_workspace_growth(batch_case):
