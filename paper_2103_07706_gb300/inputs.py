@@ -176,13 +176,16 @@ def tc5_state(verts, cells, u0=20.0, H=5960.0, g=9.8, omega=7.292e-5, b0=2000.0,
 
     Returns (U, b): U = [u, eta] with eta = h - H the elevation of the free
     surface (the depth is H + eta - b), and b at the DG1 nodes (cell vertices).
-    u = k x grad psi with psi = -u0 z (divergence free); eta and b are nodal
-    values at the cell vertices."""
+    u = k x grad psi with psi = -u0 R z / |x| (divergence free; psi is
+    evaluated at the radial projection of each sample point onto the sphere,
+    so that its variation along an edge chord is the sphere's); eta and b are
+    nodal values at the cell vertices."""
     verts = np.asarray(verts, dtype=np.float64)
     cells = np.asarray(cells, dtype=np.int64)
     edges = canonical_edges(cells)
     R = float(np.linalg.norm(verts[0]))
-    u = velocity_dofs_from_streamfunction(verts, cells, edges, lambda x: -u0 * x[..., 2])
+    u = velocity_dofs_from_streamfunction(verts, cells, edges,
+                                          lambda x: -u0 * R * x[..., 2] / np.linalg.norm(x, axis=-1))
     z = verts[:, 2]
     eta_v = -(R * omega * u0 + 0.5 * u0 * u0) * z * z / (g * R * R)
     lat = np.arcsin(np.clip(z / R, -1.0, 1.0))

@@ -56,8 +56,9 @@ def test_batch_workload_recipe():
 
 def test_tc5_state():
     """Williamson's test case 5 (Sec. 3): the velocity DOFs are those of the
-    zonal flow (u0/R)(-y, x, 0) (close to its L2 projection, exactly
-    divergence free), the elevation is -(R Omega u0 + u0^2/2) z^2/(g R^2) at
+    zonal flow (u0/R)(-y, x, 0) (second-order close to its L2 projection:
+    0.60 % at refinement 3, 0.15 % at 4; exactly divergence free), the
+    elevation is -(R Omega u0 + u0^2/2) z^2/(g R^2) at
     the vertices, and the mountain peaks at b0 at its centre and vanishes
     beyond R0."""
     import math
@@ -67,13 +68,13 @@ def test_tc5_state():
     from tests.test_oracle_operators import proj_u
     R, u0, om, g = 6.37122e6, 20.0, 7.292e-5, 9.8
     errs = []
-    for r in (3, 4):  # first order: flat cells' k x grad psi vs the projected 3-D field
+    for r in (3, 4):  # k x grad psi with psi sampled on the sphere vs the projected 3-D field
         m = oracle_model(r)
         U, b = tc5_state(m.mesh.verts, m.mesh.cells)
         u = U[: m.n_u]
         want = proj_u(m.ops, lambda x: (u0 / R) * np.stack([-x[..., 1], x[..., 0], 0 * x[..., 0]], -1))
         errs.append(np.sqrt((u - want) @ (m.ops.M1 @ (u - want)) / (want @ (m.ops.M1 @ want))))
-    assert errs[0] < 0.04 and errs[0] / errs[1] > 1.8, errs
+    assert errs[0] < 0.007 and errs[0] / errs[1] > 3.5, errs
     assert np.abs(m.ops.D @ u).max() <= 1e-12 * np.abs(m.ops.D).max() * np.abs(u).max()
     z = m.mesh.verts[m.mesh.cells.reshape(-1), 2]
     assert np.allclose(U[m.n_u:], -(R * om * u0 + 0.5 * u0 * u0) * z * z / (g * R * R), rtol=0, atol=1e-9)
