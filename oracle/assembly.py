@@ -1,17 +1,22 @@
 """Cell geometry, element matrices and global sparse matrices (paper Sec. 2.5).
 
-Geometry: flat triangles through the mesh vertices (piecewise-linear
-approximation of the sphere; the paper uses a piecewise-cubic one).  On a flat
-cell every integrand of L and N is a polynomial in the reference
-coordinates, so a rule of high enough degree integrates it exactly.  For
-cell (v0, v1, v2) with a = x_v0:
-  J = [x_v1 - a, x_v2 - a] (3 x 2),  det = |J0 x J1|,  G = J^T J,
-  k = (J0 x J1) / det (outward unit normal; cells are counter-clockwise),
-  x(xi) = a + J xi.
+Geometry (oracle/geometry.py): degree 1, flat triangles through the mesh
+vertices, or degree 3, the piecewise cubic surface of Sec. 3.  At every
+quadrature point of a cell, with J = dx/dxi (3 x 2), det = |J0 x J1|,
+G = J^T J and k = (J0 x J1) / det (outward unit normal; cells are
+counter-clockwise):
 Contravariant Piola map: u = J u_hat / det, div u = div_hat u_hat / det.
-Useful identities on a flat cell (all used below):
+Pointwise identities (hold on curved cells too, J and det taken at the point):
   (k x J a) . (J b) = det * cross2(a, b)
   grad_perp q := k x grad q = J curl_hat(q) / det,  curl_hat q = (-dq/dy, dq/dx)
+so that, with dA = det dA_hat,
+  M1_ij = int_ref psi_i . G psi_j / det,   M2_ij = int_ref phi_i phi_j det,
+  C_ij  = int_ref f cross2(psi_j, psi_i),  D_ij  = int_ref phi_i div_hat psi_j
+(D does not depend on the geometry).  On flat cells every integrand is a
+polynomial and the 4 x 4 cell rule integrates it exactly; on cubic cells the
+integrands are rational and the 5 x 5 rule is part of the discretisation.
+The attributes a, J, det, G, k are the flat (vertex) triangle's, for both
+degrees (cell-size features; the degree-1 geometry).
 
 Global numbering (the reading of this build):
   velocity: edge e, moment j -> 3 e + j;  interior DOF j of cell c -> 3 E + 3 c + j
@@ -26,7 +31,8 @@ import numpy as np
 import scipy.sparse as sp
 
 from .elements import BDM2, DG1_GRADS, dg1_values
-from .quadrature import triangle_rule
+from .geometry import CellMaps
+from .quadrature import cell_rule_points, triangle_rule
 
 
 def cross2(a, b):
@@ -34,8 +40,11 @@ def cross2(a, b):
 
 
 class Assembly:
-    def __init__(self, mesh, omega, radius):
+    def __init__(self, mesh, omega, radius, geometry_degree=1):
         self.mesh = mesh
+        self.degree = geometry_degree
+        self.maps = CellMaps(mesh, geometry_degree)
+        self.cell_n = cell_rule_points(geometry_degree)
         self.element = BDM2()
         F, E = mesh.n_cells, mesh.n_edges
         self.n_u = 3 * E + 3 * F
@@ -67,23 +76,24 @@ class Assembly:
         self._element_matrices()
 
     def coriolis(self, xi):
-        """f = 2 Omega z / R at reference points xi (Q, 2) of every cell -> (F, Q)."""
-        z = self.a[:, 2][:, None] + self.J[:, 2, 0][:, None] * xi[None, :, 0] \
-            + self.J[:, 2, 1][:, None] * xi[None, :, 1]
-        return 2.0 * self.omega * z / self.radius
+        """f = 2 Omega z / R at reference points xi (Q, 2) of every cell -> (F, Q),
+        z the third coordinate of the cell map's point."""
+        return 2.0 * self.omega * self.maps.points(xi)[..., 2] / self.radius
 
     def _element_matrices(self):
-        xq, wq = triangle_rule(4)
+        xq, wq = triangle_rule(self.cell_n)
         psi = self.element.values(xq)                       # (Q, 12, 2)
         div = self.element.divs(xq)                         # (Q, 12)
         phi = dg1_values(xq)                                # (Q, 3)
         f = self.coriolis(xq)                               # (F, Q)
-        m1 = np.einsum("q,qia,fab,qjb->fij", wq, psi, self.G, psi) / self.det[:, None, None]
+        geo = self.maps.geometry(xq)
+        Gd = geo["G"] / geo["det"][..., None, None]         # (F, Q, 2, 2)
+        m1 = np.einsum("q,qia,fqab,qjb->fij", wq, psi, Gd, psi)
         # C_ij = int w_i . f (k x w_j) dx = int_ref f cross2(psi_j, psi_i)
         cr = psi[:, None, :, 0] * psi[:, :, None, 1] - psi[:, None, :, 1] * psi[:, :, None, 0]  # (Q, i, j) = cross2(psi_j, psi_i)
         c = np.einsum("q,fq,qij->fij", wq, f, cr)
         d = np.einsum("q,qi,qj->ij", wq, phi, div)          # (3, 12) reference
-        m2 = np.einsum("q,qi,qj->ij", wq, phi, phi)[None] * self.det[:, None, None]
+        m2 = np.einsum("q,fq,qi,qj->fij", wq, geo["det"], phi, phi)
         S = self.sign
         self.M1_e = S[:, :, None] * m1 * S[:, None, :]
         self.C_e = S[:, :, None] * c * S[:, None, :]

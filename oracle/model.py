@@ -18,13 +18,15 @@ class OracleParams:
     lambda_max: float = 0.0      # 0 -> power iteration
     quad_rule: int = averaging.QUAD_MIDPOINT
     upwind: int = UPWIND_STANDARD
+    geometry_degree: int = 1     # 1 flat cells, 3 the piecewise cubic surface of Sec. 3
 
 
 class OracleModel:
     def __init__(self, params: OracleParams):
         self.p = params
         self.mesh = build_mesh(params.refinement, params.radius)
-        self.ops = Operators(self.mesh, params.g, params.H, params.omega, params.radius, params.upwind)
+        self.ops = Operators(self.mesh, params.g, params.H, params.omega, params.radius, params.upwind,
+                             geometry_degree=params.geometry_degree)
         self.n_u, self.n_eta, self.n = self.ops.n_u, self.ops.n_eta, self.ops.n
         self.lam = params.lambda_max if params.lambda_max > 0 else spectrum.power_iteration(self.ops)
 

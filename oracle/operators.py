@@ -20,8 +20,20 @@ implementation's choices):
     elevation flux is single-valued and mass is conserved exactly;
   * the + cell of an edge is the one whose counter-clockwise boundary runs
     low -> high along it.
-All facet integrals use the 4-point Gauss-Legendre rule on [0, 1], tau = 0 at
-the low vertex; the upwind choice is made point by point.
+All facet integrals use the Gauss-Legendre rule on [0, 1] (4 points on flat
+cells, 5 on cubic ones), tau = 0 at the low vertex; the upwind choice is made
+point by point.
+
+Cell integrand, in reference form at each quadrature point (J, det, G = J^T J
+and grad_hat det taken at the point; u_hat the pulled-back velocity, psi_i the
+reference test function, q_i = cross2(u_hat, psi_i) / det = u_perp . w_i):
+  u . grad_perp q_i dA = (G u_hat) . curl_hat(q_i) / det dA_hat
+                       = [d_tau cross2(u_hat, psi_i) - cross2(u_hat, psi_i) d_tau det / det] / det^2,
+  div w_i |u|^2 / 2 dA = div_hat psi_i (u_hat . G u_hat) / (2 det^2) dA_hat,
+with d_tau = (G u_hat)_1 d/dxi0 - (G u_hat)_0 d/dxi1.  The d_tau det term
+vanishes on flat cells.  On a facet, each side uses its own J and det at the
+point: t . u |dx/dtau| = d . G u_hat / det for the reference edge direction
+d, and u . n ds = cross2(u_hat, d) dtau (the Piola map preserves fluxes).
 """
 
 import numpy as np
@@ -29,7 +41,7 @@ import scipy.sparse.linalg as spla
 
 from .assembly import Assembly, cross2
 from .elements import DG1_GRADS, EDGE_DIR, EDGE_START, dg1_values
-from .quadrature import FACET_POINTS, gauss_legendre_01, triangle_rule
+from .quadrature import facet_points, gauss_legendre_01, triangle_rule
 
 UPWIND_STANDARD = 0
 UPWIND_AS_PRINTED = 1
@@ -40,9 +52,10 @@ ELEVATION_STRONG = 1
 
 
 class Operators:
-    def __init__(self, mesh, g, H, omega, radius, upwind=UPWIND_STANDARD, elevation_form=ELEVATION_WEAK):
+    def __init__(self, mesh, g, H, omega, radius, upwind=UPWIND_STANDARD, elevation_form=ELEVATION_WEAK,
+                 geometry_degree=1):
         self.mesh = mesh
-        self.asm = Assembly(mesh, omega, radius)
+        self.asm = Assembly(mesh, omega, radius, geometry_degree)
         self.g = float(g)
         self.H = float(H)
         self.upwind = upwind
@@ -90,9 +103,10 @@ class Operators:
         F = self.mesh.n_cells
         c = A.sign * u[A.udofs]                                  # (F, 12) local coefficients
         h = eta[A.etadofs] - self.b[A.etadofs]                   # (F, 3)
-        G, det = A.G, A.det
         # ---- cell integrals
-        xq, wq = triangle_rule(4)
+        xq, wq = triangle_rule(A.cell_n)
+        geo = A.maps.geometry(xq)
+        G, det, gdet = geo["G"], geo["det"], geo["grad_det"]    # (F, Q, 2, 2), (F, Q), (F, Q, 2)
         psi = el.values(xq)                                      # (Q, 12, 2)
         dpsi = el.grads(xq)                                      # (Q, 12, 2c, 2a)
         divpsi = el.divs(xq)                                     # (Q, 12)
@@ -100,16 +114,19 @@ class Operators:
         uh = np.einsum("fj,qjc->fqc", c, psi)                    # (F, Q, 2)
         duh = np.einsum("fj,qjca->fqca", c, dpsi)                # (F, Q, 2, 2)
         hh = np.einsum("fk,qk->fq", h, phi)                      # (F, Q)
-        Guh = np.einsum("fab,fqb->fqa", G, uh)                   # (F, Q, 2)
+        Guh = np.einsum("fqab,fqb->fqa", G, uh)                  # (F, Q, 2)
         # q_i = cross2(uh, psi_i);  d q_i / d xi_a = cross2(d_a uh, psi_i) + cross2(uh, d_a psi_i)
         dq = np.zeros((F, len(wq), 12, 2))
         for a_ in range(2):
             dq[..., a_] = (duh[:, :, None, 0, a_] * psi[None, :, :, 1] - duh[:, :, None, 1, a_] * psi[None, :, :, 0]
                            + uh[:, :, None, 0] * dpsi[None, :, :, 1, a_] - uh[:, :, None, 1] * dpsi[None, :, :, 0, a_])
         curl_q = np.stack([-dq[..., 1], dq[..., 0]], axis=-1)   # (F, Q, 12, 2)
-        vort = np.einsum("q,fqa,fqia->fi", wq, Guh, curl_q) / det[:, None] ** 2
+        q0 = cross2(uh[:, :, None, :], psi[None])                # (F, Q, 12)
+        dtau_det = Guh[..., 1] * gdet[..., 0] - Guh[..., 0] * gdet[..., 1]
+        integrand = np.einsum("fqa,fqia->fqi", Guh, curl_q) - q0 * (dtau_det / det)[..., None]
+        vort = np.einsum("q,fq,fqi->fi", wq, 1.0 / det ** 2, integrand)
         ke = 0.5 * np.einsum("fqa,fqa->fq", uh, Guh)             # det^2 |u|^2 / 2
-        kin = np.einsum("q,qi,fq->fi", wq, divpsi, ke) / det[:, None] ** 2
+        kin = np.einsum("q,qi,fq->fi", wq, divpsi, ke / det ** 2)
         ru = vort + kin
         strong = self.elevation_form == ELEVATION_STRONG
         if strong:
@@ -121,11 +138,19 @@ class Operators:
         else:
             re = np.einsum("q,ia,fqa,fq->fi", wq, DG1_GRADS, uh, hh)
         # ---- facet integrals
-        tau, wt = gauss_legendre_01(FACET_POINTS)
+        tau, wt = gauss_legendre_01(facet_points(A.degree))
         cp, cm = self.mesh.edge_cells[:, 0], self.mesh.edge_cells[:, 1]
         ip, im = self.mesh.edge_local[:, 0], self.mesh.edge_local[:, 1]
         xp = EDGE_START[ip][:, None, :] + tau[None, :, None] * EDGE_DIR[ip][:, None, :]            # (E, P, 2)
         xm = EDGE_START[im][:, None, :] + (1.0 - tau)[None, :, None] * EDGE_DIR[im][:, None, :]
+        # each side's geometry at the facet points: evaluate every cell on each
+        # of its three edges (both parametrisations), then pick the edge's cells
+        gp = [A.maps.geometry(EDGE_START[i][None, :] + tau[:, None] * EDGE_DIR[i][None, :]) for i in range(3)]
+        gm = [A.maps.geometry(EDGE_START[i][None, :] + (1.0 - tau)[:, None] * EDGE_DIR[i][None, :]) for i in range(3)]
+        Gp = np.stack([g["G"] for g in gp])[ip, cp]              # (E, P, 2, 2)
+        Gm = np.stack([g["G"] for g in gm])[im, cm]
+        detp = np.stack([g["det"] for g in gp])[ip, cp]          # (E, P)
+        detm = np.stack([g["det"] for g in gm])[im, cm]
         E, P = xp.shape[0], xp.shape[1]
         psip = el.values(xp.reshape(-1, 2)).reshape(E, P, 12, 2)
         psim = el.values(xm.reshape(-1, 2)).reshape(E, P, 12, 2)
@@ -140,12 +165,12 @@ class Operators:
         flux = cross2(up, dp)                                    # u+ . n+ ds / dtau
         plus_up = flux > 0.0
         plus_up_vel = plus_up if self.upwind == UPWIND_STANDARD else (flux < 0.0)
-        tan_p = np.einsum("epa,eab,epb->ep", np.broadcast_to(dp, up.shape), G[cp], up) / det[cp][:, None]
-        tan_m = -np.einsum("epa,eab,epb->ep", np.broadcast_to(dm, um.shape), G[cm], um) / det[cm][:, None]
+        tan_p = np.einsum("epa,epab,epb->ep", np.broadcast_to(dp, up.shape), Gp, up) / detp
+        tan_m = -np.einsum("epa,epab,epb->ep", np.broadcast_to(dm, um.shape), Gm, um) / detm
         tan = np.where(plus_up_vel, tan_p, tan_m)               # |e| (t . u~)
         h_up = np.where(plus_up, hp, hm)
-        qp = cross2(up[:, :, None, :], psip) / det[cp][:, None, None]      # (E, P, 12)
-        qm = cross2(um[:, :, None, :], psim) / det[cm][:, None, None]
+        qp = cross2(up[:, :, None, :], psip) / detp[:, :, None]           # (E, P, 12)
+        qm = cross2(um[:, :, None, :], psim) / detm[:, :, None]
         fp = -np.einsum("p,epi,ep->ei", wt, qp, tan)
         fm = np.einsum("p,epi,ep->ei", wt, qm, tan)
         if strong:   # int_dK phi (h_own - h~) u . n_out, u . n_out = +flux (plus cell), -flux (minus cell)

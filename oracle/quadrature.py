@@ -3,13 +3,16 @@
 The flat-facet discretisation makes every cell integrand of L and N a
 polynomial in the reference coordinates (degree <= 5), so any rule exact to
 that degree gives the exact integral; the oracle uses a Stroud conical
-product rule with 4 x 4 points (exact to degree 7).
+product rule with 4 x 4 points (exact to degree 7).  On the piecewise cubic
+surface the integrands carry 1/det and are not polynomials: the 5 x 5 rule
+(exact to degree 9 for polynomials) is then part of the discretisation, and
+every implementation has to use it.
 
 The facet rule is different: the upwind choice in N (Sec. 2.5, the definition
 of u-tilde) is taken point by point, so the facet integral depends on where
 the points are.  The facet rule is therefore part of the method's definition:
-4-point Gauss-Legendre on each edge, parametrised from its low to its high
-vertex.
+Gauss-Legendre on each edge, parametrised from its low to its high vertex,
+with 4 points on flat cells and 5 on cubic ones.
 """
 
 import numpy as np
@@ -42,3 +45,13 @@ def triangle_rule(n=4):
 
 
 FACET_POINTS = 4
+
+
+def cell_rule_points(geometry_degree):
+    """Points per direction of the Stroud cell rule: 4 (flat), 5 (cubic)."""
+    return 4 if geometry_degree == 1 else 5
+
+
+def facet_points(geometry_degree):
+    """Gauss-Legendre points per facet: 4 (flat), 5 (cubic)."""
+    return FACET_POINTS if geometry_degree == 1 else 5
