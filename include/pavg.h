@@ -100,11 +100,17 @@ typedef struct {
                              F / SMs cells, at least 32); > 0 asks for parts of at least this many
                              cells, so a small mesh's solve occupies fewer SMs and solves of other
                              contexts can run beside it (batches, concurrent streams) */
+  int geometry_degree;    /* 1 (default): flat triangles through the mesh vertices; 3: the piecewise
+                             cubic approximation of the sphere of Sec. 3 (each cell the cubic
+                             interpolant of ten points projected onto the sphere), with the 5 x 5
+                             Stroud cell rule and 5-point facet rule that its non-polynomial
+                             integrands require; the same mesh, DOFs and state layout either way */
 } pavg_params;
 
 /* Fill `p` with the defaults: r = 3, R = 6.37122e6, Omega = 7.292e-5,
  * g = 9.80616, H = 5000, cheb_tol = 1e-6, cg_rtol = 1e-14, cg_maxit = 400,
- * lambda_max = 0, midpoint rule, standard upwinding, subdomain solver, FP64 precision. */
+ * lambda_max = 0, midpoint rule, standard upwinding, subdomain solver, FP64 precision,
+ * sd_part_cells = 0, geometry_degree = 1. */
 int pavg_default_params(pavg_params* p);
 
 /* Build the mesh and FE data (Sec. 2.5, Sec. 3) on the current CUDA device and

@@ -400,15 +400,17 @@ int check_flags(pavg_ctx* ctx) {
 }
 
 // Meshes and their operator data are shared by every context with the same
-// refinement, radius and rotation rate on one device: they are read-only after
-// set-up, and instances that share them also share their L2 footprint.
+// refinement, radius, rotation rate and geometry on one device: they are
+// read-only after set-up, and instances that share them also share their L2
+// footprint.
 std::mutex g_mesh_mu;
-std::map<std::tuple<int, double, double, int>, SharedMesh*> g_meshes;
+std::map<pavg_detail::MeshKey, SharedMesh*> g_meshes;
 
 void free_device_mesh(DeviceMesh& m) {
   cudaFree(m.cell_edges); cudaFree(m.cell_aligned); cudaFree(m.edge_plus); cudaFree(m.edge_minus);
   cudaFree(m.edge_lpos); cudaFree(m.M1); cudaFree(m.C); cudaFree(m.det); cudaFree(m.G); cudaFree(m.dinv);
   cudaFree(m.M1f); cudaFree(m.Pinv); cudaFree(m.M1p); cudaFree(m.tri);
+  cudaFree(m.M2e); cudaFree(m.M2i); cudaFree(m.geo_c); cudaFree(m.geo_f);
   m = DeviceMesh();
 }
 
@@ -418,8 +420,11 @@ int build_shared_mesh(const pavg_params* p, SharedMesh* sh, std::string* why) {
   build_reference_element(&el);
   HostCellData hc;
   ConstTables tab;
-  build_cell_data(sh->mesh, el, p->omega, &hc, &tab);
-  if (upload_tables(tab) != cudaSuccess || upload_chain_tables(tab) != cudaSuccess) {
+  TablesP3<double> tab3;
+  const bool cubic = p->geometry_degree == 3;
+  build_cell_data(sh->mesh, el, p->omega, p->geometry_degree, &hc, &tab, &tab3);
+  if (upload_tables(tab) != cudaSuccess || upload_chain_tables(tab) != cudaSuccess ||
+      (cubic && upload_tables3(tab3) != cudaSuccess)) {
     *why = "constant upload failed";
     return PAVG_ERR_CUDA;
   }
@@ -437,7 +442,9 @@ int build_shared_mesh(const pavg_params* p, SharedMesh* sh, std::string* why) {
                   upload(&m.C, hc.C) == cudaSuccess && upload(&m.det, hc.det) == cudaSuccess &&
                   upload(&m.G, hc.G) == cudaSuccess && upload(&m.dinv, hc.dinv) == cudaSuccess &&
                   upload(&m.Pinv, hc.Pinv) == cudaSuccess && upload(&m.tri, hc.tri) == cudaSuccess &&
-                  upload(&m.M1p, hc.M1p) == cudaSuccess && upload(&m.M1f, hc.M1f) == cudaSuccess;
+                  upload(&m.M1p, hc.M1p) == cudaSuccess && upload(&m.M1f, hc.M1f) == cudaSuccess &&
+                  (!cubic || (upload(&m.M2e, hc.M2e) == cudaSuccess && upload(&m.M2i, hc.M2i) == cudaSuccess &&
+                              upload(&m.geo_c, hc.geo_c) == cudaSuccess && upload(&m.geo_f, hc.geo_f) == cudaSuccess));
   if (!ok) {
     free_device_mesh(m);
     *why = "device upload failed";
@@ -472,7 +479,7 @@ int sd_partition_for(SharedMesh* sh, int P, SdMesh* out, std::string* why) {
 
 int acquire_mesh(const pavg_params* p, int device, SharedMesh** out, std::string* why) {
   std::lock_guard<std::mutex> lock(g_mesh_mu);
-  const auto key = std::make_tuple(p->refinement, p->radius, p->omega, device);
+  const pavg_detail::MeshKey key = std::make_tuple(p->refinement, p->radius, p->omega, device, p->geometry_degree);
   auto it = g_meshes.find(key);
   if (it != g_meshes.end()) {
     ++it->second->refs;
@@ -538,7 +545,8 @@ bool valid_params(const pavg_params* p) {
          (p->quad_rule == PAVG_QUAD_MIDPOINT || p->quad_rule == PAVG_QUAD_CLOSED) &&
          (p->upwind_convention == PAVG_UPWIND_STANDARD || p->upwind_convention == PAVG_UPWIND_AS_PRINTED) &&
          (p->solver == PAVG_SOLVER_MIXED || p->solver == PAVG_SOLVER_FP64 || p->solver == PAVG_SOLVER_SUBDOMAIN) &&
-         (p->precision == PAVG_PRECISION_FP64 || p->precision == PAVG_PRECISION_MIXED) && p->sd_part_cells >= 0;
+         (p->precision == PAVG_PRECISION_FP64 || p->precision == PAVG_PRECISION_MIXED) && p->sd_part_cells >= 0 &&
+         (p->geometry_degree == 1 || p->geometry_degree == 3);
 }
 
 }  // namespace pavg_api
@@ -563,6 +571,7 @@ int pavg_default_params(pavg_params* p) {
   p->solver = PAVG_SOLVER_SUBDOMAIN;
   p->precision = PAVG_PRECISION_FP64;
   p->sd_part_cells = 0;
+  p->geometry_degree = 1;
   return PAVG_OK;
 }
 

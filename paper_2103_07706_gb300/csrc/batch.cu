@@ -25,6 +25,13 @@ struct ChainTables {
 };
 __constant__ ChainTables c_ktab;
 
+// Entry (k, l) of cell c's M2^{-1} on the cubic surface (packed 00, 01, 02, 11, 12, 22; [6][F]).
+__device__ __forceinline__ double m2i(const DeviceMesh& m, int64_t c, int k, int l) {
+  const int a = k < l ? k : l, b = k < l ? l : k;
+  const int idx = a == 0 ? b : (a == 1 ? 2 + b : 5);
+  return __ldg(&m.M2i[idx * m.F + c]);
+}
+
 // Step 1 on the solver's thread layout (four threads per cell, thread q of
 // cell c holds DOF triple t = tri(c, q), edges q < 3, interior q = 3):
 //   ru[3t+j] += y_u (owner only) + s (-C u + g D^T eta)   rows 3q+j of the cell,
@@ -93,17 +100,27 @@ __device__ __forceinline__ void apply_K_phase(const DeviceMesh& m, const double*
           if (y_eta) rl[l] += __ldcg(&y_eta[3 * c + l]);
         }
         double v = 0.0;
+        if (m.M2i) {  // cubic cells: the cell's own M2^{-1}
 #pragma unroll
-        for (int l = 0; l < 3; ++l) v = fma(c_ktab.M2inv_ref[q][l], rl[l], v);
-        v *= 1.0 / m.det[c];
+          for (int l = 0; l < 3; ++l) v = fma(m2i(m, c, q, l), rl[l], v);
+        } else {
+#pragma unroll
+          for (int l = 0; l < 3; ++l) v = fma(c_ktab.M2inv_ref[q][l], rl[l], v);
+          v *= 1.0 / m.det[c];
+        }
         if (z_eta) v += __ldcg(&z_eta[3 * c + q]);
         eta_out[3 * c + q] = v;
       }
     } else if (q < 3) {
       double v = 0.0;
+      if (m.M2i) {
 #pragma unroll
-      for (int l = 0; l < 3; ++l) v = fma(c_ktab.M2inv_ref[q][l], __ldcg(&y_eta[3 * c + l]), v);
-      v *= 1.0 / m.det[c];
+        for (int l = 0; l < 3; ++l) v = fma(m2i(m, c, q, l), __ldcg(&y_eta[3 * c + l]), v);
+      } else {
+#pragma unroll
+        for (int l = 0; l < 3; ++l) v = fma(c_ktab.M2inv_ref[q][l], __ldcg(&y_eta[3 * c + l]), v);
+        v *= 1.0 / m.det[c];
+      }
       if (z_eta) v += __ldcg(&z_eta[3 * c + q]);
       eta_out[3 * c + q] = v;
     }

@@ -33,10 +33,12 @@ struct AvgPlan {
 };
 
 // Mesh and operator data shared by the contexts with the same refinement,
-// radius, rotation rate and device (reference counted, read-only after set-up).
+// radius, rotation rate, device and geometry degree (reference counted,
+// read-only after set-up).
+using MeshKey = std::tuple<int, double, double, int, int>;
 struct SharedMesh {
   int refs = 0;
-  std::tuple<int, double, double, int> key;
+  MeshKey key;
   pavg_detail::SharedMesh* shared = nullptr;
   pavg::Mesh mesh;
   pavg::DeviceMesh dm;  // topo stays per context

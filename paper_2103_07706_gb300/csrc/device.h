@@ -29,6 +29,11 @@ struct DeviceMesh {
   float* Pinv = nullptr;            // [E + F][8] inverses of the 3x3 diagonal blocks of M1, FP32, padded
   float* M1p = nullptr;             // [78][F] packed M1 in FP32 (loaded into shared memory), or null
   int32_t* tri = nullptr;           // [F][4] DOF triple of (cell, q) with the owner flag in bit 31
+  // piecewise cubic surface only (null on flat cells, where M2 = det * M2_ref)
+  double* M2e = nullptr;            // [6][F] DG1 element mass matrices, packed 00, 01, 02, 11, 12, 22
+  double* M2i = nullptr;            // [6][F] their inverses
+  double* geo_c = nullptr;          // [6][kCellQ3][F] G00, G01, G11, w / det^2, d0 det / det, d1 det / det
+  double* geo_f = nullptr;          // [8][kFacetQ3][E] plus side G00, G01, G11, det; then minus side
 };
 
 // Scratch of the persistent CG solver.
@@ -225,6 +230,7 @@ cudaError_t sur_gather_rows(const float* src, const int* idx, int rows, int cols
 
 // Upload constant tables (reference element data) to the current device.
 cudaError_t upload_tables(const ConstTables& t);
+cudaError_t upload_tables3(const TablesP3<double>& t);  // the cubic-geometry nonlinear kernels' tables
 
 // Grid size for the persistent CG kernel (all blocks co-resident).
 cudaError_t cg_configure(int64_t F, CgWork* w);

@@ -18,11 +18,21 @@ namespace pavg {
 __constant__ ConstTables c_tab;
 __constant__ TablesT<float> c_tabf;
 
+__constant__ TablesP3<double> c_tab3;
+__constant__ TablesP3<float> c_tab3f;
+
 cudaError_t upload_tables(const ConstTables& t) {
   cudaError_t e = cudaMemcpyToSymbol(c_tab, &t, sizeof(t));
   if (e != cudaSuccess) return e;
   const TablesT<float> f = tables_to_float(t);
   return cudaMemcpyToSymbol(c_tabf, &f, sizeof(f));
+}
+
+cudaError_t upload_tables3(const TablesP3<double>& t) {
+  cudaError_t e = cudaMemcpyToSymbol(c_tab3, &t, sizeof(t));
+  if (e != cudaSuccess) return e;
+  const TablesP3<float> f = tables_to_float(t);
+  return cudaMemcpyToSymbol(c_tab3f, &f, sizeof(f));
 }
 
 namespace {
@@ -199,6 +209,15 @@ __global__ void __launch_bounds__(kCgThreads) k_cg(DeviceMesh m, CgWork w, CgPar
   }
 }
 
+// Entry (k, l) of a cell's symmetric 3 x 3 matrix stored packed 00, 01, 02,
+// 11, 12, 22 in structure-of-arrays form [6][F] (k, l compile-time constants
+// in unrolled loops).
+__device__ __forceinline__ double sym3(const double* __restrict__ P, int64_t F, int64_t c, int k, int l) {
+  const int a = k < l ? k : l, b = k < l ? l : k;
+  const int idx = a == 0 ? b : (a == 1 ? 2 + b : 5);
+  return __ldg(&P[idx * F + c]);
+}
+
 // ru = y_u + s (-C u + g D^T eta);  eta_out = M2^{-1}(y_eta + s (-H D u)) + z_eta.
 __global__ void __launch_bounds__(128) k_apply_K(DeviceMesh m, const double* __restrict__ U, double s,
                                                  double g, double H, const double* __restrict__ y_u,
@@ -244,16 +263,29 @@ __global__ void __launch_bounds__(128) k_apply_K(DeviceMesh m, const double* __r
     if (i < 9) atomicAdd(&ru[dof[i]], v);
     else ru[dof[i]] = v;
   }
+  double rl[3];
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    rl[l] = s * (-H * Du[l]);
+    if (y_eta) rl[l] += __ldg(&y_eta[3 * c + l]);
+  }
+  if (m.M2i) {  // cubic cells: the cell's own M2^{-1}
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      double v = 0.0;
+#pragma unroll
+      for (int l = 0; l < 3; ++l) v = fma(sym3(m.M2i, F, c, k, l), rl[l], v);
+      if (z_eta) v += __ldg(&z_eta[3 * c + k]);
+      eta_out[3 * c + k] = v;
+    }
+    return;
+  }
   const double idet = 1.0 / m.det[c];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     double v = 0.0;
 #pragma unroll
-    for (int l = 0; l < 3; ++l) {
-      double rl = s * (-H * Du[l]);
-      if (y_eta) rl += __ldg(&y_eta[3 * c + l]);
-      v = fma(c_tab.M2inv_ref[k][l], rl, v);
-    }
+    for (int l = 0; l < 3; ++l) v = fma(c_tab.M2inv_ref[k][l], rl[l], v);
     v *= idet;
     if (z_eta) v += __ldg(&z_eta[3 * c + k]);
     eta_out[3 * c + k] = v;
@@ -270,6 +302,18 @@ template <>
 __device__ __forceinline__ const TablesT<double>& tab<double>() { return c_tab; }
 template <>
 __device__ __forceinline__ const TablesT<float>& tab<float>() { return c_tabf; }
+template <typename R>
+__device__ __forceinline__ const TablesP3<R>& tab3();
+template <>
+__device__ __forceinline__ const TablesP3<double>& tab3<double>() { return c_tab3; }
+template <>
+__device__ __forceinline__ const TablesP3<float>& tab3<float>() { return c_tab3f; }
+// the nonlinear kernels' tables for geometry degree GEO
+template <typename R, int GEO>
+__device__ __forceinline__ const auto& ntab() {
+  if constexpr (GEO == 3) return tab3<R>();
+  else return tab<R>();
+}
 
 // Explicitly rounded operations (never contracted or reordered by the compiler).
 template <typename R>
@@ -328,6 +372,13 @@ __device__ __forceinline__ void load_side(const DeviceMesh& m, const double* __r
   S.G11 = (R)__ldg(&m.G[2 * m.F + cell]);
 }
 
+// One side's metric at a facet point: the cell's constant one on flat cells,
+// the cubic map's at the point otherwise.
+template <typename R>
+struct SideGeom {
+  R G00, G01, G11, det;
+};
+
 template <typename R>
 struct FacetValues {
   R flux;     // u+ . n+ ds / dtau
@@ -341,10 +392,10 @@ struct FacetValues {
 // explicitly rounded operations so that both cells obtain identical bits.
 // Upwind: the side the flow leaves (flux > 0: plus); the printed rule of
 // Sec. 2.5 (u~ = u+ when u . n+ < 0) is the alternative for the velocity.
-template <typename R>
-__device__ __forceinline__ FacetValues<R> facet_point(const Side<R>& P, int lp, const Side<R>& Mn, int lm, int p,
+template <typename R, typename TT>
+__device__ __forceinline__ FacetValues<R> facet_point(const TT& T, const Side<R>& P, const SideGeom<R>& gP, int lp,
+                                                      const Side<R>& Mn, const SideGeom<R>& gM, int lm, int p,
                                                       int upwind) {
-  const TablesT<R>& T = tab<R>();
   using O = Rn<R>;
   FacetValues<R> f;
   R a0 = 0, a1 = 0, b0 = 0, b1 = 0, hp = 0, hm = 0;
@@ -367,13 +418,13 @@ __device__ __forceinline__ FacetValues<R> facet_point(const Side<R>& P, int lp, 
   const bool plus_up_vel = upwind == PAVG_UPWIND_STANDARD ? plus_up : (flux < R(0));
   R tan;
   if (plus_up_vel) {
-    R g0 = O::fma(P.G00, a0, O::mul(P.G01, a1));
-    R g1 = O::fma(P.G01, a0, O::mul(P.G11, a1));
-    tan = O::div(O::fma(dp0, g0, O::mul(dp1, g1)), P.det);
+    R g0 = O::fma(gP.G00, a0, O::mul(gP.G01, a1));
+    R g1 = O::fma(gP.G01, a0, O::mul(gP.G11, a1));
+    tan = O::div(O::fma(dp0, g0, O::mul(dp1, g1)), gP.det);
   } else {
-    R g0 = O::fma(Mn.G00, b0, O::mul(Mn.G01, b1));
-    R g1 = O::fma(Mn.G01, b0, O::mul(Mn.G11, b1));
-    tan = -O::div(O::fma(dm0, g0, O::mul(dm1, g1)), Mn.det);
+    R g0 = O::fma(gM.G00, b0, O::mul(gM.G01, b1));
+    R g1 = O::fma(gM.G01, b0, O::mul(gM.G11, b1));
+    tan = -O::div(O::fma(dm0, g0, O::mul(dm1, g1)), gM.det);
   }
   f.flux = flux;
   f.tan = tan;
@@ -391,12 +442,17 @@ __device__ __forceinline__ FacetValues<R> facet_point(const Side<R>& P, int lp, 
 //   re_k -/+ w phi_k (u . n+) ((eta - b)_side - (eta - b)~)   (elevation tests, strong form)
 // are summed over the points in FP64 and stored in the side's slot
 // FR[cell][local edge][15] (each slot written by exactly one edge).
-template <typename R>
+// GEO = 1: flat cells (4 points, each cell's constant metric); GEO = 3: the
+// piecewise cubic surface (5 points, each side's metric at the point, from
+// m.geo_f), where the scale factor of the velocity term is 1 / det of the
+// side at the point.
+template <typename R, int GEO>
 __global__ void __launch_bounds__(128) k_facets(DeviceMesh m, const double* __restrict__ Uall, double* FRall,
                                                 int upwind) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m.E) return;
-  const TablesT<R>& T = tab<R>();
+  constexpr int NQ = GEO == 3 ? kFacetQ3 : kFacetQ;
+  const auto& T = ntab<R, GEO>();
   constexpr bool kStrongDG = true;  // both precisions: see k_nonlinear
   const double* U = Uall + (int64_t)blockIdx.y * m.n;
   double* FR = FRall + (int64_t)blockIdx.y * m.F * 45;
@@ -410,10 +466,21 @@ __global__ void __launch_bounds__(128) k_facets(DeviceMesh m, const double* __re
 #pragma unroll
   for (int j = 0; j < 12; ++j) rp[j] = rm[j] = 0.0;
 #pragma unroll 1
-  for (int p = 0; p < kFacetQ; ++p) {
+  for (int p = 0; p < NQ; ++p) {
     const R wp = T.fq_w[p];
-    const FacetValues<R> f = facet_point(P, lp, Mn, lm, p, upwind);
-    const R scp = -wp * f.tan / P.det, scm = wp * f.tan / Mn.det;
+    SideGeom<R> gP, gM;
+    if constexpr (GEO == 3) {
+      const int64_t PE = (int64_t)NQ * m.E, o = (int64_t)p * m.E + e;
+      gP = {(R)__ldg(&m.geo_f[0 * PE + o]), (R)__ldg(&m.geo_f[1 * PE + o]), (R)__ldg(&m.geo_f[2 * PE + o]),
+            (R)__ldg(&m.geo_f[3 * PE + o])};
+      gM = {(R)__ldg(&m.geo_f[4 * PE + o]), (R)__ldg(&m.geo_f[5 * PE + o]), (R)__ldg(&m.geo_f[6 * PE + o]),
+            (R)__ldg(&m.geo_f[7 * PE + o])};
+    } else {
+      gP = {P.G00, P.G01, P.G11, P.det};
+      gM = {Mn.G00, Mn.G01, Mn.G11, Mn.det};
+    }
+    const FacetValues<R> f = facet_point(T, P, gP, lp, Mn, gM, lm, p, upwind);
+    const R scp = -wp * f.tan / gP.det, scm = wp * f.tan / gM.det;
 #pragma unroll
     for (int j = 0; j < 12; ++j) {
       rp[j] += (double)(scp * (f.up0 * T.fq_psi[0][lp][p][j][1] - f.up1 * T.fq_psi[0][lp][p][j][0]));
@@ -454,12 +521,21 @@ __global__ void __launch_bounds__(128) k_facets(DeviceMesh m, const double* __re
 // not).  In FP64 that cancellation cost about two decimal digits of the
 // elevation part of N on balanced states at refinement 6; in FP32 all of
 // them.
-template <typename R>
+//
+// GEO = 3, the piecewise cubic surface: J, det and G vary over the cell and
+// the integrand gains the term of d_tau det (the derivative of 1 / det in
+// u_perp . w_i = cross2(u_hat, psi_i) / det):
+//   w / det^2 [d_tau cross2(u_hat, psi_i) - cross2(u_hat, psi_i) d_tau det / det
+//              + div psi_i (u_hat . v) / 2],
+// with G, w / det^2 and grad_hat det / det per point from m.geo_c and the
+// 25-point Stroud rule.  The elevation terms do not involve the geometry.
+template <typename R, int GEO>
 __global__ void __launch_bounds__(128) k_nonlinear(DeviceMesh m, const double* __restrict__ Uall, double* Rall,
                                                    const double* __restrict__ FRall) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= m.F) return;
-  const TablesT<R>& T = tab<R>();
+  constexpr int NQ = GEO == 3 ? kCellQ3 : kCellQ;
+  const auto& T = ntab<R, GEO>();
   constexpr bool kStrongDG = true;  // both precisions: see k_nonlinear
   const int64_t n = m.n;
   const double* U = Uall + (int64_t)blockIdx.y * n;
@@ -471,7 +547,7 @@ __global__ void __launch_bounds__(128) k_nonlinear(DeviceMesh m, const double* _
   for (int i = 0; i < 12; ++i) r[i] = 0.0;
   // ---- cell terms
 #pragma unroll 1
-  for (int q = 0; q < kCellQ; ++q) {
+  for (int q = 0; q < NQ; ++q) {
     R u0 = 0, u1 = 0, d00 = 0, d01 = 0, d10 = 0, d11 = 0;  // d_ca = d u_c / d x_a
 #pragma unroll
     for (int j = 0; j < 12; ++j) {
@@ -484,16 +560,37 @@ __global__ void __launch_bounds__(128) k_nonlinear(DeviceMesh m, const double* _
       d11 = fma(cj, T.cq_dpsi[q][j][1][1], d11);
     }
     const R h = own.h[0] * T.cq_phi[q][0] + own.h[1] * T.cq_phi[q][1] + own.h[2] * T.cq_phi[q][2];
-    const R v0 = own.G00 * u0 + own.G01 * u1;
-    const R v1 = own.G01 * u0 + own.G11 * u1;
+    R G00, G01, G11, W;
+    R tx = 0, ty = 0;  // grad_hat det / det (cubic cells)
+    if constexpr (GEO == 3) {
+      const int64_t QF = (int64_t)NQ * m.F, o = (int64_t)q * m.F + c;
+      G00 = (R)__ldg(&m.geo_c[0 * QF + o]);
+      G01 = (R)__ldg(&m.geo_c[1 * QF + o]);
+      G11 = (R)__ldg(&m.geo_c[2 * QF + o]);
+      W = (R)__ldg(&m.geo_c[3 * QF + o]);
+      tx = (R)__ldg(&m.geo_c[4 * QF + o]);
+      ty = (R)__ldg(&m.geo_c[5 * QF + o]);
+    } else {
+      G00 = own.G00;
+      G01 = own.G01;
+      G11 = own.G11;
+      W = T.cq_w[q];
+    }
+    const R v0 = G00 * u0 + G01 * u1;
+    const R v1 = G01 * u0 + G11 * u1;
     const R wq = T.cq_w[q];
     const R half_ke = R(0.5) * (u0 * v0 + u1 * v1);
-    const R t0 = v1 * d00 - v0 * d01;  // d_tau u_hat
-    const R t1 = v1 * d10 - v0 * d11;
+    R t0 = v1 * d00 - v0 * d01;  // d_tau u_hat
+    R t1 = v1 * d10 - v0 * d11;
+    if constexpr (GEO == 3) {  // - cross2(u_hat, psi_i) d_tau det / det
+      const R tau = v1 * tx - v0 * ty;
+      t0 -= u0 * tau;
+      t1 -= u1 * tau;
+    }
     // coefficients of psi_i0, psi_i1, d0 psi_i0, d1 psi_i0, d0 psi_i1, d1 psi_i1
-    const R k0 = -t1 * wq, k1 = t0 * wq;
-    const R k2 = (-u1 * v1 + half_ke) * wq, k3 = (u1 * v0) * wq;
-    const R k4 = (u0 * v1) * wq, k5 = (-u0 * v0 + half_ke) * wq;
+    const R k0 = -t1 * W, k1 = t0 * W;
+    const R k2 = (-u1 * v1 + half_ke) * W, k3 = (u1 * v0) * W;
+    const R k4 = (u0 * v1) * W, k5 = (-u0 * v0 + half_ke) * W;
 #pragma unroll
     for (int i = 0; i < 12; ++i) {
       R t = k0 * T.cq_psi[q][i][0];
@@ -518,9 +615,11 @@ __global__ void __launch_bounds__(128) k_nonlinear(DeviceMesh m, const double* _
       re[2] += (double)(u1 * hw);
     }
   }
-  const double idet2 = 1.0 / ((double)own.det * (double)own.det);
+  if constexpr (GEO != 3) {  // flat cells: the constant 1 / det^2 (per point on cubic cells)
+    const double idet2 = 1.0 / ((double)own.det * (double)own.det);
 #pragma unroll
-  for (int i = 0; i < 12; ++i) r[i] *= idet2;
+    for (int i = 0; i < 12; ++i) r[i] *= idet2;
+  }
   // ---- facet terms, evaluated once per edge by k_facets (slots [c][local edge][15])
   const double* FR = FRall + ((int64_t)blockIdx.y * m.F + c) * 45;
 #pragma unroll
@@ -550,10 +649,20 @@ __global__ void k_m2inv(DeviceMesh m, const double* __restrict__ r, int64_t rstr
   if (c >= m.F) return;
   const double* rb = r + blockIdx.y * rstride;
   double* ob = out + blockIdx.y * ostride;
-  const double idet = 1.0 / m.det[c];
   double v[3];
 #pragma unroll
   for (int l = 0; l < 3; ++l) v[l] = rb[3 * c + l];
+  if (m.M2i) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      double t = 0.0;
+#pragma unroll
+      for (int l = 0; l < 3; ++l) t = fma(sym3(m.M2i, m.F, c, k, l), v[l], t);
+      ob[3 * c + k] = t;
+    }
+    return;
+  }
+  const double idet = 1.0 / m.det[c];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     double t = 0.0;
@@ -624,8 +733,11 @@ __global__ void __launch_bounds__(256) k_winner(DeviceMesh m, const double* __re
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
-      for (int l = 0; l < 3; ++l)
-        se = fma(U[m.n_u + 3 * c + k] * c_tab.M2_ref[k][l] * det, V[m.n_u + 3 * c + l], se);
+      for (int l = 0; l < 3; ++l) {
+        const double a = m.M2e ? U[m.n_u + 3 * c + k] * sym3(m.M2e, m.F, c, k, l)
+                               : U[m.n_u + 3 * c + k] * c_tab.M2_ref[k][l] * det;
+        se = fma(a, V[m.n_u + 3 * c + l], se);
+      }
     acc += H * su + g * se;
   }
   double s3[3];
@@ -661,8 +773,13 @@ __global__ void __launch_bounds__(256) k_norms(DeviceMesh m, const double* __res
     for (int k = 0; k < 3; ++k)
 #pragma unroll
       for (int l = 0; l < 3; ++l) {
-        dv = fma(d[k] * c_tab.M2inv_ref[k][l] / det, d[l], dv);
-        e = fma(h[k] * c_tab.M2_ref[k][l] * det, h[l], e);
+        if (m.M2i) {  // cubic cells: the cell's own M2 and M2^{-1}
+          dv = fma(d[k] * sym3(m.M2i, m.F, c, k, l), d[l], dv);
+          e = fma(h[k] * sym3(m.M2e, m.F, c, k, l), h[l], e);
+        } else {
+          dv = fma(d[k] * c_tab.M2inv_ref[k][l] / det, d[l], dv);
+          e = fma(h[k] * c_tab.M2_ref[k][l] * det, h[l], e);
+        }
       }
   }
   double s3[3];
@@ -742,12 +859,19 @@ cudaError_t launch_nonlinear_rhs(const DeviceMesh& m, const double* U, double* r
     const double* Ub = U + (int64_t)b0 * m.n;
     double* rb = r + (int64_t)b0 * m.n;
     dim3 ge((unsigned)((m.E + 127) / 128), (unsigned)nb), gc((unsigned)((m.F + 127) / 128), (unsigned)nb);
-    if (fp32) {
-      k_facets<float><<<ge, 128, 0, st>>>(m, Ub, facets, upwind);
-      k_nonlinear<float><<<gc, 128, 0, st>>>(m, Ub, rb, facets);
+    const bool cubic = m.geo_c != nullptr;
+    if (fp32 && cubic) {
+      k_facets<float, 3><<<ge, 128, 0, st>>>(m, Ub, facets, upwind);
+      k_nonlinear<float, 3><<<gc, 128, 0, st>>>(m, Ub, rb, facets);
+    } else if (fp32) {
+      k_facets<float, 1><<<ge, 128, 0, st>>>(m, Ub, facets, upwind);
+      k_nonlinear<float, 1><<<gc, 128, 0, st>>>(m, Ub, rb, facets);
+    } else if (cubic) {
+      k_facets<double, 3><<<ge, 128, 0, st>>>(m, Ub, facets, upwind);
+      k_nonlinear<double, 3><<<gc, 128, 0, st>>>(m, Ub, rb, facets);
     } else {
-      k_facets<double><<<ge, 128, 0, st>>>(m, Ub, facets, upwind);
-      k_nonlinear<double><<<gc, 128, 0, st>>>(m, Ub, rb, facets);
+      k_facets<double, 1><<<ge, 128, 0, st>>>(m, Ub, facets, upwind);
+      k_nonlinear<double, 1><<<gc, 128, 0, st>>>(m, Ub, rb, facets);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -14,6 +14,11 @@ namespace pavg {
 // definition because the upwind choice is taken per point).
 constexpr int kCellQ = 7;
 constexpr int kFacetQ = 4;
+// On the piecewise cubic surface (Sec. 3) the integrands carry 1/det and are
+// not polynomials, so the rules are part of the discretisation: the 5 x 5
+// Stroud conical product rule in cells, 5-point Gauss-Legendre on facets.
+constexpr int kCellQ3 = 25;
+constexpr int kFacetQ3 = 5;
 
 // Canonical icosahedral mesh (paper Sec. 3).
 struct Mesh {
@@ -68,6 +73,29 @@ struct TablesT {
 };
 using ConstTables = TablesT<double>;
 
+// Reference tables of the cubic-geometry nonlinear kernels (same layout
+// conventions as TablesT, for the rules of kCellQ3 and kFacetQ3 points).
+template <typename R>
+struct TablesP3 {
+  R cq_w[kCellQ3];
+  R cq_psi[kCellQ3][12][2];
+  R cq_dpsi[kCellQ3][12][2][2];
+  R cq_phi[kCellQ3][3];
+  R fq_w[kFacetQ3];
+  R fq_psi[2][3][kFacetQ3][12][2];
+  R fq_phi[2][3][kFacetQ3][3];
+  R edge_dir[3][2];
+};
+
+inline TablesP3<float> tables_to_float(const TablesP3<double>& t) {
+  static_assert(sizeof(TablesP3<double>) == 2 * sizeof(TablesP3<float>), "tables must be plain arrays");
+  TablesP3<float> f;
+  const double* src = reinterpret_cast<const double*>(&t);
+  float* dst = reinterpret_cast<float*>(&f);
+  for (size_t i = 0; i < sizeof(TablesP3<double>) / sizeof(double); ++i) dst[i] = (float)src[i];
+  return f;
+}
+
 inline TablesT<float> tables_to_float(const ConstTables& t) {
   static_assert(sizeof(ConstTables) == 2 * sizeof(TablesT<float>), "tables must be plain arrays");
   TablesT<float> f;
@@ -89,9 +117,29 @@ struct HostCellData {
   std::vector<float> Pinv;     // [E + F][8] inverses of the 3x3 diagonal blocks of M1 (00,01,02,11,12,22,-,-)
   std::vector<float> M1p;      // [78][F] M1 rounded to FP32, packed upper triangle (shared-memory path)
   std::vector<int32_t> tri;    // [F][4] DOF triple of (cell, q) | owner bit 31 (q = 0..2 edges, 3 interior)
+  // cubic geometry only (empty on flat cells, where M2 = det * M2_ref)
+  std::vector<double> M2e;     // [6][F] DG1 element mass matrices, packed 00, 01, 02, 11, 12, 22
+  std::vector<double> M2i;     // [6][F] their inverses, same packing
+  std::vector<double> geo_c;   // [6][kCellQ3][F] per cell point: G00, G01, G11, w / det^2,
+                               // (d det / d xi0) / det, (d det / d xi1) / det
+  std::vector<double> geo_f;   // [8][kFacetQ3][E] per edge point: the plus cell's G00, G01, G11, det,
+                               // then the minus cell's, each at its own parameter of the point
 };
-void build_cell_data(const Mesh& m, const RefElement& el, double omega, HostCellData* out,
-                     ConstTables* tab);
+// Element data on the flat (geometry_degree 1) or piecewise cubic (3) surface.
+// `tab3` receives the cubic kernels' tables (filled for degree 3 only).
+void build_cell_data(const Mesh& m, const RefElement& el, double omega, int geometry_degree, HostCellData* out,
+                     ConstTables* tab, TablesP3<double>* tab3);
+
+// The cubic cell map (Sec. 3) of cell c at reference point (x, y).
+struct PointGeometry {
+  double x[3];                  // the point
+  double J[3][2];               // dx / dxi
+  double det, G00, G01, G11;    // |J0 x J1|, J^T J
+  double ddet[2];               // d det / d xi_a
+};
+void p3_geometry(const Mesh& m, int64_t c, double x, double y, PointGeometry* g);
+// 5 x 5 Stroud conical product rule on the reference triangle (area 1/2).
+void stroud_rule(int n, std::vector<double>* px, std::vector<double>* py, std::vector<double>* pw);
 
 // Partition of the cells for the subdomain mass solver: part p owns the
 // contiguous cells cell0[p] .. cell0[p+1]-1 and numbers the DOF triples its

@@ -180,6 +180,202 @@ void gauss_legendre01(int n, double* x, double* w) {
 
 namespace {
 
+// Jacobi polynomial P_n^{(a,b)}(x) by its three-term recurrence in n.
+double jacobi(int n, double a, double b, double x) {
+  if (n == 0) return 1.0;
+  double p0 = 1.0, p1 = 0.5 * (2.0 * (a + 1.0) + (a + b + 2.0) * (x - 1.0));
+  for (int k = 2; k <= n; ++k) {
+    const double s = 2.0 * k + a + b;
+    const double c1 = 2.0 * k * (k + a + b) * (s - 2.0);
+    const double c2 = (s - 1.0) * (s * (s - 2.0) * x + a * a - b * b);
+    const double c3 = 2.0 * (k + a - 1.0) * (k + b - 1.0) * s;
+    const double p2 = (c2 * p1 - c3 * p0) / c1;
+    p0 = p1;
+    p1 = p2;
+  }
+  return p1;
+}
+
+}  // namespace
+
+// Gauss-Jacobi rule for the weight (1 - x) on [-1, 1] (a = 1, b = 0): the
+// nodes are the zeros of P_n^{(1,0)}, bracketed by sign changes on a fine grid
+// and bisected to the last bit; the weights are
+// 4 / ((1 - x^2) P_n'(x)^2), with P_n' = (n + 2)/2 P_{n-1}^{(2,1)}.
+void gauss_jacobi10(int n, double* x, double* w) {
+  const int grid = 4096;
+  int found = 0;
+  double xa = -1.0, fa = jacobi(n, 1.0, 0.0, xa);
+  for (int k = 1; k <= grid && found < n; ++k) {
+    const double xb = -1.0 + 2.0 * k / grid, fb = jacobi(n, 1.0, 0.0, xb);
+    if (fa == 0.0 || (fa < 0.0) != (fb < 0.0)) {
+      double lo = xa, hi = xb, flo = fa;
+      for (int it = 0; it < 200 && hi - lo > 0.0; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        const double fm = jacobi(n, 1.0, 0.0, mid);
+        if ((fm < 0.0) == (flo < 0.0)) { lo = mid; flo = fm; } else hi = mid;
+      }
+      x[found++] = 0.5 * (lo + hi);
+    }
+    xa = xb;
+    fa = fb;
+  }
+  if (found != n) throw std::runtime_error("Gauss-Jacobi: roots not bracketed");
+  for (int i = 0; i < n; ++i) {
+    const double d = 0.5 * (n + 2.0) * jacobi(n - 1, 2.0, 1.0, x[i]);
+    w[i] = 4.0 / ((1.0 - x[i] * x[i]) * d * d);
+  }
+}
+
+// Stroud conical product rule on the reference triangle: x = s, y = t (1 - s)
+// with s from Gauss-Jacobi (its weight absorbs the Jacobian 1 - s, mapped to
+// [0, 1]) and t from Gauss-Legendre; n x n points, exact to degree 2n - 1.
+// Checked against int x^a y^b = a! b! / (a + b + 2)! for a + b <= 2n - 1.
+void stroud_rule(int n, std::vector<double>* px, std::vector<double>* py, std::vector<double>* pw) {
+  std::vector<double> xs(n), ws(n), t(n), wt(n);
+  gauss_jacobi10(n, xs.data(), ws.data());
+  gauss_legendre01(n, t.data(), wt.data());
+  px->clear(); py->clear(); pw->clear();
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const double s = 0.5 * (xs[i] + 1.0);
+      px->push_back(s);
+      py->push_back(t[j] * (1.0 - s));
+      pw->push_back(0.25 * ws[i] * wt[j]);
+    }
+  for (int a = 0; a <= 2 * n - 1; ++a)
+    for (int b = 0; a + b <= 2 * n - 1; ++b) {
+      double sum = 0.0;
+      for (size_t k = 0; k < pw->size(); ++k) sum += (*pw)[k] * std::pow((*px)[k], a) * std::pow((*py)[k], b);
+      const double want = std::tgamma(a + 1.0) * std::tgamma(b + 1.0) / std::tgamma(a + b + 3.0);
+      if (std::fabs(sum - want) > 1e-15) throw std::runtime_error("Stroud rule check failed");
+    }
+}
+
+// ---------------------------------------------------------------- cubic geometry (Sec. 3)
+// The piecewise cubic surface: each cell's map is the cubic Lagrange
+// interpolant, in barycentric coordinates (l0, l1, l2) = (1 - x - y, x, y),
+// of ten nodes: the vertices, the points (2/3, 1/3) of each edge and the
+// centroid of the flat triangle, each projected radially onto the sphere.
+// Basis: vertex i  l_i (3 l_i - 1)(3 l_i - 2) / 2,
+//        edge (i,j) 9/2 l_i l_j (3 l_i - 1)   (the node with l_i = 2/3, l_j = 1/3),
+//        centroid  27 l0 l1 l2.
+namespace {
+
+struct P3Nodes {
+  double X[10][3];
+};
+
+const int kP3Pair[6][2] = {{0, 1}, {1, 0}, {1, 2}, {2, 1}, {2, 0}, {0, 2}};
+
+void p3_nodes(const Mesh& m, int64_t c, double radius, P3Nodes* n) {
+  const double* v[3] = {&m.verts[3 * m.cells[3 * c + 0]], &m.verts[3 * m.cells[3 * c + 1]],
+                        &m.verts[3 * m.cells[3 * c + 2]]};
+  for (int k = 0; k < 10; ++k) {
+    double lam[3] = {0.0, 0.0, 0.0};
+    if (k < 3) lam[k] = 1.0;
+    else if (k < 9) { lam[kP3Pair[k - 3][0]] = 2.0 / 3.0; lam[kP3Pair[k - 3][1]] = 1.0 / 3.0; }
+    else lam[0] = lam[1] = lam[2] = 1.0 / 3.0;
+    double p[3];
+    for (int d = 0; d < 3; ++d) p[d] = lam[0] * v[0][d] + lam[1] * v[1][d] + lam[2] * v[2][d];
+    if (k < 3) {
+      for (int d = 0; d < 3; ++d) n->X[k][d] = v[k][d];
+    } else {
+      const double s = radius / std::sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+      for (int d = 0; d < 3; ++d) n->X[k][d] = p[d] * s;
+    }
+  }
+}
+
+// Value, lambda-gradient and lambda-Hessian of cubic basis function k.
+void p3_basis(int k, const double l[3], double* N, double dN[3], double d2N[3][3]) {
+  for (int a = 0; a < 3; ++a) {
+    dN[a] = 0.0;
+    for (int b = 0; b < 3; ++b) d2N[a][b] = 0.0;
+  }
+  if (k < 3) {
+    const double t = l[k];
+    *N = 0.5 * t * (3.0 * t - 1.0) * (3.0 * t - 2.0);
+    dN[k] = 0.5 * (27.0 * t * t - 18.0 * t + 2.0);
+    d2N[k][k] = 27.0 * t - 9.0;
+  } else if (k < 9) {
+    const int i = kP3Pair[k - 3][0], j = kP3Pair[k - 3][1];
+    *N = 4.5 * l[i] * l[j] * (3.0 * l[i] - 1.0);
+    dN[i] = 4.5 * l[j] * (6.0 * l[i] - 1.0);
+    dN[j] = 4.5 * l[i] * (3.0 * l[i] - 1.0);
+    d2N[i][i] = 27.0 * l[j];
+    d2N[i][j] = d2N[j][i] = 4.5 * (6.0 * l[i] - 1.0);
+  } else {
+    *N = 27.0 * l[0] * l[1] * l[2];
+    dN[0] = 27.0 * l[1] * l[2];
+    dN[1] = 27.0 * l[0] * l[2];
+    dN[2] = 27.0 * l[0] * l[1];
+    d2N[0][1] = d2N[1][0] = 27.0 * l[2];
+    d2N[0][2] = d2N[2][0] = 27.0 * l[1];
+    d2N[1][2] = d2N[2][1] = 27.0 * l[0];
+  }
+}
+
+void cross3(const double a[3], const double b[3], double out[3]) {
+  out[0] = a[1] * b[2] - a[2] * b[1];
+  out[1] = a[2] * b[0] - a[0] * b[2];
+  out[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+void p3_eval(const P3Nodes& n, double x, double y, PointGeometry* g) {
+  const double l[3] = {1.0 - x - y, x, y};
+  const double dl[2][3] = {{-1.0, 1.0, 0.0}, {-1.0, 0.0, 1.0}};  // d lambda / d xi_a
+  double H[2][2][3] = {};
+  for (int d = 0; d < 3; ++d) { g->x[d] = 0.0; g->J[d][0] = g->J[d][1] = 0.0; }
+  for (int k = 0; k < 10; ++k) {
+    double N, dN[3], d2N[3][3];
+    p3_basis(k, l, &N, dN, d2N);
+    double da[2], dab[2][2];
+    for (int a = 0; a < 2; ++a) {
+      da[a] = dN[0] * dl[a][0] + dN[1] * dl[a][1] + dN[2] * dl[a][2];
+      for (int b = 0; b < 2; ++b) {
+        double t = 0.0;
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) t += d2N[i][j] * dl[a][i] * dl[b][j];
+        dab[a][b] = t;
+      }
+    }
+    for (int d = 0; d < 3; ++d) {
+      g->x[d] += N * n.X[k][d];
+      for (int a = 0; a < 2; ++a) {
+        g->J[d][a] += da[a] * n.X[k][d];
+        for (int b = 0; b < 2; ++b) H[a][b][d] += dab[a][b] * n.X[k][d];
+      }
+    }
+  }
+  const double J0[3] = {g->J[0][0], g->J[1][0], g->J[2][0]};
+  const double J1[3] = {g->J[0][1], g->J[1][1], g->J[2][1]};
+  double cr[3];
+  cross3(J0, J1, cr);
+  g->det = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+  g->G00 = J0[0] * J0[0] + J0[1] * J0[1] + J0[2] * J0[2];
+  g->G01 = J0[0] * J1[0] + J0[1] * J1[1] + J0[2] * J1[2];
+  g->G11 = J1[0] * J1[0] + J1[1] * J1[1] + J1[2] * J1[2];
+  // d det / d xi_a = k . (d_a J0 x J1 + J0 x d_a J1),  d_a J_b = H[a][b]
+  for (int a = 0; a < 2; ++a) {
+    double u[3], v[3];
+    cross3(H[a][0], J1, u);
+    cross3(J0, H[a][1], v);
+    g->ddet[a] = (cr[0] * (u[0] + v[0]) + cr[1] * (u[1] + v[1]) + cr[2] * (u[2] + v[2])) / g->det;
+  }
+}
+
+}  // namespace
+
+void p3_geometry(const Mesh& m, int64_t c, double x, double y, PointGeometry* g) {
+  P3Nodes n;
+  p3_nodes(m, c, m.radius, &n);
+  p3_eval(n, x, y, g);
+}
+
+namespace {
+
 // Collapsed Gauss-Legendre rule on the reference triangle:
 // x = s, y = t (1 - s), weight w_s w_t (1 - s); exact to degree 2n - 2.
 void triangle_gl(int n, std::vector<double>* px, std::vector<double>* py, std::vector<double>* pw) {
@@ -369,9 +565,10 @@ void RefElement::eval_grad(double x, double y, double grad[12][2][2]) const {
 // D_ij = int phi_i div psi_j is the same on every cell.  Signs map the cell's
 // counter-clockwise edge DOFs to the global ones: (-1)^(j+1) for moment j on an
 // edge the cell runs high -> low.
-void build_cell_data(const Mesh& m, const RefElement& el, double omega, HostCellData* out,
-                     ConstTables* tab) {
+void build_cell_data(const Mesh& m, const RefElement& el, double omega, int geometry_degree, HostCellData* out,
+                     ConstTables* tab, TablesP3<double>* tab3) {
   const int64_t F = m.F(), E = m.E();
+  const bool cubic = geometry_degree == 3;
   const int64_t n_u = 3 * E + 3 * F;
   std::vector<double> qx, qy, qw;
   triangle_gl(4, &qx, &qy, &qw);
@@ -411,6 +608,22 @@ void build_cell_data(const Mesh& m, const RefElement& el, double omega, HostCell
   out->det.assign(F, 0.0);
   out->G.assign(3 * F, 0.0);
   std::vector<double> diag(n_u, 0.0);
+  // cubic surface: the 5 x 5 Stroud rule and the reference data at its points
+  std::vector<double> sx, sy, sw, spsi, sphi;
+  if (cubic) {
+    stroud_rule(5, &sx, &sy, &sw);
+    spsi.resize(kCellQ3 * 24);
+    sphi.resize(kCellQ3 * 3);
+    for (int q = 0; q < kCellQ3; ++q) {
+      el.eval(sx[q], sy[q], reinterpret_cast<double(*)[2]>(&spsi[q * 24]));
+      sphi[q * 3 + 0] = 1.0 - sx[q] - sy[q];
+      sphi[q * 3 + 1] = sx[q];
+      sphi[q * 3 + 2] = sy[q];
+    }
+    out->M2e.assign(6 * F, 0.0);
+    out->M2i.assign(6 * F, 0.0);
+    out->geo_c.assign((size_t)6 * kCellQ3 * F, 0.0);
+  }
   for (int64_t c = 0; c < F; ++c) {
     const double* a = &m.verts[3 * m.cells[3 * c + 0]];
     const double* b = &m.verts[3 * m.cells[3 * c + 1]];
@@ -422,7 +635,7 @@ void build_cell_data(const Mesh& m, const RefElement& el, double omega, HostCell
     double G00 = J0[0] * J0[0] + J0[1] * J0[1] + J0[2] * J0[2];
     double G01 = J0[0] * J1[0] + J0[1] * J1[1] + J0[2] * J1[2];
     double G11 = J1[0] * J1[0] + J1[1] * J1[1] + J1[2] * J1[2];
-    out->det[c] = det;
+    out->det[c] = det;  // the flat triangle's (cell-size features on either surface)
     out->G[0 * F + c] = G00;
     out->G[1 * F + c] = G01;
     out->G[2 * F + c] = G11;
@@ -435,24 +648,73 @@ void build_cell_data(const Mesh& m, const RefElement& el, double omega, HostCell
         dof[3 * i + j] = 3 * m.cell_edges[3 * c + i] + j;
       }
     for (int j = 0; j < 3; ++j) { sgn[9 + j] = 1.0; dof[9 + j] = (int)(3 * E + 3 * c + j); }
-    double fz[64];
-    for (int q = 0; q < Q; ++q) {
-      double z = a[2] + J0[2] * qx[q] + J1[2] * qy[q];
-      fz[q] = 2.0 * omega * z / m.radius;
+    double m1[12][12], cc[12][12];  // unsigned element matrices (upper triangles used)
+    if (cubic) {
+      // M1_ij = sum_q w psi_i . G psi_j / det,  C_ij = sum_q w f cross2(psi_j, psi_i),
+      // M2_kl = sum_q w det phi_k phi_l, with J, det, G and f = 2 Omega z / R at each point
+      P3Nodes nodes;
+      p3_nodes(m, c, m.radius, &nodes);
+      double m2[3][3] = {};
+      for (int i = 0; i < 12; ++i)
+        for (int j = 0; j < 12; ++j) m1[i][j] = cc[i][j] = 0.0;
+      for (int q = 0; q < kCellQ3; ++q) {
+        PointGeometry g;
+        p3_eval(nodes, sx[q], sy[q], &g);
+        const double f = 2.0 * omega * g.x[2] / m.radius;
+        const double wq = sw[q];
+        const double* ps = &spsi[q * 24];
+        for (int i = 0; i < 12; ++i)
+          for (int j = i; j < 12; ++j) {
+            const double* pi = ps + 2 * i;
+            const double* pj = ps + 2 * j;
+            m1[i][j] += wq * (pi[0] * (g.G00 * pj[0] + g.G01 * pj[1]) + pi[1] * (g.G01 * pj[0] + g.G11 * pj[1])) / g.det;
+            cc[i][j] += wq * f * (pj[0] * pi[1] - pj[1] * pi[0]);
+          }
+        for (int k = 0; k < 3; ++k)
+          for (int l = 0; l < 3; ++l) m2[k][l] += wq * g.det * sphi[q * 3 + k] * sphi[q * 3 + l];
+        double* gc = &out->geo_c[0];
+        const int64_t QF = (int64_t)kCellQ3 * F;
+        gc[0 * QF + q * F + c] = g.G00;
+        gc[1 * QF + q * F + c] = g.G01;
+        gc[2 * QF + q * F + c] = g.G11;
+        gc[3 * QF + q * F + c] = wq / (g.det * g.det);
+        gc[4 * QF + q * F + c] = g.ddet[0] / g.det;
+        gc[5 * QF + q * F + c] = g.ddet[1] / g.det;
+      }
+      double inv[9], mm[9];
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) mm[3 * k + l] = 0.5 * (m2[k][l] + m2[l][k]);
+      if (!invert(3, mm, inv)) throw std::runtime_error("singular DG1 element mass");
+      const int pk[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+      for (int k = 0; k < 6; ++k) {
+        out->M2e[(int64_t)k * F + c] = mm[3 * pk[k][0] + pk[k][1]];
+        out->M2i[(int64_t)k * F + c] = 0.5 * (inv[3 * pk[k][0] + pk[k][1]] + inv[3 * pk[k][1] + pk[k][0]]);
+      }
+    } else {
+      double fz[64];
+      for (int q = 0; q < Q; ++q) {
+        double z = a[2] + J0[2] * qx[q] + J1[2] * qy[q];
+        fz[q] = 2.0 * omega * z / m.radius;
+      }
+      for (int i = 0; i < 12; ++i)
+        for (int j = i; j < 12; ++j) {
+          double sm = 0, sc = 0;
+          for (int q = 0; q < Q; ++q) {
+            const double* pi = &psi[q * 24 + 2 * i];
+            const double* pj = &psi[q * 24 + 2 * j];
+            sm += qw[q] * (pi[0] * (G00 * pj[0] + G01 * pj[1]) + pi[1] * (G01 * pj[0] + G11 * pj[1]));
+            sc += qw[q] * fz[q] * (pj[0] * pi[1] - pj[1] * pi[0]);
+          }
+          m1[i][j] = sm / det;
+          cc[i][j] = sc;
+        }
     }
     for (int i = 0; i < 12; ++i)
       for (int j = i; j < 12; ++j) {
-        double sm = 0, sc = 0;
-        for (int q = 0; q < Q; ++q) {
-          const double* pi = &psi[q * 24 + 2 * i];
-          const double* pj = &psi[q * 24 + 2 * j];
-          sm += qw[q] * (pi[0] * (G00 * pj[0] + G01 * pj[1]) + pi[1] * (G01 * pj[0] + G11 * pj[1]));
-          sc += qw[q] * fz[q] * (pj[0] * pi[1] - pj[1] * pi[0]);
-        }
         double ss = sgn[i] * sgn[j];
-        out->M1[(int64_t)packed_sym(i, j) * F + c] = ss * sm / det;
-        if (j > i) out->C[(int64_t)packed_asym(i, j) * F + c] = ss * sc;
-        if (i == j) diag[dof[i]] += sm / det;
+        out->M1[(int64_t)packed_sym(i, j) * F + c] = ss * m1[i][j];
+        if (j > i) out->C[(int64_t)packed_asym(i, j) * F + c] = ss * cc[i][j];
+        if (i == j) diag[dof[i]] += m1[i][j];
       }
   }
   out->dinv.resize(n_u);
@@ -544,6 +806,52 @@ void build_cell_data(const Mesh& m, const RefElement& el, double omega, HostCell
       double fp = std::tgamma(p + 1.0), fq = std::tgamma(q + 1.0), fpq = std::tgamma(p + q + 3.0);
       if (std::fabs(s - fp * fq / fpq) > 1e-15) throw std::runtime_error("degree-5 rule check failed");
     }
+
+  if (!cubic) return;
+  // cubic surface: the kernels' rules (the Stroud cell rule, 5-point facets),
+  // and each edge's two cells' metric at every facet point, each at its own
+  // parameter of the point (tau on the plus side, 1 - tau on the minus side)
+  for (int q = 0; q < kCellQ3; ++q) {
+    tab3->cq_w[q] = sw[q];
+    el.eval(sx[q], sy[q], tab3->cq_psi[q]);
+    el.eval_grad(sx[q], sy[q], tab3->cq_dpsi[q]);
+    tab3->cq_phi[q][0] = 1.0 - sx[q] - sy[q];
+    tab3->cq_phi[q][1] = sx[q];
+    tab3->cq_phi[q][2] = sy[q];
+  }
+  double gx[kFacetQ3], gw[kFacetQ3];
+  gauss_legendre01(kFacetQ3, gx, gw);
+  for (int p = 0; p < kFacetQ3; ++p) tab3->fq_w[p] = gw[p];
+  for (int side = 0; side < 2; ++side)
+    for (int i = 0; i < 3; ++i)
+      for (int p = 0; p < kFacetQ3; ++p) {
+        double t = side == 0 ? gx[p] : 1.0 - gx[p];
+        double x = kEdgeStart[i][0] + t * kEdgeDir[i][0];
+        double y = kEdgeStart[i][1] + t * kEdgeDir[i][1];
+        el.eval(x, y, tab3->fq_psi[side][i][p]);
+        tab3->fq_phi[side][i][p][0] = 1.0 - x - y;
+        tab3->fq_phi[side][i][p][1] = x;
+        tab3->fq_phi[side][i][p][2] = y;
+      }
+  for (int i = 0; i < 3; ++i) { tab3->edge_dir[i][0] = kEdgeDir[i][0]; tab3->edge_dir[i][1] = kEdgeDir[i][1]; }
+  out->geo_f.assign((size_t)8 * kFacetQ3 * E, 0.0);
+  const int64_t PE = (int64_t)kFacetQ3 * E;
+  for (int64_t e = 0; e < E; ++e) {
+    const int64_t cell[2] = {m.edge_plus[e], m.edge_minus[e]};
+    const int loc[2] = {m.edge_lpos[e] & 3, m.edge_lpos[e] >> 2};
+    for (int side = 0; side < 2; ++side) {
+      P3Nodes nodes;
+      p3_nodes(m, cell[side], m.radius, &nodes);
+      for (int p = 0; p < kFacetQ3; ++p) {
+        const double t = side == 0 ? gx[p] : 1.0 - gx[p];
+        PointGeometry g;
+        p3_eval(nodes, kEdgeStart[loc[side]][0] + t * kEdgeDir[loc[side]][0],
+                kEdgeStart[loc[side]][1] + t * kEdgeDir[loc[side]][1], &g);
+        const double v[4] = {g.G00, g.G01, g.G11, g.det};
+        for (int k = 0; k < 4; ++k) out->geo_f[(4 * side + k) * PE + p * E + e] = v[k];
+      }
+    }
+  }
 }
 
 // ---------------------------------------------------------------- Chebyshev coefficients

@@ -63,6 +63,7 @@ class Params(ctypes.Structure):
         ("solver", ctypes.c_int),
         ("precision", ctypes.c_int),
         ("sd_part_cells", ctypes.c_int),
+        ("geometry_degree", ctypes.c_int),
     ]
 
 

@@ -8,13 +8,17 @@
 //                         then one coefficient per line (count 0: refused)
 //   shifts T M RULE       the Riemann-sum shifts and weights (Sec. 2.2):
 //                         prints the status, then "s w" per line
-//   cells R RADIUS OMEGA PREFIX
+//   cells R RADIUS OMEGA PREFIX [DEGREE]
 //                         the per-cell element matrices of M1 and C (Sec. 2.5)
 //                         as the kernels store them (signed, packed), expanded
 //                         and placed at their global DOFs: writes
 //                         PREFIX.{m1,c}.{row,col} (int64) and .val (float64)
 //                         triplets, PREFIX.det and PREFIX.g (float64 [3][F]:
-//                         G00, G01, G11 of G = J^T J); prints "n_u F"
+//                         G00, G01, G11 of G = J^T J); prints "n_u F".  With
+//                         DEGREE 3 (the piecewise cubic surface of Sec. 3) also
+//                         PREFIX.m2e, .m2i (float64 [6][F]), .geoc (float64
+//                         [6][25][F]) and .geof (float64 [8][5][E])
+//   stroud N              the N x N Stroud conical product rule: "x y w" lines
 //   tables                the reference tables the kernels read from constant
 //                         memory: prints D (3 x 12), then M2 and M2^{-1} (3 x 3)
 //                         of the reference cell, one row per line
@@ -92,14 +96,22 @@ int main(int argc, char** argv) {
     for (size_t i = 0; i < s.size(); ++i) std::printf("%.17g %.17g\n", s[i], w[i]);
     return 0;
   }
-  if (cmd == "cells" && argc == 6) {
+  if (cmd == "stroud" && argc == 3) {
+    std::vector<double> x, y, w;
+    pavg::stroud_rule(std::atoi(argv[2]), &x, &y, &w);
+    for (size_t k = 0; k < w.size(); ++k) std::printf("%.17g %.17g %.17g\n", x[k], y[k], w[k]);
+    return 0;
+  }
+  if (cmd == "cells" && (argc == 6 || argc == 7)) {
     pavg::Mesh m;
     pavg::build_mesh(std::atoi(argv[2]), std::strtod(argv[3], nullptr), &m);
     pavg::RefElement el;
     pavg::build_reference_element(&el);
     pavg::HostCellData cd;
     pavg::ConstTables tab;
-    pavg::build_cell_data(m, el, std::strtod(argv[4], nullptr), &cd, &tab);
+    pavg::TablesP3<double> tab3;
+    const int degree = argc == 7 ? std::atoi(argv[6]) : 1;
+    pavg::build_cell_data(m, el, std::strtod(argv[4], nullptr), degree, &cd, &tab, &tab3);
     const int64_t F = m.F();
     std::vector<int64_t> r1, c1, rc, cc;
     std::vector<double> v1, vc;
@@ -126,6 +138,12 @@ int main(int argc, char** argv) {
         !write_all(p + ".c.col", cc.data(), 8 * cc.size()) || !write_all(p + ".c.val", vc.data(), 8 * vc.size()) ||
         !write_all(p + ".det", cd.det.data(), 8 * cd.det.size()) || !write_all(p + ".g", cd.G.data(), 8 * cd.G.size()))
       return 3;
+    if (degree == 3 &&
+        (!write_all(p + ".m2e", cd.M2e.data(), 8 * cd.M2e.size()) ||
+         !write_all(p + ".m2i", cd.M2i.data(), 8 * cd.M2i.size()) ||
+         !write_all(p + ".geoc", cd.geo_c.data(), 8 * cd.geo_c.size()) ||
+         !write_all(p + ".geof", cd.geo_f.data(), 8 * cd.geo_f.size())))
+      return 3;
     std::printf("%lld %lld\n", (long long)(3 * m.E() + 3 * F), (long long)F);
     return 0;
   }
@@ -136,7 +154,7 @@ int main(int argc, char** argv) {
     pavg::build_reference_element(&el);
     pavg::HostCellData cd;
     pavg::ConstTables tab;
-    pavg::build_cell_data(m, el, 0.0, &cd, &tab);
+    pavg::build_cell_data(m, el, 0.0, 1, &cd, &tab, nullptr);
     for (int i = 0; i < 3; ++i) {
       for (int j = 0; j < 12; ++j) std::printf("%.17g ", tab.D[i][j]);
       std::printf("\n");
@@ -153,7 +171,7 @@ int main(int argc, char** argv) {
     pavg::build_reference_element(&el);
     pavg::HostCellData cd;
     pavg::ConstTables tab;
-    pavg::build_cell_data(m, el, 7.292e-5, &cd, &tab);
+    pavg::build_cell_data(m, el, 7.292e-5, 1, &cd, &tab, nullptr);
     const std::string p = argv[4];
     if (!write_all(p + ".tri", cd.tri.data(), 4 * cd.tri.size()) ||
         !write_all(p + ".pinv", cd.Pinv.data(), 4 * cd.Pinv.size()) ||
@@ -174,7 +192,7 @@ int main(int argc, char** argv) {
     pavg::build_reference_element(&el);
     pavg::HostCellData cd;
     pavg::ConstTables tab;
-    pavg::build_cell_data(m, el, 7.292e-5, &cd, &tab);
+    pavg::build_cell_data(m, el, 7.292e-5, 1, &cd, &tab, nullptr);
     if (cmd == "spectrum") {
       double lo = 0, hi = 0;
       pavg::sd_spectrum(m.F(), m.E(), cd.M1, cd.tri, cd.Pinv, std::atoi(argv[4]), &lo, &hi);
@@ -231,7 +249,7 @@ int main(int argc, char** argv) {
     pavg::build_reference_element(&el);
     pavg::HostCellData cd;
     pavg::ConstTables tab;
-    pavg::build_cell_data(m, el, 0.0, &cd, &tab);
+    pavg::build_cell_data(m, el, 0.0, 1, &cd, &tab, nullptr);
     for (int q = 0; q < pavg::kCellQ; ++q)
       std::printf("%.17g %.17g %.17g %.17g\n", tab.cq_w[q], tab.cq_phi[q][0], tab.cq_phi[q][1], tab.cq_phi[q][2]);
     return 0;
@@ -243,7 +261,7 @@ int main(int argc, char** argv) {
     pavg::build_reference_element(&el);
     pavg::HostCellData cd;
     pavg::ConstTables tab;
-    pavg::build_cell_data(m, el, 0.0, &cd, &tab);
+    pavg::build_cell_data(m, el, 0.0, 1, &cd, &tab, nullptr);
     auto line = [](const double* p, size_t n) {
       for (size_t i = 0; i < n; ++i) std::printf("%.17g ", p[i]);
       std::printf("\n");

@@ -116,6 +116,75 @@ def test_element_matrices_assemble_to_the_oracles(harness, tmp_path, r):
     assert np.abs(asm.G[:, 0, 1] - asm.G[:, 1, 0]).max() == 0.0
 
 
+def test_stroud_rule_matches_the_oracle(harness):
+    """The library's 5 x 5 Stroud rule (Gauss-Jacobi nodes by bracketing and
+    bisection) against the oracle's (scipy's Gauss-Jacobi), point by point in
+    the same order."""
+    from oracle.quadrature import triangle_rule
+    got = np.array([list(map(float, line.split())) for line in run(harness, "stroud", 5)])
+    xq, wq = triangle_rule(5)
+    assert got.shape == (25, 3)
+    assert np.abs(got[:, :2] - xq).max() <= 2e-16 and np.abs(got[:, 2] - wq).max() <= 1e-16
+
+
+@pytest.mark.parametrize("r", [0, 1, 2, 3])
+def test_cubic_cell_data_match_oracle(harness, tmp_path, r):
+    """Element matrices and per-point metric of the piecewise cubic surface
+    (Sec. 3): the library's cubic map (closed-form barycentric basis) against
+    the oracle's (inverted Vandermonde over monomials)."""
+    import scipy.sparse as sp
+
+    from oracle.assembly import Assembly
+    from oracle.elements import EDGE_DIR, EDGE_START
+    from oracle.quadrature import gauss_legendre_01, triangle_rule
+    omega = 7.292e-5
+    n, F = map(int, run(harness, "cells", r, repr(R), repr(omega), tmp_path / "c", 3)[0].split())
+
+    def load(k):
+        rows = np.fromfile(tmp_path / f"c.{k}.row", dtype=np.int64)
+        cols = np.fromfile(tmp_path / f"c.{k}.col", dtype=np.int64)
+        vals = np.fromfile(tmp_path / f"c.{k}.val", dtype=np.float64)
+        return sp.coo_matrix((vals, (rows, cols)), shape=(n, n)).tocsr()
+
+    mesh = build_mesh(r, R)
+    asm = Assembly(mesh, omega, R, geometry_degree=3)
+    M1, C, _, M2 = asm.global_matrices()
+    assert abs(load("m1") - M1).max() <= 1e-13 * abs(M1).max()
+    assert abs(load("c") - C).max() <= 1e-12 * abs(C).max()
+    pk = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    m2e = np.fromfile(tmp_path / "c.m2e", dtype=np.float64).reshape(6, F)
+    m2i = np.fromfile(tmp_path / "c.m2i", dtype=np.float64).reshape(6, F)
+    want = np.stack([asm.M2_e[:, a, b] for a, b in pk])
+    assert np.abs(m2e - want).max() <= 1e-13 * np.abs(want).max()
+    inv = np.linalg.inv(asm.M2_e)
+    wanti = np.stack([inv[:, a, b] for a, b in pk])
+    assert np.abs(m2i - wanti).max() <= 1e-11 * np.abs(wanti).max()
+    # per cell point: G, w / det^2, grad det / det at the Stroud points
+    xq, wq = triangle_rule(5)
+    g = asm.maps.geometry(xq)
+    geoc = np.fromfile(tmp_path / "c.geoc", dtype=np.float64).reshape(6, 25, F)
+    wantc = np.stack([g["G"][..., 0, 0], g["G"][..., 0, 1], g["G"][..., 1, 1], wq[None, :] / g["det"] ** 2,
+                      g["grad_det"][..., 0] / g["det"], g["grad_det"][..., 1] / g["det"]]).transpose(0, 2, 1)
+    for k in range(4):
+        assert np.abs(geoc[k] - wantc[k]).max() <= 1e-12 * np.abs(wantc[k]).max(), k
+    # d ln det / d xi: a small difference of second-derivative products (the
+    # cell's curvature); both sides round it at the scale of the metric's
+    # unit-size reference terms
+    for k in (4, 5):
+        assert np.abs(geoc[k] - wantc[k]).max() <= 1e-12, k
+    # per facet point: each side's G and det at its own parameter
+    E = mesh.n_edges
+    tau, _ = gauss_legendre_01(5)
+    geof = np.fromfile(tmp_path / "c.geof", dtype=np.float64).reshape(8, 5, E)
+    for side, t in ((0, tau), (1, 1.0 - tau)):
+        cells, loc = mesh.edge_cells[:, side], mesh.edge_local[:, side]
+        gs = [asm.maps.geometry(EDGE_START[i][None, :] + t[:, None] * EDGE_DIR[i][None, :]) for i in range(3)]
+        G = np.stack([x["G"] for x in gs])[loc, cells]           # (E, 5, 2, 2)
+        det = np.stack([x["det"] for x in gs])[loc, cells]
+        for k, v in enumerate([G[..., 0, 0], G[..., 0, 1], G[..., 1, 1], det]):
+            assert np.abs(geof[4 * side + k] - v.T).max() <= 1e-12 * np.abs(v).max(), (side, k)
+
+
 def test_reference_tables_match_the_oracle(harness):
     """The constant-memory tables the kernels scale per cell: D-hat (the
     oracle's D_e with its orientation signs divided out, the same for every
