@@ -541,6 +541,53 @@ def _marching_leg(model, Ud):
                                  "shared basis needs fewer solves at every (T, M)"}
 
 
+def _cubic_leg(pavg, U_flat, out_flat):
+    """The piecewise cubic surface of Sec. 3 (geometry_degree = 3) at the
+    benchmark configuration: evaluations per second of the same averaged_rhs
+    (its own lambda_max, estimated by the library), the relative difference
+    from the flat-cell result (the geometry's effect on the average), and the
+    Chebyshev degrees of Table 1 (g = 9.8, H = 5960 m; windows 15, 30, 60
+    min) on both surfaces from each surface's estimated lambda_max."""
+    import torch
+    res = {}
+    m = pavg.Model(6, lambda_max=0.0, geometry_degree=3)
+    nu = m.n_u
+    o = torch.empty_like(U_flat)
+    m.averaged_rhs(3600.0, 64, U_flat, o)
+    m.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        m.averaged_rhs(3600.0, 64, U_flat, o)
+    e1.record()
+    torch.cuda.synchronize()
+    m.sync()
+    ms = e0.elapsed_time(e1) / reps
+    res.update({"workload": "refinement 6, M = 64, T = 1 h, cubic cells (5x5 cell rule, 5-point facets)",
+                "value": 1e3 / ms, "unit": "evals/s", "ms_per_eval": ms, "lambda_max": m.lambda_max,
+                "K_max": m.stats()["last_degree"],
+                "rel_diff_vs_flat_u": float((o[:nu] - out_flat[:nu]).norm() / out_flat[:nu].norm()),
+                "rel_diff_vs_flat_eta": float((o[nu:] - out_flat[nu:]).norm() / out_flat[nu:].norm())})
+    m.close()
+    table = []
+    for r in (3, 4, 5):
+        for deg in (1, 3):
+            mm = pavg.Model(r, lambda_max=0.0, g=9.8, H=5960.0, geometry_degree=deg)
+            z = torch.zeros(mm.n, dtype=torch.float64, device="cuda")
+            ks = []
+            for t in (900.0, 1800.0, 3600.0):  # Delta s = 15, 30, 60 min
+                mm.expL(t, z)
+                ks.append(mm.stats()["last_degree"])
+            mm.sync()
+            table.append({"refinement": r, "geometry_degree": deg, "lambda_max": mm.lambda_max, "K": ks})
+            mm.close()
+    res["table1"] = table
+    res["table1_printed"] = {"3": [10, 15, 24], "4": [16, 25, 41], "5": [26, 42, 73]}
+    return res
+
+
 # ----------------------------------------------------------------------------- CPU oracle leg
 # The oracle's sample at the benchmark configuration: the complete literal
 # terms w_m e^{-s_m L} N(e^{s_m L} U) of the ORACLE_GROUP central shifts
@@ -870,6 +917,7 @@ def run_pavg(args):
     groups = _shift_groups_leg(model, cfg, Ud, ms / args.steps, out) if "groups" in legs else None
     tc5 = _tc5_leg(pavg, args.days) if "tc5" in legs else None
     marching = _marching_leg(model, Ud) if "marching" in legs else None
+    cubic = _cubic_leg(pavg, Ud, out) if "cubic" in legs else None
 
     # parity against the oracle (computed by the spawned leg): the small
     # configuration in full, and the central shift group at the benchmark size
@@ -951,7 +999,7 @@ def run_pavg(args):
                     "d2h_bytes_per_step": 8 * model.n},
             "gpu_launches": st["kernel_launches"] * args.steps,
             "roofline": roof, "cpu_baseline": cpu, "parity": parity, "precision_mixed": mixed, "literal": literal, "precision_days": days, "day_r5": day_r5, "batch": batch, "surrogate": surrogate,
-            "shift_groups": groups, "tc5": tc5, "marching": marching,
+            "shift_groups": groups, "tc5": tc5, "marching": marching, "cubic": cubic,
             "clocks": clk,
             "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
             "alu_peaks_measured_tflops": ALU_PEAKS,
@@ -975,7 +1023,7 @@ def main():
                          "instead of the 8 central terms: a timed evaluation and whole-average parity")
     ap.add_argument("--batch-n", type=int, default=None, help="instances of the batched leg (profiling only)")
     ap.add_argument("--batch-max-r", type=int, default=None, help="largest refinement of the batched leg (profiling only)")
-    ap.add_argument("--legs", default="fp64,mixed,literal,batch,surrogate,groups,marching",
+    ap.add_argument("--legs", default="fp64,mixed,literal,batch,surrogate,groups,marching,cubic",
                     help="comma list: fp64 (always), mixed, literal, batch, surrogate, groups, marching, "
                          "precision_days, day_r5, tc5 (single GPU only)")
     ap.add_argument("--days", type=float, default=1.0, help="simulated days of the precision_days and tc5 legs")

@@ -56,10 +56,12 @@ def test_complex_recurrence_equals_real_form():
 def test_table1_refinement3():
     """Paper Table 1, refinement 3: degrees 10 / 15 / 24 for 15 / 30 / 60 min
     with lambda_max from power iteration (g = 9.8, H = 5960 as in Sec. 3).
-    Refinements 4 and 5 come out 3 and 9 terms lower at 1 h with this build's
-    flat-facet geometry: lambda_max doubles per refinement here, while the
-    printed degrees imply a factor of about 2.3 (cubic geometry, or another
-    lambda_max estimate)."""
+    Refinements 4 and 5 come out 3 and 9 terms lower at 1 h: lambda_max
+    doubles per refinement here, while the printed degrees imply a factor of
+    about 2.3.  The piecewise cubic surface of Sec. 3 does not explain it:
+    its lambda_max is within 0.2 % of the flat one at refinements 3-5
+    (0.0031019 / 0.0062327 / 0.0124868 against 0.0031056 / 0.0062346 /
+    0.0124878 s^-1) and gives the same degrees at refinements 4 and 5."""
     from tests.conftest import oracle_model
     rows = np.loadtxt(os.path.join(GOLDEN, "paper_table1.txt"), comments="#")
     m = oracle_model(3, g=9.8, H=5960.0)

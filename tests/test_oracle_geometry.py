@@ -171,3 +171,14 @@ def test_cubic_operators_keep_the_invariants(om, r):
     assert abs(s) <= 1e-12 * abs(energy_ip(U, ops.L(V)))
     assert abs(ops.mass(ops.N(U))) <= 1e-9 * np.abs(ops.N(U)[m.n_u:]).max() * 4.0 * math.pi * R * R
     assert np.linalg.eigvalsh(ops.M1.toarray()).min() > 0 and np.linalg.eigvalsh(ops.M2.toarray()).min() > 0
+
+
+def test_cubic_surface_keeps_lambda_max():
+    """The fastest gravity wave hardly notices the surface: lambda_max of L on
+    the cubic surface is within 0.2 % of the flat one (refinement 3, Table 1's
+    g = 9.8, H = 5960 m), so Table 1's degrees do not depend on it."""
+    from oracle import spectrum
+    from tests.conftest import oracle_model
+    lf = spectrum.power_iteration(oracle_model(3, g=9.8, H=5960.0).ops, iters=400)
+    lc = spectrum.power_iteration(oracle_model(3, g=9.8, H=5960.0, geometry_degree=3).ops, iters=400)
+    assert abs(lc / lf - 1.0) < 2e-3, (lc, lf)
