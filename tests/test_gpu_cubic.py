@@ -115,7 +115,8 @@ def test_flat_and_cubic_contexts_side_by_side():
     geometry's O(h^2) change of the operators."""
     gf, gc_ = gpu(3), cg(3)
     of, oc = orc(3), co(3)
-    U = state(of, eta_noise=5.0)
+    U = np.random.default_rng(33).standard_normal(of.n) * 1e6  # not balanced: every part of L is O(1)
+    U[of.n_u:] *= 1e-4
     Lf = gf.linear(dev(U)).cpu().numpy()
     Lc = gc_.linear(dev(U)).cpu().numpy()
     assert_close(of, Lf, of.L(U))
