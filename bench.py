@@ -445,7 +445,7 @@ def _shift_groups_leg(model, cfg, Ud, ms_full, full):
     return res
 
 
-def _tc5_leg(pavg, days=1.0):
+def _tc5_leg(pavg, days=1.0, geometry_degree=3):
     """Williamson's test case 5 (Sec. 3) at refinement 5: the error of the
     averaged model at `days` against the unaveraged (T = 0) Lawson RK4 at
     dt = 22.5 s, for a sweep of windows T at dt = 450, 900 and 1350 s, in the
@@ -457,7 +457,8 @@ def _tc5_leg(pavg, days=1.0):
 
     from paper_2103_07706_gb300.inputs import tc5_state
     g_, H_ = 9.8, 5960.0
-    m = pavg.Model(5, g=g_, H=H_, omega=7.292e-5, radius=6.37122e6, lambda_max=0.0)
+    m = pavg.Model(5, g=g_, H=H_, omega=7.292e-5, radius=6.37122e6, lambda_max=0.0,
+                   geometry_degree=geometry_degree)
     lam = m.lambda_max
     verts, cells = m.mesh()
     U0, b = tc5_state(verts, cells, g=g_, H=H_)
@@ -470,7 +471,8 @@ def _tc5_leg(pavg, days=1.0):
     m.sync()
     ref_s = time.time() - t0
     nref = m.norms(Ur)
-    res = {"setup": f"refinement 5 (20480 cells, flat facets), g = {g_}, H = {H_} m, u0 = 20 m/s, mountain "
+    surface = "cubic surface" if geometry_degree == 3 else "flat cells"
+    res = {"setup": f"refinement 5 (20480 cells, {surface}), g = {g_}, H = {H_} m, u0 = 20 m/s, mountain "
                     f"b0 = 2000 m at (30N, 90W); lambda_max = {lam:.5f} s^-1 (library estimate); reference: "
                     f"Lawson RK4 without averaging (T = 0) at dt = 22.5 s ({n_ref} steps, {ref_s:.0f} s)",
            "days": days, "runs": []}
@@ -915,7 +917,7 @@ def run_pavg(args):
     day_r5 = _day_r5(pavg) if "day_r5" in legs else None
     surrogate = _surrogate_leg(pavg, sur_states) if "surrogate" in legs else None
     groups = _shift_groups_leg(model, cfg, Ud, ms / args.steps, out) if "groups" in legs else None
-    tc5 = _tc5_leg(pavg, args.days) if "tc5" in legs else None
+    tc5 = _tc5_leg(pavg, args.days, args.tc5_geometry) if "tc5" in legs else None
     marching = _marching_leg(model, Ud) if "marching" in legs else None
     cubic = _cubic_leg(pavg, Ud, out) if "cubic" in legs else None
 
@@ -1027,6 +1029,8 @@ def main():
                     help="comma list: fp64 (always), mixed, literal, batch, surrogate, groups, marching, "
                          "precision_days, day_r5, tc5 (single GPU only)")
     ap.add_argument("--days", type=float, default=1.0, help="simulated days of the precision_days and tc5 legs")
+    ap.add_argument("--tc5-geometry", type=int, default=3, choices=(1, 3),
+                    help="surface of the tc5 leg: 3 the paper's piecewise cubic one, 1 flat cells")
     ap.add_argument("--refinement", type=int, default=None, help="smaller case (profiling only)")
     ap.add_argument("--M", type=int, default=None, help="number of shifts (profiling only)")
     args = ap.parse_args()
