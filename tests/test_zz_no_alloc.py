@@ -72,3 +72,37 @@ def test_noalloc_mixed_precision_within_the_solve_tolerance():
         assert eu <= 1e-4, eu
         assert ee <= 1e-13, ee   # the eta part is a cell-local 3x3 solve in FP64 on both paths
     m.close()
+
+
+def test_noalloc_inside_a_global_mode_graph_capture():
+    """The entry point's reason to exist: after one call outside capture, the
+    call can be recorded in a global-mode stream capture (which fails any
+    allocating or otherwise capture-unsafe call made meanwhile) and the
+    graph replayed on new inputs copied into the captured buffer."""
+    import torch
+
+    from paper_2103_07706_gb300 import pavg
+    m = pavg.Model(4, lambda_max=0.0057)
+    rng = np.random.default_rng(46)
+    Uin = torch.zeros(m.n, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(Uin)
+    m.linear_noalloc(Uin, out)  # first call before any capture (device address lookup)
+    m.sync()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="global"):
+        m.linear_noalloc(Uin, out)
+    for _ in range(2):
+        U = rng.standard_normal(m.n) * 1e6
+        U[m.n_u:] *= 1e-4
+        Uin.copy_(torch.from_numpy(U).cuda())
+        g.replay()
+        torch.cuda.synchronize()
+        m.sync()
+        got = out.cpu().numpy()
+        want = m.linear(Uin).cpu().numpy()
+        m.sync()
+        for sl in (slice(0, m.n_u), slice(m.n_u, m.n)):
+            err = np.linalg.norm(got[sl] - want[sl]) / np.linalg.norm(want[sl])
+            assert err <= 1e-12, err
+    del g
+    m.close()
