@@ -216,6 +216,57 @@ int get_plan(pavg_ctx* ctx, double T, int M, AvgPlan** out, int m0, int m1) {
   }
   AvgPlan pl;
   pl.T = T; pl.M = M; pl.K = K; pl.M_rule = Mrule; pl.m0 = m0;
+  const int tile = combine_tile();
+  // Pairs: every shift s > 0 with a partner -s of the same coefficients and
+  // weight (the midpoint rule with even M, and symmetric groups of it); the
+  // contractions then run once per pair (E +/- O).  Pairs ordered by
+  // decreasing degree, rows 2p (s > 0) and 2p + 1 (s < 0) of U_m and r_m.
+  {
+    std::vector<int> pos, used(M, 0);
+    std::vector<std::pair<int, int>> pairs;
+    for (int m = 0; m < M; ++m)
+      if (s[m] > 0.0) pos.push_back(m);
+    bool ok = 2 * (int)pos.size() == M;
+    for (int a : pos) {
+      if (!ok) break;
+      int b = -1;
+      for (int m = 0; m < M && b < 0; ++m)
+        if (!used[m] && s[m] == -s[a] && w[m] == w[a] && cs[m] == cs[a]) b = m;
+      if (b < 0) ok = false;
+      else { used[b] = 1; pairs.emplace_back(a, b); }
+    }
+    if (ok && !pairs.empty()) {
+      std::stable_sort(pairs.begin(), pairs.end(),
+                       [&](const std::pair<int, int>& x, const std::pair<int, int>& y) {
+                         return cs[x.first].size() > cs[y.first].size();
+                       });
+      const int P = (int)pairs.size();
+      std::vector<double> Ap((size_t)P * (K + 1), 0.0), Bp((size_t)(K + 1) * P, 0.0);
+      for (int p = 0; p < P; ++p) {
+        const int m = pairs[p].first;
+        for (int k = 0; k < (int)cs[m].size(); ++k) {
+          Ap[(size_t)p * (K + 1) + k] = cs[m][k];
+          Bp[(size_t)k * P + p] = w[m] * cs[m][k];
+        }
+      }
+      std::vector<int> la((P + tile - 1) / tile), lb((K + 1 + tile - 1) / tile);
+      for (size_t j = 0; j < la.size(); ++j) la[j] = (int)cs[pairs[j * tile].first].size();
+      for (size_t j = 0; j < lb.size(); ++j) {
+        int cnt = 0;
+        for (int p = 0; p < P; ++p) cnt += (int)cs[pairs[p].first].size() > (int)(j * tile) ? 1 : 0;
+        lb[j] = cnt;
+      }
+      if (upload(&pl.dAp, Ap) != cudaSuccess || upload(&pl.dBp, Bp) != cudaSuccess ||
+          upload(&pl.dlimAp, la) != cudaSuccess || upload(&pl.dlimBp, lb) != cudaSuccess) {
+        cudaFree(pl.dAp); cudaFree(pl.dBp); cudaFree(pl.dlimAp); cudaFree(pl.dlimBp);
+        return set_err(ctx, PAVG_ERR_NOMEM, "plan upload failed");
+      }
+      pl.P = P;
+      auto res = ctx->plans.emplace(key, pl);
+      *out = &res.first->second;
+      return PAVG_OK;
+    }
+  }
   // Shifts ordered by decreasing degree K_m: each 8-row tile of the forward
   // table then uses a prefix of the k range, and each 8-row tile of the
   // backward table a prefix of the shifts; the contractions skip the zeros.
@@ -235,7 +286,6 @@ int get_plan(pavg_ctx* ctx, double T, int M, AvgPlan** out, int m0, int m1) {
       bw *= -sg;
     }
   }
-  const int tile = combine_tile();
   std::vector<int> limA((M + tile - 1) / tile), limB((K + 1 + tile - 1) / tile);
   for (size_t j = 0; j < limA.size(); ++j) limA[j] = (int)cs[ord[j * tile]].size();
   for (size_t j = 0; j < limB.size(); ++j) {
@@ -257,12 +307,14 @@ int enq_avg_shifts(pavg_ctx* ctx, const AvgPlan& pl, cudaStream_t st) {
   const int K = pl.K, M = pl.M;
   double* Q = ctx->Q;
   const bool fp32 = ctx->p.precision == PAVG_PRECISION_MIXED;
-  KL(launch_combine(pl.dA, M, K + 1, pl.dlimA, Q, n, ctx->Um, n, n, st, fp32));
+  if (pl.P > 0) KL(launch_combine_pairs_fwd(pl.dAp, pl.P, K + 1, pl.dlimAp, Q, n, ctx->Um, n, n, st, fp32));
+  else KL(launch_combine(pl.dA, M, K + 1, pl.dlimA, Q, n, ctx->Um, n, n, st, fp32));
   CK(cudaMemset2DAsync(ctx->Rm, sizeof(double) * n, 0, sizeof(double) * 3 * m.E, M, st));
   KL(launch_nonlinear_rhs(m, ctx->Um, ctx->Rm, M, ctx->p.upwind_convention, st, fp32, ctx->facets, ctx->facet_chunk));
   // the weighted sum over shifts stays FP64 in every precision: the average
   // cancels most of the oscillating terms, so rounding here is amplified
-  KL(launch_combine(pl.dB, K + 1, M, pl.dlimB, ctx->Rm, n, Q, n, n, st));  // y_k overwrite Q_k
+  if (pl.P > 0) KL(launch_combine_pairs_bwd(pl.dBp, K + 1, pl.P, pl.dlimBp, ctx->Rm, n, Q, n, n, st));
+  else KL(launch_combine(pl.dB, K + 1, M, pl.dlimB, ctx->Rm, n, Q, n, n, st));  // y_k overwrite Q_k
   return PAVG_OK;
 }
 
@@ -514,6 +566,10 @@ void free_ctx(pavg_ctx* c) {
     cudaFree(kv.second.dlimB);
     cudaFree(kv.second.dA);
     cudaFree(kv.second.dB);
+    cudaFree(kv.second.dAp);
+    cudaFree(kv.second.dBp);
+    cudaFree(kv.second.dlimAp);
+    cudaFree(kv.second.dlimBp);
   }
   DeviceMesh& m = c->dm;
   cudaFree(m.topo);

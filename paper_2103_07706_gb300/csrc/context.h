@@ -26,6 +26,13 @@ struct AvgPlan {
   double* dB = nullptr;      // [K+1][M]  backward combine
   int* dlimA = nullptr;      // per 8-row tile of A: number of k with a nonzero entry
   int* dlimB = nullptr;      // per 8-row tile of B: number of (reordered) shifts with a nonzero entry
+  // shifts in +s / -s pairs with equal coefficients and weights (symmetric
+  // rules): the paired contractions replace dA / dB (then null)
+  int P = 0;                 // pairs (0: not paired)
+  double* dAp = nullptr;     // [P][K+1] c_k of each pair
+  double* dBp = nullptr;     // [K+1][P] w c_k of each pair
+  int* dlimAp = nullptr;     // per 8-pair tile: number of k with a nonzero entry
+  int* dlimBp = nullptr;     // per 8-row tile: number of pairs with a nonzero entry
   cudaGraphExec_t exec = nullptr;
   bool timed = false;        // captured with CG event brackets
   int launches = 0;          // kernels in the captured graph

@@ -269,6 +269,18 @@ int combine_tile();
 cudaError_t launch_combine(const double* A, int Mo, int Ki, const int* lim, const double* in, int64_t in_stride,
                            double* out, int64_t out_stride, int64_t len, cudaStream_t st, bool fp32 = false);
 
+// The contractions for shifts in +/- pairs (equal coefficients and weights):
+// forward out[2p] = E_p + O_p, out[2p+1] = E_p - O_p from A [P][Ki] (even and
+// odd k of row p), lim per tile of combine_tile() pairs; backward out[k] =
+// sum_p B[k][p] (k even ? R[2p+1] + R[2p] : R[2p+1] - R[2p]), lim per tile of
+// combine_tile() rows (pairs with a nonzero entry).
+cudaError_t launch_combine_pairs_fwd(const double* A, int P, int Ki, const int* lim, const double* in,
+                                     int64_t in_stride, double* out, int64_t out_stride, int64_t len,
+                                     cudaStream_t st, bool fp32 = false);
+cudaError_t launch_combine_pairs_bwd(const double* B, int Ko, int P, const int* lim, const double* R,
+                                     int64_t r_stride, double* out, int64_t out_stride, int64_t len,
+                                     cudaStream_t st);
+
 // out = a x + b y (+ c z); any of y, z may be null.
 cudaError_t launch_lincomb(double* out, double a, const double* x, double b, const double* y,
                            double c, const double* z, int64_t len, cudaStream_t st);

@@ -703,6 +703,91 @@ __global__ void __launch_bounds__(256) k_combine(const double* __restrict__ A, i
   }
 }
 
+// The same contractions when the shifts come in pairs +s, -s with equal
+// coefficients c_k(lam |s|) and weights (a symmetric rule): for pair p,
+//   E_p = sum_{k even} c_pk Q_k,  O_p = sum_{k odd} c_pk Q_k,
+//   U_{2p} = E_p + O_p (s > 0),  U_{2p+1} = E_p - O_p (s < 0),
+// one multiply-add per pair and k instead of one per shift and k.  A is
+// [P][Ki] (c_pk), lim[t] the k range of pair tile t.
+template <int MT, typename TA>
+__global__ void __launch_bounds__(256) k_combine_pairs_fwd(const double* __restrict__ A, int P, int Ki,
+                                                           const int* __restrict__ lim, const double* __restrict__ in,
+                                                           int64_t in_stride, double* out, int64_t out_stride,
+                                                           int64_t len) {
+  extern __shared__ __align__(16) unsigned char sA_raw[];
+  TA* sA = reinterpret_cast<TA*>(sA_raw);  // [MT][Ki]
+  const int p0 = blockIdx.y * MT;
+  const int kn = lim ? lim[blockIdx.y] : Ki;
+  for (int t = threadIdx.x; t < MT * Ki; t += blockDim.x) {
+    int pp = p0 + t / Ki, k = t % Ki;
+    sA[t] = pp < P ? (TA)A[(int64_t)pp * Ki + k] : TA(0);
+  }
+  __syncthreads();
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < len; j += (int64_t)gridDim.x * blockDim.x) {
+    TA e[MT], o[MT];
+#pragma unroll
+    for (int t = 0; t < MT; ++t) { e[t] = TA(0); o[t] = TA(0); }
+    int k = 0;
+    for (; k + 1 < kn; k += 2) {
+      const TA v0 = (TA)__ldg(&in[(int64_t)k * in_stride + j]);
+      const TA v1 = (TA)__ldg(&in[(int64_t)(k + 1) * in_stride + j]);
+#pragma unroll
+      for (int t = 0; t < MT; ++t) {
+        e[t] = fma(sA[t * Ki + k], v0, e[t]);
+        o[t] = fma(sA[t * Ki + k + 1], v1, o[t]);
+      }
+    }
+    if (k < kn) {
+      const TA v0 = (TA)__ldg(&in[(int64_t)k * in_stride + j]);
+#pragma unroll
+      for (int t = 0; t < MT; ++t) e[t] = fma(sA[t * Ki + k], v0, e[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < MT; ++t)
+      if (p0 + t < P) {
+        out[(int64_t)(2 * (p0 + t)) * out_stride + j] = (double)(e[t] + o[t]);
+        out[(int64_t)(2 * (p0 + t) + 1) * out_stride + j] = (double)(e[t] - o[t]);
+      }
+  }
+}
+
+// Backward contraction over pairs: y_k = sum_p B_kp (k even ? S_p : D_p) with
+// S_p = r_{2p+1} + r_{2p}, D_p = r_{2p+1} - r_{2p} (B_kp = w_p c_pk; the
+// pair's +s member carries (-1)^k, its -s member 1).  B is [Ko][P], lim[t]
+// the number of pairs of row tile t with a nonzero entry; MT is even, so the
+// parity of row k0 + t is that of t.
+template <int MT>
+__global__ void __launch_bounds__(256) k_combine_pairs_bwd(const double* __restrict__ B, int Ko, int P,
+                                                           const int* __restrict__ lim, const double* __restrict__ R,
+                                                           int64_t r_stride, double* out, int64_t out_stride,
+                                                           int64_t len) {
+  static_assert(MT % 2 == 0, "row tiles start at even k");
+  extern __shared__ __align__(16) unsigned char sB_raw[];
+  double* sB = reinterpret_cast<double*>(sB_raw);  // [MT][P]
+  const int k0 = blockIdx.y * MT;
+  const int pn = lim ? lim[blockIdx.y] : P;
+  for (int t = threadIdx.x; t < MT * P; t += blockDim.x) {
+    int kk = k0 + t / P, pp = t % P;
+    sB[t] = kk < Ko ? B[(int64_t)kk * P + pp] : 0.0;
+  }
+  __syncthreads();
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < len; j += (int64_t)gridDim.x * blockDim.x) {
+    double acc[MT];
+#pragma unroll
+    for (int t = 0; t < MT; ++t) acc[t] = 0.0;
+    for (int pp = 0; pp < pn; ++pp) {
+      const double rp = __ldg(&R[(int64_t)(2 * pp) * r_stride + j]);
+      const double rm = __ldg(&R[(int64_t)(2 * pp + 1) * r_stride + j]);
+      const double S = rm + rp, D = rm - rp;
+#pragma unroll
+      for (int t = 0; t < MT; ++t) acc[t] = fma(sB[t * P + pp], (t & 1) ? D : S, acc[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < MT; ++t)
+      if (k0 + t < Ko) out[(int64_t)(k0 + t) * out_stride + j] = acc[t];
+  }
+}
+
 __global__ void k_lincomb(double* out, double a, const double* __restrict__ x, double b,
                           const double* __restrict__ y, double c, const double* __restrict__ z, int64_t len) {
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < len; j += (int64_t)gridDim.x * blockDim.x) {
@@ -902,6 +987,42 @@ cudaError_t launch_combine(const double* A, int Mo, int Ki, const int* lim, cons
   dim3 grid((unsigned)grid_for(len, 256, 152 * 4), (unsigned)((Mo + MT - 1) / MT));
   if (fp32) k_combine<MT, float><<<grid, 256, smem, st>>>(A, Mo, Ki, lim, in, in_stride, out, out_stride, len);
   else k_combine<MT, double><<<grid, 256, smem, st>>>(A, Mo, Ki, lim, in, in_stride, out, out_stride, len);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine_pairs_fwd(const double* A, int P, int Ki, const int* lim, const double* in,
+                                     int64_t in_stride, double* out, int64_t out_stride, int64_t len,
+                                     cudaStream_t st, bool fp32) {
+  constexpr int MT = 8;
+  const size_t smem = (fp32 ? sizeof(float) : sizeof(double)) * MT * Ki;
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_combine_pairs_fwd<MT, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_combine_pairs_fwd<MT, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  dim3 grid((unsigned)grid_for(len, 256, 152 * 4), (unsigned)((P + MT - 1) / MT));
+  if (fp32)
+    k_combine_pairs_fwd<MT, float><<<grid, 256, smem, st>>>(A, P, Ki, lim, in, in_stride, out, out_stride, len);
+  else
+    k_combine_pairs_fwd<MT, double><<<grid, 256, smem, st>>>(A, P, Ki, lim, in, in_stride, out, out_stride, len);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine_pairs_bwd(const double* B, int Ko, int P, const int* lim, const double* R,
+                                     int64_t r_stride, double* out, int64_t out_stride, int64_t len,
+                                     cudaStream_t st) {
+  constexpr int MT = 8;
+  const size_t smem = sizeof(double) * MT * P;
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_combine_pairs_bwd<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  dim3 grid((unsigned)grid_for(len, 256, 152 * 4), (unsigned)((Ko + MT - 1) / MT));
+  k_combine_pairs_bwd<MT><<<grid, 256, smem, st>>>(B, Ko, P, lim, R, r_stride, out, out_stride, len);
   return cudaGetLastError();
 }
 

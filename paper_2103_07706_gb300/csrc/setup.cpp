@@ -898,7 +898,11 @@ int shifts_weights(double T, int M, int rule, std::vector<double>* s, std::vecto
   s->assign(M, 0.0);
   w->assign(M, 0.0);
   if (rule == PAVG_QUAD_MIDPOINT) {
-    for (int m = 0; m < M; ++m) (*s)[m] = -0.5 * T + (m + 0.5) * T / M;
+    // exactly antisymmetric: s_{M-1-m} = -s_m (and s = 0 in the middle of an odd M)
+    for (int m = 0; m < M / 2; ++m) {
+      (*s)[m] = -0.5 * T + (m + 0.5) * T / M;
+      (*s)[M - 1 - m] = -(*s)[m];
+    }
   } else if (rule == PAVG_QUAD_CLOSED) {
     if (M < 3 || M % 2 == 0) return PAVG_ERR_INVAL;
     int Nh = (M - 1) / 2;
