@@ -131,11 +131,21 @@ def velocity_dofs_from_streamfunction(verts, cells, edges, psi):
     return u
 
 
-def harmonic_state(verts, cells, seed, lmax, eta_rms=100.0, g=9.80616, omega=7.292e-5):
+def harmonic_state(verts, cells, seed, lmax, eta_rms=100.0, g=9.80616, omega=7.292e-5, rossby=None):
     """Balanced seeded state U = [u (3E + 3F), eta (3F)] as float64.
 
-    Returns (U, info) with info = {"rossby": ..., "u_rms": ...}.
+    With `rossby` given, the amplitude is chosen instead so that the Rossby
+    number (below) takes that value: u and eta are both proportional to the
+    amplitude, so the state at eta_rms is scaled by rossby / Ro(eta_rms), and
+    info["eta_rms"] reports the resulting elevation rms.
+
+    Returns (U, info) with info = {"rossby": ..., "u_rms": ..., "eta_rms": ...}.
     """
+    if rossby is not None:
+        U, info = harmonic_state(verts, cells, seed, lmax, eta_rms, g, omega)
+        f = rossby / info["rossby"]
+        info = dict(info, rossby=info["rossby"] * f, u_rms=info["u_rms"] * f, eta_rms=eta_rms * f)
+        return U * f, info
     verts = np.asarray(verts, dtype=np.float64)
     cells = np.asarray(cells, dtype=np.int64)
     edges = canonical_edges(cells)
@@ -161,7 +171,7 @@ def harmonic_state(verts, cells, seed, lmax, eta_rms=100.0, g=9.80616, omega=7.2
     radius = float(np.linalg.norm(verts[0]))
     l_eff = max(1.0, float(np.sqrt(np.sum(coeffs ** 2 * np.arange(lmax + 1)[:, None] ** 2) / np.sum(coeffs ** 2))))
     rossby = u_rms / (f0 * math.pi * radius / l_eff)
-    return np.concatenate([u, eta]), {"rossby": rossby, "u_rms": u_rms, "edges": E, "cells": F}
+    return np.concatenate([u, eta]), {"rossby": rossby, "u_rms": u_rms, "eta_rms": eta_rms, "edges": E, "cells": F}
 
 
 def tc5_state(verts, cells, u0=20.0, H=5960.0, g=9.8, omega=7.292e-5, b0=2000.0, lat_c=math.pi / 6.0,

@@ -466,3 +466,17 @@ def test_shift_marching_parity(r, T, M, rule):
     want = averaging.averaged_rhs_marching(o, T, M, U, rule)
     assert_close(o, g.averaged_rhs_marching(T, M, dev(U)).cpu().numpy(), want)
     g.sync()
+
+
+@pytest.mark.parametrize("r", [3, 4])
+def test_parity_at_rossby_0p1(r):
+    """States at Rossby number 0.1 (the configurations' regime, 10x the
+    default amplitude): N is 100x stronger relative to L, the upwind choice
+    flips at more facet points, and the parity bound is the same."""
+    from paper_2103_07706_gb300.inputs import harmonic_state
+    g, o = gpu(r), orc(r)
+    U, info = harmonic_state(o.mesh.verts, o.mesh.cells, 2103, 8 if r < 4 else 16, rossby=0.1)
+    assert abs(info["rossby"] - 0.1) < 1e-12
+    assert_close(o, g.nonlinear(dev(U)).cpu().numpy(), o.N(U))
+    assert_close(o, g.averaged_rhs(3600.0, 8, dev(U)).cpu().numpy(), o.averaged_rhs(3600.0, 8, U))
+    g.sync()

@@ -81,3 +81,16 @@ def test_mixed_full_size_vs_fp64_gpu():
     assert du <= 1e-5 and de <= 5e-4, (du, de)
     g64.close()
     gmx.close()
+
+
+def test_mixed_at_rossby_0p1():
+    """Mixed precision on a Rossby-0.1 state (refinement 4, M = 16, T = 1 h)
+    against the oracle: the measured error is printed; bounds u <= 1e-5,
+    eta <= 1e-4."""
+    from paper_2103_07706_gb300.inputs import harmonic_state
+    g, o = gpu(4, precision=MIXED), orc(4)
+    U, _ = harmonic_state(o.mesh.verts, o.mesh.cells, 2103, 16, rossby=0.1)
+    ru, re = rel(o, g.averaged_rhs(3600.0, 16, dev(U)).cpu().numpy(), o.averaged_rhs(3600.0, 16, U))
+    print(f"mixed precision averaged_rhs r4 M16 T1h, Rossby 0.1: rel L2 u {ru:.2e} eta {re:.2e}")
+    assert ru <= 1e-5 and re <= 1e-4, (ru, re)
+    g.sync()

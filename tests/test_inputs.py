@@ -81,3 +81,19 @@ def test_tc5_state():
     assert b.max() <= 2000.0 and b.max() > 1500.0 and (b >= 0).all()
     lat = np.arcsin(z / R)
     assert (b[np.abs(lat - math.pi / 6) > math.pi / 9 + 0.01] == 0).all()
+
+
+def test_harmonic_state_at_a_requested_rossby_number():
+    """The amplitude that gives Rossby 0.1 (the configurations' regime): the
+    same field scaled, u and eta by the same factor, still divergence free."""
+    from paper_2103_07706_gb300.inputs import harmonic_state
+    from tests.conftest import oracle_model
+    m = oracle_model(3)
+    U0, i0 = harmonic_state(m.mesh.verts, m.mesh.cells, 7, 8)
+    U1, i1 = harmonic_state(m.mesh.verts, m.mesh.cells, 7, 8, rossby=0.1)
+    assert abs(i1["rossby"] - 0.1) < 1e-12
+    f = 0.1 / i0["rossby"]
+    assert np.allclose(U1, U0 * f, rtol=1e-15, atol=0.0)
+    assert abs(i1["eta_rms"] - 100.0 * f) < 1e-9 * f
+    assert 500.0 < i1["eta_rms"] < 5000.0
+    assert np.abs(m.ops.D @ U1[: m.n_u]).max() <= 1e-12 * np.abs(m.ops.D).max() * np.abs(U1[: m.n_u]).max()
