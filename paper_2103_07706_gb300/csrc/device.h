@@ -33,7 +33,7 @@ struct DeviceMesh {
   double* M2e = nullptr;            // [6][F] DG1 element mass matrices, packed 00, 01, 02, 11, 12, 22
   double* M2i = nullptr;            // [6][F] their inverses
   double* geo_c = nullptr;          // [6][kCellQ3][F] G00, G01, G11, w / det^2, d0 det / det, d1 det / det
-  double* geo_f = nullptr;          // [8][kFacetQ3][E] plus side G00, G01, G11, det; then minus side
+  double* geo_f = nullptr;          // [8][kFacetQ3][E] plus side G00, G01, G11, 1 / det; then minus side
 };
 
 // Scratch of the persistent CG solver.

@@ -10,6 +10,8 @@
 // arithmetic, so the result does not depend on the order of arrival.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "device.h"
 #include "device_common.cuh"
 
@@ -376,7 +378,7 @@ __device__ __forceinline__ void load_side(const DeviceMesh& m, const double* __r
 // the cubic map's at the point otherwise.
 template <typename R>
 struct SideGeom {
-  R G00, G01, G11, det;
+  R G00, G01, G11, inv_det;  // J^T J and 1 / det
 };
 
 template <typename R>
@@ -388,10 +390,10 @@ struct FacetValues {
   R up0, up1, um0, um1;
 };
 
-// Values shared by the two cells of a facet at point p, evaluated with
-// explicitly rounded operations so that both cells obtain identical bits.
-// Upwind: the side the flow leaves (flux > 0: plus); the printed rule of
-// Sec. 2.5 (u~ = u+ when u . n+ < 0) is the alternative for the velocity.
+// Values shared by the two cells of a facet at point p (formed once per edge
+// and point, for both cells).  Upwind: the side the flow leaves (flux > 0:
+// plus); the printed rule of Sec. 2.5 (u~ = u+ when u . n+ < 0) is the
+// alternative for the velocity.
 template <typename R, typename TT>
 __device__ __forceinline__ FacetValues<R> facet_point(const TT& T, const Side<R>& P, const SideGeom<R>& gP, int lp,
                                                       const Side<R>& Mn, const SideGeom<R>& gM, int lm, int p,
@@ -420,11 +422,11 @@ __device__ __forceinline__ FacetValues<R> facet_point(const TT& T, const Side<R>
   if (plus_up_vel) {
     R g0 = O::fma(gP.G00, a0, O::mul(gP.G01, a1));
     R g1 = O::fma(gP.G01, a0, O::mul(gP.G11, a1));
-    tan = O::div(O::fma(dp0, g0, O::mul(dp1, g1)), gP.det);
+    tan = O::mul(O::fma(dp0, g0, O::mul(dp1, g1)), gP.inv_det);
   } else {
     R g0 = O::fma(gM.G00, b0, O::mul(gM.G01, b1));
     R g1 = O::fma(gM.G01, b0, O::mul(gM.G11, b1));
-    tan = -O::div(O::fma(dm0, g0, O::mul(dm1, g1)), gM.det);
+    tan = -O::mul(O::fma(dm0, g0, O::mul(dm1, g1)), gM.inv_det);
   }
   f.flux = flux;
   f.tan = tan;
@@ -465,6 +467,11 @@ __global__ void __launch_bounds__(128) k_facets(DeviceMesh m, const double* __re
   double rp[12], rm[12], ep[3] = {0.0, 0.0, 0.0}, em[3] = {0.0, 0.0, 0.0};
 #pragma unroll
   for (int j = 0; j < 12; ++j) rp[j] = rm[j] = 0.0;
+  R inv_p = R(0), inv_m = R(0);  // flat cells: one reciprocal per side and edge
+  if constexpr (GEO != 3) {
+    inv_p = R(1) / P.det;
+    inv_m = R(1) / Mn.det;
+  }
 #pragma unroll 1
   for (int p = 0; p < NQ; ++p) {
     const R wp = T.fq_w[p];
@@ -476,15 +483,25 @@ __global__ void __launch_bounds__(128) k_facets(DeviceMesh m, const double* __re
       gM = {(R)__ldg(&m.geo_f[4 * PE + o]), (R)__ldg(&m.geo_f[5 * PE + o]), (R)__ldg(&m.geo_f[6 * PE + o]),
             (R)__ldg(&m.geo_f[7 * PE + o])};
     } else {
-      gP = {P.G00, P.G01, P.G11, P.det};
-      gM = {Mn.G00, Mn.G01, Mn.G11, Mn.det};
+      gP = {P.G00, P.G01, P.G11, inv_p};
+      gM = {Mn.G00, Mn.G01, Mn.G11, inv_m};
     }
     const FacetValues<R> f = facet_point(T, P, gP, lp, Mn, gM, lm, p, upwind);
-    const R scp = -wp * f.tan / gP.det, scm = wp * f.tan / gM.det;
+    // u_perp . w_j = cross2(u_hat, psi_j) / det on each side, times w (t . u~)
+    const R tw = wp * f.tan;
+    const R scp = -tw * gP.inv_det, scm = tw * gM.inv_det;
+    const R Ap = scp * f.up0, Bp = scp * f.up1, Am = scm * f.um0, Bm = scm * f.um1;
 #pragma unroll
     for (int j = 0; j < 12; ++j) {
-      rp[j] += (double)(scp * (f.up0 * T.fq_psi[0][lp][p][j][1] - f.up1 * T.fq_psi[0][lp][p][j][0]));
-      rm[j] += (double)(scm * (f.um0 * T.fq_psi[1][lm][p][j][1] - f.um1 * T.fq_psi[1][lm][p][j][0]));
+      const R* qp = T.fq_psi[0][lp][p][j];
+      const R* qm = T.fq_psi[1][lm][p][j];
+      if constexpr (std::is_same<R, double>::value) {
+        rp[j] = fma(Ap, qp[1], fma(-Bp, qp[0], rp[j]));
+        rm[j] = fma(Am, qm[1], fma(-Bm, qm[0], rm[j]));
+      } else {  // FP32 contributions, FP64 sums over the points
+        rp[j] += (double)fmaf(Ap, qp[1], -Bp * qp[0]);
+        rm[j] += (double)fmaf(Am, qm[1], -Bm * qm[0]);
+      }
     }
     const R fhp = kStrongDG ? wp * f.flux * (f.hp - f.hup) : -wp * f.flux * f.hup;
     const R fhm = kStrongDG ? wp * f.flux * (f.hup - f.hm) : wp * f.flux * f.hup;
@@ -593,13 +610,22 @@ __global__ void __launch_bounds__(128) k_nonlinear(DeviceMesh m, const double* _
     const R k4 = (u0 * v1) * W, k5 = (-u0 * v0 + half_ke) * W;
 #pragma unroll
     for (int i = 0; i < 12; ++i) {
-      R t = k0 * T.cq_psi[q][i][0];
-      t = fma(k1, T.cq_psi[q][i][1], t);
-      t = fma(k2, T.cq_dpsi[q][i][0][0], t);
-      t = fma(k3, T.cq_dpsi[q][i][0][1], t);
-      t = fma(k4, T.cq_dpsi[q][i][1][0], t);
-      t = fma(k5, T.cq_dpsi[q][i][1][1], t);
-      r[i] += (double)t;
+      if constexpr (std::is_same<R, double>::value) {  // straight into the point sum
+        double t = fma(k0, T.cq_psi[q][i][0], r[i]);
+        t = fma(k1, T.cq_psi[q][i][1], t);
+        t = fma(k2, T.cq_dpsi[q][i][0][0], t);
+        t = fma(k3, T.cq_dpsi[q][i][0][1], t);
+        t = fma(k4, T.cq_dpsi[q][i][1][0], t);
+        r[i] = fma(k5, T.cq_dpsi[q][i][1][1], t);
+      } else {  // FP32 contribution of the point, FP64 sum over the points
+        R t = k0 * T.cq_psi[q][i][0];
+        t = fma(k1, T.cq_psi[q][i][1], t);
+        t = fma(k2, T.cq_dpsi[q][i][0][0], t);
+        t = fma(k3, T.cq_dpsi[q][i][0][1], t);
+        t = fma(k4, T.cq_dpsi[q][i][1][0], t);
+        t = fma(k5, T.cq_dpsi[q][i][1][1], t);
+        r[i] += (double)t;
+      }
     }
     if (kStrongDG) {
       // div_hat(u_hat h_hat) = h_hat (d00 + d11) + u_hat . grad_hat h_hat (DG1: constant gradient)

@@ -122,7 +122,7 @@ struct HostCellData {
   std::vector<double> M2i;     // [6][F] their inverses, same packing
   std::vector<double> geo_c;   // [6][kCellQ3][F] per cell point: G00, G01, G11, w / det^2,
                                // (d det / d xi0) / det, (d det / d xi1) / det
-  std::vector<double> geo_f;   // [8][kFacetQ3][E] per edge point: the plus cell's G00, G01, G11, det,
+  std::vector<double> geo_f;   // [8][kFacetQ3][E] per edge point: the plus cell's G00, G01, G11, 1 / det,
                                // then the minus cell's, each at its own parameter of the point
 };
 // Element data on the flat (geometry_degree 1) or piecewise cubic (3) surface.

@@ -847,7 +847,7 @@ void build_cell_data(const Mesh& m, const RefElement& el, double omega, int geom
         PointGeometry g;
         p3_eval(nodes, kEdgeStart[loc[side]][0] + t * kEdgeDir[loc[side]][0],
                 kEdgeStart[loc[side]][1] + t * kEdgeDir[loc[side]][1], &g);
-        const double v[4] = {g.G00, g.G01, g.G11, g.det};
+        const double v[4] = {g.G00, g.G01, g.G11, 1.0 / g.det};
         for (int k = 0; k < 4; ++k) out->geo_f[(4 * side + k) * PE + p * E + e] = v[k];
       }
     }

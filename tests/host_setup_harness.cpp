@@ -17,7 +17,8 @@
 //                         G00, G01, G11 of G = J^T J); prints "n_u F".  With
 //                         DEGREE 3 (the piecewise cubic surface of Sec. 3) also
 //                         PREFIX.m2e, .m2i (float64 [6][F]), .geoc (float64
-//                         [6][25][F]) and .geof (float64 [8][5][E])
+//                         [6][25][F]) and .geof (float64 [8][5][E]; G00, G01, G11,
+//                         1 / det per side)
 //   stroud N              the N x N Stroud conical product rule: "x y w" lines
 //   tables                the reference tables the kernels read from constant
 //                         memory: prints D (3 x 12), then M2 and M2^{-1} (3 x 3)

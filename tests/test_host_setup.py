@@ -181,7 +181,7 @@ def test_cubic_cell_data_match_oracle(harness, tmp_path, r):
         gs = [asm.maps.geometry(EDGE_START[i][None, :] + t[:, None] * EDGE_DIR[i][None, :]) for i in range(3)]
         G = np.stack([x["G"] for x in gs])[loc, cells]           # (E, 5, 2, 2)
         det = np.stack([x["det"] for x in gs])[loc, cells]
-        for k, v in enumerate([G[..., 0, 0], G[..., 0, 1], G[..., 1, 1], det]):
+        for k, v in enumerate([G[..., 0, 0], G[..., 0, 1], G[..., 1, 1], 1.0 / det]):
             assert np.abs(geof[4 * side + k] - v.T).max() <= 1e-12 * np.abs(v).max(), (side, k)
 
 
