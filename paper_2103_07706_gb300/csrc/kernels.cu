@@ -246,12 +246,17 @@ __global__ void __launch_bounds__(128) k_apply_K(DeviceMesh m, const double* __r
       r[j] = fma(a, u[i], r[j]);
     }
   }
+  // the orientation signs are +-1: applied as sign flips of the operands
+  // (exact, and no FP64 multiplications), the same numbers as D_ki sg_i u_i
+  double us[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) us[i] = sg[i] < 0.0 ? -u[i] : u[i];
   double Du[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     double t = 0.0;
 #pragma unroll
-    for (int i = 0; i < 12; ++i) t = fma(c_tab.D[k][i] * sg[i], u[i], t);
+    for (int i = 0; i < 12; ++i) t = fma(c_tab.D[k][i], us[i], t);
     Du[k] = t;
   }
 #pragma unroll
@@ -259,7 +264,7 @@ __global__ void __launch_bounds__(128) k_apply_K(DeviceMesh m, const double* __r
     double t = 0.0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) t = fma(c_tab.D[k][i], eta[k], t);
-    double v = s * fma(g * sg[i], t, r[i]);
+    double v = s * fma(g, sg[i] < 0.0 ? -t : t, r[i]);
     bool own = i >= 9 || ((al >> (i / 3)) & 1u);
     if (own && y_u) v += __ldg(&y_u[dof[i]]);
     if (i < 9) atomicAdd(&ru[dof[i]], v);
@@ -352,7 +357,8 @@ __device__ __forceinline__ void load_side(const DeviceMesh& m, const double* __r
   double cd[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
-    cd[k] = sg[k] * __ldg(&U[dof[k]]);
+    const double v = __ldg(&U[dof[k]]);
+    cd[k] = sg[k] < 0.0 ? -v : v;  // orientation sign (+-1) as a sign flip
     S.c[k] = (R)cd[k];
   }
   {
@@ -661,7 +667,7 @@ __global__ void __launch_bounds__(128) k_nonlinear(DeviceMesh m, const double* _
   cell_dofs(m, c, dof, sg);
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
-    double v = sg[k] * r[k];
+    double v = sg[k] < 0.0 ? -r[k] : r[k];  // orientation sign as a sign flip
     if (k < 9) atomicAdd(&Rout[dof[k]], v);
     else Rout[dof[k]] = v;
   }
