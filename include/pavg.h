@@ -70,10 +70,11 @@ extern "C" {
                                     residuals; falls back to PAVG_SOLVER_MIXED where the parts do not
                                     fit in shared memory (refinement 7 and above on 152 SMs) */
 #define PAVG_PRECISION_FP64 0    /* every result FP64-accurate (mass solves to cg_rtol) */
-#define PAVG_PRECISION_MIXED 1   /* N and the forward shift contraction in FP32 arithmetic (FP64 sums
-                                    over quadrature points), mass solves to max(cg_rtol, 1e-5) (one FP32
-                                    CG sweep, FP64 residual); the weighted sum over shifts, state
-                                    vectors, recurrences and timestep updates stay FP64 */
+#define PAVG_PRECISION_MIXED 1   /* N, the forward shift contraction and the K-hat products of L in
+                                    FP32 arithmetic (FP64 sums over quadrature points), mass solves to
+                                    max(cg_rtol, 1e-5) (one FP32 sweep, FP64 residual); the weighted sum
+                                    over shifts, state vectors, recurrences and timestep updates stay
+                                    FP64 */
 
 typedef struct pavg_ctx pavg_ctx; /* opaque, library-owned */
 

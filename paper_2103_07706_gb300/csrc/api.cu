@@ -114,7 +114,7 @@ int enq_step(pavg_ctx* ctx, const double* in, double s, const double* y, const d
   if (in) {
     CK(cudaMemsetAsync(ctx->ru, 0, sizeof(double) * 3 * m.E, st));
     KL(launch_apply_K(m, in, s, ctx->p.g, ctx->p.H, y, y ? y + nu : nullptr, z ? z + nu : nullptr, ctx->ru,
-                      out + nu, st));
+                      out + nu, st, ctx->p.precision == PAVG_PRECISION_MIXED));
     return enq_cg(ctx, ctx->ru, out, 1.0, z, st);
   }
   // in == 0: out = M^{-1} y + z
@@ -462,7 +462,7 @@ void free_device_mesh(DeviceMesh& m) {
   cudaFree(m.cell_edges); cudaFree(m.cell_aligned); cudaFree(m.edge_plus); cudaFree(m.edge_minus);
   cudaFree(m.edge_lpos); cudaFree(m.M1); cudaFree(m.C); cudaFree(m.det); cudaFree(m.G); cudaFree(m.dinv);
   cudaFree(m.M1f); cudaFree(m.Pinv); cudaFree(m.M1p); cudaFree(m.tri);
-  cudaFree(m.M2e); cudaFree(m.M2i); cudaFree(m.geo_c); cudaFree(m.geo_f);
+  cudaFree(m.M2e); cudaFree(m.M2i); cudaFree(m.geo_c); cudaFree(m.geo_f); cudaFree(m.Cf);
   m = DeviceMesh();
 }
 
@@ -495,6 +495,7 @@ int build_shared_mesh(const pavg_params* p, SharedMesh* sh, std::string* why) {
                   upload(&m.G, hc.G) == cudaSuccess && upload(&m.dinv, hc.dinv) == cudaSuccess &&
                   upload(&m.Pinv, hc.Pinv) == cudaSuccess && upload(&m.tri, hc.tri) == cudaSuccess &&
                   upload(&m.M1p, hc.M1p) == cudaSuccess && upload(&m.M1f, hc.M1f) == cudaSuccess &&
+                  upload(&m.Cf, std::vector<float>(hc.C.begin(), hc.C.end())) == cudaSuccess &&
                   (!cubic || (upload(&m.M2e, hc.M2e) == cudaSuccess && upload(&m.M2i, hc.M2i) == cudaSuccess &&
                               upload(&m.geo_c, hc.geo_c) == cudaSuccess && upload(&m.geo_f, hc.geo_f) == cudaSuccess));
   if (!ok) {

@@ -21,6 +21,7 @@ struct DeviceMesh {
   uint8_t* edge_lpos = nullptr;     // [E]
   double* M1 = nullptr;             // [78][F]
   double* C = nullptr;              // [66][F]
+  float* Cf = nullptr;              // [66][F] C rounded to FP32 (the mixed mode's K-hat products)
   double* det = nullptr;            // [F]
   double* G = nullptr;              // [3][F]
   double* dinv = nullptr;           // [n_u]
@@ -246,7 +247,7 @@ cudaError_t launch_cg(const DeviceMesh& m, const CgWork& w, const CgParams& cp, 
 // (the first 3E entries) before the call.
 cudaError_t launch_apply_K(const DeviceMesh& m, const double* U, double s, double g, double H,
                            const double* y_u, const double* y_eta, const double* z_eta,
-                           double* ru, double* eta_out, cudaStream_t st);
+                           double* ru, double* eta_out, cudaStream_t st, bool fp32 = false);
 
 // Weak-form right-hand side of N for B states [B][n] -> r [B][n]
 // (r's velocity edge DOFs must be zeroed first), in chunks of `chunk` states:

@@ -30,6 +30,14 @@ cudaError_t upload_tables(const ConstTables& t) {
   return cudaMemcpyToSymbol(c_tabf, &f, sizeof(f));
 }
 
+// The reference tables in the arithmetic type R (FP64, or the FP32 copy).
+template <typename R>
+__device__ __forceinline__ const TablesT<R>& tab();
+template <>
+__device__ __forceinline__ const TablesT<double>& tab<double>() { return c_tab; }
+template <>
+__device__ __forceinline__ const TablesT<float>& tab<float>() { return c_tabf; }
+
 cudaError_t upload_tables3(const TablesP3<double>& t) {
   cudaError_t e = cudaMemcpyToSymbol(c_tab3, &t, sizeof(t));
   if (e != cudaSuccess) return e;
@@ -221,6 +229,10 @@ __device__ __forceinline__ double sym3(const double* __restrict__ P, int64_t F, 
 }
 
 // ru = y_u + s (-C u + g D^T eta);  eta_out = M2^{-1}(y_eta + s (-H D u)) + z_eta.
+// T: the arithmetic of the K-hat products (double; float in the mixed mode,
+// with the FP32 copy of C): the additions of y and z, the M2 inverse and the
+// outputs stay FP64 (they are the recurrences' own terms).
+template <typename T>
 __global__ void __launch_bounds__(128) k_apply_K(DeviceMesh m, const double* __restrict__ U, double s,
                                                  double g, double H, const double* __restrict__ y_u,
                                                  const double* __restrict__ y_eta,
@@ -229,42 +241,45 @@ __global__ void __launch_bounds__(128) k_apply_K(DeviceMesh m, const double* __r
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= m.F) return;
   const int64_t F = m.F;
+  const TablesT<T>& TT = tab<T>();
   int dof[12];
   double sg[12];
   unsigned al = cell_dofs(m, c, dof, sg);
-  double u[12], r[12], eta[3];
+  T u[12], r[12], eta[3];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) { u[k] = __ldg(&U[dof[k]]); r[k] = 0.0; }
+  for (int k = 0; k < 12; ++k) { u[k] = (T)__ldg(&U[dof[k]]); r[k] = T(0); }
 #pragma unroll
-  for (int k = 0; k < 3; ++k) eta[k] = __ldg(&U[m.n_u + 3 * c + k]);
+  for (int k = 0; k < 3; ++k) eta[k] = (T)__ldg(&U[m.n_u + 3 * c + k]);
 #pragma unroll
   for (int i = 0; i < 12; ++i) {
 #pragma unroll
     for (int j = i + 1; j < 12; ++j) {
-      double a = __ldg(&m.C[pasym(i, j) * F + c]);
+      T a;
+      if constexpr (std::is_same<T, double>::value) a = __ldg(&m.C[pasym(i, j) * F + c]);
+      else a = __ldg(&m.Cf[pasym(i, j) * F + c]);
       r[i] = fma(-a, u[j], r[i]);
       r[j] = fma(a, u[i], r[j]);
     }
   }
   // the orientation signs are +-1: applied as sign flips of the operands
-  // (exact, and no FP64 multiplications), the same numbers as D_ki sg_i u_i
-  double us[12];
+  // (exact, and no multiplications), the same numbers as D_ki sg_i u_i
+  T us[12];
 #pragma unroll
   for (int i = 0; i < 12; ++i) us[i] = sg[i] < 0.0 ? -u[i] : u[i];
-  double Du[3];
+  T Du[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    double t = 0.0;
+    T t = T(0);
 #pragma unroll
-    for (int i = 0; i < 12; ++i) t = fma(c_tab.D[k][i], us[i], t);
+    for (int i = 0; i < 12; ++i) t = fma(TT.D[k][i], us[i], t);
     Du[k] = t;
   }
 #pragma unroll
   for (int i = 0; i < 12; ++i) {
-    double t = 0.0;
+    T t = T(0);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) t = fma(c_tab.D[k][i], eta[k], t);
-    double v = s * fma(g, sg[i] < 0.0 ? -t : t, r[i]);
+    for (int k = 0; k < 3; ++k) t = fma(TT.D[k][i], eta[k], t);
+    double v = (double)((T)s * fma((T)g, sg[i] < 0.0 ? -t : t, r[i]));
     bool own = i >= 9 || ((al >> (i / 3)) & 1u);
     if (own && y_u) v += __ldg(&y_u[dof[i]]);
     if (i < 9) atomicAdd(&ru[dof[i]], v);
@@ -273,7 +288,7 @@ __global__ void __launch_bounds__(128) k_apply_K(DeviceMesh m, const double* __r
   double rl[3];
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
-    rl[l] = s * (-H * Du[l]);
+    rl[l] = (double)((T)s * (-(T)H * Du[l]));
     if (y_eta) rl[l] += __ldg(&y_eta[3 * c + l]);
   }
   if (m.M2i) {  // cubic cells: the cell's own M2^{-1}
@@ -303,12 +318,6 @@ __global__ void __launch_bounds__(128) k_apply_K(DeviceMesh m, const double* __r
 // Arithmetic type R: double (FP64 path) or float (mixed precision, where each
 // quadrature point's contribution is formed in FP32 and the sums over the
 // quadrature points are accumulated in FP64).
-template <typename R>
-__device__ __forceinline__ const TablesT<R>& tab();
-template <>
-__device__ __forceinline__ const TablesT<double>& tab<double>() { return c_tab; }
-template <>
-__device__ __forceinline__ const TablesT<float>& tab<float>() { return c_tabf; }
 template <typename R>
 __device__ __forceinline__ const TablesP3<R>& tab3();
 template <>
@@ -962,9 +971,10 @@ cudaError_t launch_cg(const DeviceMesh& m, const CgWork& w, const CgParams& cp, 
 
 cudaError_t launch_apply_K(const DeviceMesh& m, const double* U, double s, double g, double H,
                            const double* y_u, const double* y_eta, const double* z_eta, double* ru,
-                           double* eta_out, cudaStream_t st) {
+                           double* eta_out, cudaStream_t st, bool fp32) {
   int g_ = (int)((m.F + 127) / 128);
-  k_apply_K<<<g_, 128, 0, st>>>(m, U, s, g, H, y_u, y_eta, z_eta, ru, eta_out);
+  if (fp32 && m.Cf) k_apply_K<float><<<g_, 128, 0, st>>>(m, U, s, g, H, y_u, y_eta, z_eta, ru, eta_out);
+  else k_apply_K<double><<<g_, 128, 0, st>>>(m, U, s, g, H, y_u, y_eta, z_eta, ru, eta_out);
   return cudaGetLastError();
 }
 

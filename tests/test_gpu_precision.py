@@ -1,7 +1,8 @@
 """Mixed-precision mode (PAVG_PRECISION_MIXED) against FP64 references.
 
-The mode computes N and the forward shift contraction in FP32 arithmetic (with
-FP64 sums over the quadrature points and an FP64 cell divergence), solves with
+The mode computes N, the forward shift contraction and the K-hat products of
+L in FP32 arithmetic (with FP64 sums over the quadrature points and an FP64
+cell divergence; the recurrences add the FP32 products in FP64), solves with
 M1 by FP32 CG inside FP64 residual refinement stopped at a relative residual
 of 1e-5, and keeps the Chebyshev recurrences, the weighted sum over shifts and
 the timestep update in FP64.  Stated bounds, relative L2 per field in the

@@ -53,7 +53,10 @@ def test_noalloc_mixed_precision_within_the_solve_tolerance():
     """Under PAVG_PRECISION_MIXED both pavg_linear and the allocation-free
     entry point stop their mass solves at a relative residual of 1e-5 (with
     different solvers: block-Jacobi FP32 refinement and FP64 Jacobi CG), so
-    their results agree to about that level, not to rounding."""
+    their results agree to about that level, not to rounding; pavg_linear
+    also forms the K-hat products in FP32 in this mode (the allocation-free
+    entry point in FP64), which the eta part (a cell-local solve on both
+    paths) shows at the FP32 rounding level."""
     import torch
 
     from paper_2103_07706_gb300 import pavg
@@ -70,7 +73,7 @@ def test_noalloc_mixed_precision_within_the_solve_tolerance():
         ee = np.linalg.norm(got[m.n_u:] - want[m.n_u:]) / np.linalg.norm(want[m.n_u:])
         print(f"noalloc vs linear, mixed precision: u {eu:.2e}, eta {ee:.2e}")
         assert eu <= 1e-4, eu
-        assert ee <= 1e-13, ee   # the eta part is a cell-local 3x3 solve in FP64 on both paths
+        assert ee <= 1e-6, ee   # FP32 against FP64 K-hat products, then the same cell-local solve
     m.close()
 
 
