@@ -7,11 +7,12 @@ M1 by FP32 CG inside FP64 residual refinement stopped at a relative residual
 of 1e-5, and keeps the Chebyshev recurrences, the weighted sum over shifts and
 the timestep update in FP64.  Stated bounds, relative L2 per field in the
 finite element norms (measured values in brackets):
-  N, refinement 3               u, eta <= 1e-5     [2.8e-6, 2.0e-7]
-  e^{tL}, refinement 3, 1 h     u, eta <= 1e-6     [1.4e-7, 8.5e-8]
-  averaged_rhs, r4, M 16        u, eta <= 1e-5     [3.4e-6, 2.0e-6]
-  two timesteps, r3, M 8        u, eta <= 1e-6     [1.1e-7, 5.1e-8]
-  averaged_rhs, r6, M 64, 1 h   u <= 1e-5, eta <= 5e-4   [3.3e-6, 1.5e-4]
+  N, refinement 3               u, eta <= 1e-5     [2.9e-6, 2.0e-7]
+  e^{tL}, refinement 3, 1 h     u, eta <= 1e-6     [2.5e-7, 2.0e-7]
+  averaged_rhs, r4, M 16        u, eta <= 1e-5     [3.7e-6, 2.0e-6]
+  two timesteps, r3, M 8        u, eta <= 1e-6     [1.3e-7, 9.2e-8]
+  averaged_rhs, r6, M 64, 1 h   u <= 1e-5, eta <= 5e-4   [6.1e-6, 3.2e-4]
+(with the K-hat products in FP64 the r6 errors were 3.3e-6 and 1.3e-4).
 The refinement-6 eta bound is wider because the seeded state is geostrophic:
 u is tangent to the contours of eta and divergence-free, so the exact eta
 part of N is zero and what the FP64 path returns is discretisation residue,
