@@ -48,7 +48,6 @@ constexpr int kSdThreads = 768;   // one thread per local cell (up to 768) and t
 constexpr int kSdRounds = 2;      // local triples per thread at most
 constexpr int kSdMatStride = 79;  // floats per cell's packed matrix (78, padded: conflict-free columns)
 constexpr int kSdMaxIters = 256;  // Chebyshev iterations per sweep at most (the set-up caps it)
-constexpr double kSdCheapRes2 = 1e-18;  // (1e-9)^2: below it a sweep's residual comes from the FP32 recursion
 
 __device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
   unsigned long long v;
@@ -261,7 +260,6 @@ __global__ void __launch_bounds__(NT, 1)
   const double tol2 = sp.rtol * sp.rtol * bb;
   double rr = bb;
   int sweeps = 0;
-  bool true_res = true;  // r64 is b - M1 x formed in FP64 (not a recursive update)
   const float inv_theta = (float)(1.0 / sp.theta);
 
   while (alive && !bad && !conv && sweeps < sp.max_sweeps) {
@@ -348,27 +346,13 @@ __global__ void __launch_bounds__(NT, 1)
           float u[3];
           apply_p(P[j], r[j], u);
           s_d[lt] = make_float4(fmaf(c1, dk[0], c2 * u[0]), fmaf(c1, dk[1], c2 * u[1]), fmaf(c1, dk[2], c2 * u[2]), 0.f);
-        } else {
-          s_d[lt] = make_float4(r[j][0], r[j][1], r[j][2], 0.f);  // the sweep's final FP32 residual
         }
       }
       if (fail) atomicOr(w.flags, kFlagTimeout);
       if (__syncthreads_or(fail)) return;
     }
-    const double inv = 1.0 / scale;
-    // ---- A sweep that started from a true FP64 residual of at most 1e-9 ||b||
-    //      takes its new residual from the FP32 recursion instead of a product:
-    //      r32 started as fl(r ||r||^-1) and ended as r32 - M1 x_32 (up to the
-    //      recursion's rounding, about 1e-6 of the start), so
-    //        r <- (r - r32_start ||r||) + r32_end ||r||
-    //      is the update r - M1 x_32 ||r|| to within 1e-6 ||r|| <= 1e-15 ||b||.
-    //      No product and no exchange (a shared triple's copies of r32 are
-    //      bitwise equal in both parts).  rr and bb are grid-wide values, so
-    //      every block takes the same branch; a sweep after such a one forms
-    //      b - M1 x in FP64 again.
-    const bool cheap = true_res && rr <= kSdCheapRes2 * bb;
-    if (cheap) rr_loc = 0.0;
     // ---- FP64 refinement: x += x_32 ||r||, staged in shared memory for the product
+    const double inv = 1.0 / scale;
 #pragma unroll
     for (int j = 0; j < kSdRounds; ++j) {
       const int lt = tid + j * NT;
@@ -378,30 +362,10 @@ __global__ void __launch_bounds__(NT, 1)
         double* px = &w.x64[3 * (int64_t)(l0 + lt) + k];
         const double xn = fma((double)x[j][k], inv, __ldcg(px));
         __stcg(px, xn);
-        if (cheap) {
-          double* pr = &w.r64[3 * (int64_t)(l0 + lt) + k];
-          const double rp = __ldcg(pr);
-          const float r0 = (float)(rp * scale);  // the sweep's start value, formed as above
-          const float4 rf = s_d[lt];               // its end value (the last inner iteration)
-          const float re = k == 0 ? rf.x : (k == 1 ? rf.y : rf.z);
-          const double rk = fma((double)re, inv, fma(-(double)r0, inv, rp));
-          __stcg(pr, rk);
-          if (gt[j] >> 31) rr_loc = fma(rk, rk, rr_loc);
-        } else {
-          s_x64[3 * lt + k] = xn;
-        }
+        s_x64[3 * lt + k] = xn;
       }
     }
     have_x = true;
-    if (cheap) {
-      alive = sd_grid_sum<NT>(w, nb, bid, base + (++ep), rr_loc, &rr, limit);
-      ++sweeps;
-      if (!isfinite(rr)) bad = true;
-      conv = rr <= tol2;
-      true_res = false;
-      continue;
-    }
-    true_res = true;
     __syncthreads();
     ++ep;
     const unsigned tag64 = (unsigned)(base + ep);
