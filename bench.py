@@ -56,7 +56,7 @@ SOLVER_KERNELS = {0: "k_cg_ir (persistent mixed-precision M1 solve: FP32 CG + FP
                   1: "k_cg (persistent FP64 Jacobi CG)",
                   2: "k_cheb_sd (subdomain M1 solve: FP32 Chebyshev per SM, neighbour exchange, FP64 sweeps)"}
 SOLVER_DRAM_BYTES = {(SOLVER_KERNELS[0], 6): (206.434304 + 80.506624) * 1e6,
-                     (SOLVER_KERNELS[2], 6): (101.747712 + 6.292480) * 1e6}
+                     (SOLVER_KERNELS[2], 6): (101.791744 + 5.998592) * 1e6}
 
 
 def _cg_flops(F, n_u, iters, sweeps):
