@@ -197,17 +197,7 @@ __global__ void __launch_bounds__(NT, 1)
   // the recurrence's scalars, the same in every sweep: d_{k+1} = c1[k] d_k + c2[k] P r_{k+1}
   __shared__ float s_c1[kSdMaxIters], s_c2[kSdMaxIters];
 
-  const int nb = gridDim.x, tid = threadIdx.x;
-  int bid = blockIdx.x;
-  if (sd.smid_part) {  // one block per SM: the part belongs to the SM, not to the block index
-    unsigned id;
-    asm volatile("mov.u32 %0, %%smid;" : "=r"(id));
-    bid = id < (unsigned)sd.nsmid ? __ldg(&sd.smid_part[id]) : -1;
-    if (bid < 0 || bid >= nb) {  // not the placement the set-up saw: refuse (the others' waits run out)
-      if (tid == 0) atomicOr(w.flags, kFlagTimeout);
-      return;
-    }
-  }
+  const int nb = gridDim.x, bid = blockIdx.x, tid = threadIdx.x;
   if (sp.stall_mode == 1 && bid == sp.stall_part) return;  // test hook: never arrives
   const int64_t F = m.F;
   const int c0 = sd.cell0[bid], nc = sd.cell0[bid + 1] - c0;
@@ -486,22 +476,6 @@ __global__ void __launch_bounds__(NT, 1)
 
 }  // namespace
 
-namespace {
-
-// Records the SM id of each block (launched with the solver's shared memory,
-// so one block per SM).
-__global__ void k_smid_probe(int* out) {
-  extern __shared__ float4 smem_probe[];
-  if (threadIdx.x == 0) {
-    unsigned id;
-    asm volatile("mov.u32 %0, %%smid;" : "=r"(id));
-    out[blockIdx.x] = (int)id;
-    smem_probe[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-}
-
-}  // namespace
-
 template <class T>
 static cudaError_t upload_vec(T** dst, const std::vector<T>& v) {
   cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * std::max<size_t>(v.size(), 1));
@@ -563,45 +537,13 @@ cudaError_t sd_configure(int64_t F, int64_t E, const std::vector<int32_t>& tri, 
     return e;
   }
   s.P = P;
-  // placement: with one part per SM of the device, the parts follow the SM
-  // ids (read once by a probe with the solver's shared memory per block, so
-  // one block per SM).  If the probe does not see P distinct SMs the parts
-  // stay with the block indices.
-  if (P == sms) {
-    int* d_ids = nullptr;
-    std::vector<int> ids(P, -1);
-    e = cudaMalloc((void**)&d_ids, sizeof(int) * P);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_smid_probe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) {
-      k_smid_probe<<<P, 32, smem>>>(d_ids);
-      e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = cudaMemcpy(ids.data(), d_ids, sizeof(int) * P, cudaMemcpyDeviceToHost);
-    cudaFree(d_ids);
-    if (e != cudaSuccess) {
-      sd_free(&s);
-      return e;
-    }
-    std::vector<int> sorted(ids);
-    std::sort(sorted.begin(), sorted.end());
-    const bool distinct = sorted[0] >= 0 && std::adjacent_find(sorted.begin(), sorted.end()) == sorted.end();
-    if (distinct) {
-      std::vector<int32_t> table(sorted.back() + 1, -1);
-      for (int k = 0; k < P; ++k) table[sorted[k]] = k;
-      if ((e = upload_vec(&s.smid_part, table)) != cudaSuccess) {
-        sd_free(&s);
-        return e;
-      }
-      s.nsmid = (int)table.size();
-    }
-  }
   *sd = s;
   return cudaSuccess;
 }
 
 void sd_free(SdMesh* sd) {
   cudaFree(sd->cell0); cudaFree(sd->lt0); cudaFree(sd->lt_gtri); cudaFree(sd->lt_slot); cudaFree(sd->lt_recv);
-  cudaFree(sd->cell_lt); cudaFree(sd->cell_send); cudaFree(sd->smid_part);
+  cudaFree(sd->cell_lt); cudaFree(sd->cell_send);
   *sd = SdMesh();
 }
 

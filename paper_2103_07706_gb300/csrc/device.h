@@ -117,12 +117,6 @@ struct SdMesh {
   int32_t* lt_recv = nullptr;    // [lt] partner's send slot of a shared triple, -1 otherwise
   ushort4* cell_lt = nullptr;    // [F] local triples of the cell's four (cell, q)
   int4* cell_send = nullptr;     // [F] send slot of (cell, q), q < 3, -1 when not shared
-  // placement (launches of one part per SM of the device): the part of the
-  // block on SM id s is smid_part[s], the parts in the order of the SM ids, so
-  // that consecutive parts (neighbours in the mesh) sit on SMs with close ids;
-  // null: part = block index
-  int32_t* smid_part = nullptr;  // [nsmid], -1 for an id no block ran on
-  int nsmid = 0;
 };
 
 // Per-context scratch of the subdomain solver.
